@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark: FFG build + PageRank + proportion of centrality on one space.
+
+Workload (per rank): the single large tuning space -- 9 parameters,
+2,162,688 raw / 1,419,392 valid configurations under three product and
+divisibility clauses, seeded multimodal runtimes with 3 % failures (seed
+1 + rank).  One step = for the Hamming and the adjacent neighbourhood:
+build the FFG (count + fill), PageRank in FP32 (damping 0.85, FP64
+reductions) and C_p at p = 1, 5, 10 %.
+
+Metric: FFG edges x PageRank iterations per second over whole steps
+(sum over both graphs of E * iterations / step time), inputs resident in
+HBM, L2 flushed (256 MiB write) between steps outside the timed events.
+Also reported: the FP64 PageRank on the same graphs, spaces/s, an end-to-end
+run through the public API from pinned host memory, the roofline of the
+PageRank kernel, the CPU oracle as a baseline, and SM clocks.
+
+``--impl reference`` times the CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FFG edges·PageRank-iters/sec"
+UNIT = "edges*iters/s"
+P_LIST = [0.01, 0.05, 0.10]
+DAMPING = 0.85
+TOL = 1e-12
+WORKLOAD = ("single large space: 9 params, 2,162,688 raw / 1,419,392 valid configs, "
+            "Hamming + adjacent FFGs, FP32 PageRank (damping 0.85, FP64 reductions), "
+            "C_p at 1/5/10 %")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ffg", choices=["ffg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------
+
+ORACLE_SAMPLE = ("oracle (plain C, 1 thread) on the same space, Hamming FFG: full build + "
+                 "20 FP64 power iterations + C_p")
+
+
+def oracle_sample(spec, f, iters=20):
+    """One bounded sample of the workload on the CPU oracle; returns (units, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    og = oracle.build(spec, f, oracle.HAMMING)
+    x, it, res, conv = oracle.pagerank_power(og, DAMPING, TOL, max_iter=iters)
+    oracle.centrality(og, x / x.sum(), P_LIST)
+    dt = time.perf_counter() - t0
+    return og.n_edges * it, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import ffg_inputs as fi
+    spec = fi.single_large()
+    f = fi.runtimes(spec, seed=1)
+    for _ in range(args.warmup):
+        oracle_sample(spec, f)
+    units = secs = 0.0
+    for _ in range(args.steps):
+        u, s = oracle_sample(spec, f)
+        units += u
+        secs += s
+    v = units / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": ORACLE_SAMPLE},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": ORACLE_SAMPLE},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for row in open(self.path):
+            parts = [x.strip() for x in row.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], parts[5:9]):
+                if val.lower() in ("active", "0x1") or val.startswith("Active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# roofline helpers
+# --------------------------------------------------------------------------
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def pagerank_bytes(n, e, iters, elem):
+    """Algorithmic DRAM bytes of one PageRank launch:
+    per iteration in_idx 4E + in_ptr 8N + outdeg 4N + own w read + new w write
+    (2 * elem * N); prologue outdeg + w write, epilogue outdeg + w read + ranks
+    write."""
+    per_iter = 4 * e + 8 * (n + 1) + 4 * n + 2 * elem * n
+    return iters * per_iter + (4 + elem) * n + (4 + 2 * elem) * n
+
+
+def ncu_traffic(kernel_file):
+    """DRAM traffic per launch from the committed ncu summary, if the kernel
+    source is unchanged since the capture."""
+    summary = os.path.join(ROOT, "profiles", "pagerank_f32_single_large_hamming.txt")
+    src = os.path.join(ROOT, "paper_2210_01465_gb300", "csrc", kernel_file)
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        kv = {}
+        for line in open(summary):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") != sha:
+            return None, None
+        return float(kv["dram_bytes_per_launch"]), float(kv["iters_per_launch"])
+    except Exception:
+        return None, None
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import ffg_inputs as fi
+    import paper_2210_01465_gb300 as ffg
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    ffg.build()
+    ffg.load()
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    spec = fi.single_large()
+    f_host = fi.runtimes(spec, seed=1 + rank)
+    space = ffg.Space.from_spec(spec)
+    fd = torch.from_numpy(f_host).to(dev)
+    f_pinned = torch.from_numpy(f_host).pin_memory()
+
+    nbhs = (ffg.HAMMING, ffg.ADJACENT)
+    ws_b = {n: ffg.workspace(ffg.ffg_workspace_bytes(space, n), dev) for n in nbhs}
+    graphs = {}
+    for n in nbhs:
+        graphs[n] = ffg.build_graph(space, fd, n, ws=ws_b[n])
+    N = graphs[ffg.HAMMING].n_nodes
+    pr_need = ffg.pagerank_workspace_bytes(N, ffg.F64)
+    pr_ws = {n: ffg.workspace(pr_need, dev) for n in nbhs}
+    ranks32 = {n: torch.empty(N, dtype=torch.float32, device=dev) for n in nbhs}
+    ranks64 = {n: torch.empty(N, dtype=torch.float64, device=dev) for n in nbhs}
+    cp_need = ffg.centrality_workspace_bytes(len(P_LIST))
+    cp_ws = ffg.workspace(cp_need, dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
+
+    def step(fit, prec=ffg.F32, record=None):
+        """One pass of the path over both neighbourhoods; returns sum E*iters."""
+        units = 0
+        rk = ranks32 if prec == ffg.F32 else ranks64
+        for n in nbhs:
+            g = graphs[n]
+            need = ffg.ffg_workspace_bytes(space, n)
+            g0 = ffg.ffg_graph()
+            st = ffg.ffg_build_count(space, fit.data_ptr(), n, 1e10, g0, ws_b[n].data_ptr(), need,
+                                     sh)
+            assert st == 0 and g0.n_edges == g.n_edges and g0.n_nodes == g.n_nodes, st
+            g.c.f_opt, g.c.n_minima = g0.f_opt, g0.n_minima
+            st = ffg.ffg_build_fill(space, fit.data_ptr(), n, 1e10, g.c, ws_b[n].data_ptr(),
+                                    need, sh)
+            assert st == 0, st
+            if record is not None:
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ea.record(stream)
+            st, _, _ = ffg.pagerank_solve(g.c, DAMPING, TOL, 10000, prec, rk[n].data_ptr(), 0,
+                                          pr_ws[n].data_ptr(), pr_need, sync=False, stream=sh)
+            assert st == 0, st
+            if record is not None:
+                eb.record(stream)
+            st, it, res = ffg.pagerank_query(pr_ws[n].data_ptr(), sh)
+            assert st == 0, (st, it, res)
+            if record is not None:
+                record.append((n, ea, eb, it))
+            out = np.zeros(len(P_LIST))
+            st = ffg.centrality_proportion(g.c, fit.data_ptr(), rk[n].data_ptr(), prec, P_LIST,
+                                           out, cp_ws.data_ptr(), cp_need, sh)
+            assert st == 0, st
+            units += g.n_edges * it
+        return units
+
+    def timed(prec, steps, warmup, e2e=False):
+        for _ in range(warmup):
+            step(fd, prec)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        total_ms, units, recs = 0.0, 0, []
+        l0 = ffg.ffg_launch_count()
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if e2e:
+                fd.copy_(f_pinned, non_blocking=True)
+            units += step(fd, prec, recs)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        torch.cuda.synchronize(dev)
+        launches = ffg.ffg_launch_count() - l0
+        return total_ms, units, recs, launches
+
+    def reduce_max_sum(ms, units):
+        if world == 1:
+            return ms, units
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+        return float(t.item()), float(u.item())
+
+    clocks = ClockSampler(dev.index if world == 1 else local)
+    ms32, units32, recs32, launches = timed(ffg.F32, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms64, units64, recs64, _ = timed(ffg.F64, max(2, args.steps // 2), 1)
+    e2e = None
+    if not args.no_e2e:
+        ms_e, units_e, _, _ = timed(ffg.F32, args.steps, 1, e2e=True)
+        ms_e, units_e = reduce_max_sum(ms_e, units_e)
+        h2d = f_host.nbytes
+        d2h = 2 * (40 + 32 + 8 * (len(P_LIST) + 1))
+        e2e = {"value": units_e / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e / args.steps}
+    ms32_all, units32_all = reduce_max_sum(ms32, units32)
+    ms64_all, units64_all = reduce_max_sum(ms64, units64)
+
+    # roofline of the dominant kernel: FP32 PageRank launch on the Hamming FFG
+    gH = graphs[ffg.HAMMING]
+    durs = [ea.elapsed_time(eb) for (n, ea, eb, it) in recs32 if n == ffg.HAMMING]
+    its = [it for (n, ea, eb, it) in recs32 if n == ffg.HAMMING]
+    bytes_launch = pagerank_bytes(gH.n_nodes, gH.n_edges, statistics.mean(its), 4)
+    achieved = bytes_launch / (statistics.mean(durs) / 1e3) / 1e9
+    peak, peak_kind = hbm_peak()
+    traffic, traffic_iters = ncu_traffic("ffg_pagerank.cu")
+    if traffic is not None and traffic_iters:
+        traffic = traffic / traffic_iters * statistics.mean(its)
+    pr_ms_32 = sum(ea.elapsed_time(eb) for (_, ea, eb, _) in recs32)
+    pr_ms_64 = sum(ea.elapsed_time(eb) for (_, ea, eb, _) in recs64)
+    it_32 = sum(it for (*_, it) in recs32)
+    it_64 = sum(it for (*_, it) in recs64)
+    durs64 = [ea.elapsed_time(eb) for (n, ea, eb, it) in recs64 if n == ffg.HAMMING]
+    its64 = [it for (n, ea, eb, it) in recs64 if n == ffg.HAMMING]
+    ach64 = pagerank_bytes(gH.n_nodes, gH.n_edges, statistics.mean(its64), 8) / \
+        (statistics.mean(durs64) / 1e3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        u, s = oracle_sample(spec, f_host)
+        cpu = {"value": u / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": ORACLE_SAMPLE + f" ({s:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": units32_all / (ms32_all / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms32_all / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_raw": gH.n_raw, "n_nodes": gH.n_nodes,
+                       "edges_hamming": gH.n_edges,
+                       "edges_adjacent": graphs[ffg.ADJACENT].n_edges,
+                       "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                       "parallelism": f"{world} independent spaces (seed 1+rank)"},
+            "spaces_per_s": world * 2 * args.steps / (ms32_all / 1e3),
+            "pagerank_iters_per_step": it_32 / args.steps,
+            "f64_plain": {"value": units64_all / (ms64_all / 1e3), "unit": UNIT,
+                          "ms_per_step": ms64_all / max(2, args.steps // 2),
+                          "pagerank_iters_per_step": it_64 / max(2, args.steps // 2),
+                          "pagerank_gbs": ach64},
+            "fp32_vs_fp64_pagerank_per_iter_speedup":
+                (pr_ms_64 / it_64) / (pr_ms_32 / it_32) if it_32 and it_64 else None,
+            "roofline": {"bound": "hbm", "kernel": "k_pagerank<float> (Hamming FFG)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": traffic, "algorithmic_bytes": bytes_launch,
+                         "launch_ms": statistics.mean(durs)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * ffg.h -- C ABI of the GB300 (sm_103a) fitness-flow-graph library.
+ *
+ * The library computes the landscape-difficulty metric of "Benchmarking
+ * optimization algorithms for auto-tuning GPU kernels" (Schoonhoven, van
+ * Werkhoven, Batenburg; arXiv 2210.01465):
+ *
+ *   1. the fitness flow graph (FFG) of a discrete tuning space (Sec. VII-B):
+ *      every valid configuration is a node, with a directed edge to every
+ *      neighbour -- Hamming (Sec. III-B, Eq. 2) or adjacent-value (the
+ *      restriction stated right after Eq. 2) -- whose fitness is strictly
+ *      lower;
+ *   2. PageRank centrality of every node on that graph (Sec. VII-B);
+ *   3. the p-proportion of centrality C_p (Sec. VII-B, Eq. 3): the share of
+ *      the centrality of all local minima held by minima within (1+p) of the
+ *      optimal fitness.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers documented "device" must be CUDA device (or managed) memory of
+ *    the current device; "host" pointers are ordinary host memory.  The
+ *    caller owns every buffer.  The library never allocates device memory:
+ *    scratch space is a caller-provided workspace whose size is reported by
+ *    the matching *_workspace_bytes function.  A workspace must be 256-byte
+ *    aligned and must not be used by two calls that can run concurrently.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it in order; the only host
+ *    synchronisations are the documented scalar read-backs.
+ *  - Every function returns an ffg_status.  On an error other than
+ *    FFG_ERR_NOT_CONVERGED the contents of output buffers are unspecified.
+ *    Argument errors are detected on the host before any work is enqueued.
+ *  - All functions are thread-safe as long as their buffers are distinct.
+ */
+#ifndef FFG_H
+#define FFG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FFG_MAX_PARAMS 16       /* parameters per space */
+#define FFG_MAX_VALUES 1024     /* entries over all value lists of a space */
+#define FFG_MAX_CONSTRAINTS 16  /* clauses per space */
+#define FFG_MAX_P 32            /* thresholds per centrality call */
+
+typedef enum {
+    FFG_OK = 0,
+    FFG_ERR_INVALID_ARG = 1,   /* a bad argument, detected on the host */
+    FFG_ERR_OVERFLOW = 2,      /* a size or product does not fit the index types */
+    FFG_ERR_CUDA = 3,          /* a CUDA runtime call failed (see ffg_last_error) */
+    FFG_ERR_EMPTY = 4,         /* the space has no valid configuration / no minimum */
+    FFG_ERR_NOT_CONVERGED = 5, /* max_iter reached; the ranks are still written */
+    FFG_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired */
+    FFG_ERR_NO_MEMORY = 7      /* the workspace passed is too small */
+} ffg_status;
+
+typedef enum { FFG_HAMMING = 0, FFG_ADJACENT = 1 } ffg_nbh;
+typedef enum { FFG_F64 = 0, FFG_F32 = 1 } ffg_prec;
+
+/* Constraint clause kinds.  P(mask) is the product of the values of the
+ * parameters whose bit is set in `mask` (1 for an empty mask). */
+typedef enum {
+    FFG_PROD_LE = 0,      /* P(mask_a) <= bound                  */
+    FFG_PROD_GE = 1,      /* P(mask_a) >= bound                  */
+    FFG_DIVIDES = 2,      /* P(mask_b) != 0 and P(mask_a) % P(mask_b) == 0 */
+    FFG_PROD_LE_PROD = 3  /* P(mask_a) <= P(mask_b)              */
+} ffg_constraint_kind;
+
+typedef struct {
+    int32_t kind;      /* ffg_constraint_kind */
+    uint32_t mask_a;   /* bit i = parameter i takes part in the left product */
+    uint32_t mask_b;   /* right product (FFG_DIVIDES, FFG_PROD_LE_PROD) */
+    int32_t reserved;  /* must be 0 */
+    int64_t bound;     /* FFG_PROD_LE / FFG_PROD_GE bound */
+} ffg_constraint;
+
+/* A search space X = S_1 x ... x S_n (Sec. III-B), all arrays in HOST memory.
+ * Raw point r has digits d_i in row-major order (the last parameter varies
+ * fastest): r = sum_i d_i * stride_i, stride_{n-1} = 1,
+ * stride_i = stride_{i+1} * radix_{i+1}; its value in parameter i is
+ * values[offset_i + d_i] with offset_i = radix_0 + ... + radix_{i-1}.
+ * A raw point is a valid configuration iff every clause holds.
+ * Limits: 1 <= n_params <= 16; radix_i >= 1; sum(radix) <= 1024;
+ * 0 <= n_constraints <= 16; product of radices <= 2^31 - 1; for every clause
+ * and product, prod over the mask of max|value| < 2^63 (else
+ * FFG_ERR_OVERFLOW). */
+typedef struct {
+    int32_t n_params;
+    const int32_t *radix;
+    const int64_t *values;
+    int32_t n_constraints;
+    const ffg_constraint *constraints;
+} ffg_space;
+
+/* The fitness flow graph in DEVICE memory, buffers owned by the caller.
+ * Node v (0 <= v < n_nodes) is the v-th valid raw point in ascending raw
+ * order.  Edge u -> v iff v is a neighbour of u and key(v) < key(u), where
+ * key(x) = f(x) if f(x) < fail_thr and +inf otherwise (failed points, Sec. V:
+ * fitness 1e10; NaN counts as failed).  Both adjacency lists of every node
+ * are sorted by ascending node id.
+ *   out_ptr[n_nodes+1], out_idx[n_edges]  -- CSR of out-edges (int64 / int32)
+ *   in_ptr[n_nodes+1],  in_idx[n_edges]   -- CSR of in-edges
+ *   outdeg[n_nodes]                        -- out-degree (int32)
+ *   node_raw[n_nodes]                      -- raw index of each node (int64)
+ *   is_min[n_nodes]                        -- 1 iff not failed and outdeg == 0
+ *                                             (local minimum, Sec. III-B)
+ * n_raw, n_nodes, n_edges, n_minima and f_opt (best non-failed fitness,
+ * +inf if every node failed) are host fields written by ffg_build_count. */
+typedef struct {
+    int64_t n_raw, n_nodes, n_edges, n_minima;
+    int64_t *out_ptr;
+    int32_t *out_idx;
+    int64_t *in_ptr;
+    int32_t *in_idx;
+    int32_t *outdeg;
+    int64_t *node_raw;
+    uint8_t *is_min;
+    double f_opt;
+} ffg_graph;
+
+/* ---- FFG construction (Sec. III-B neighbourhoods, Sec. VII-B graph) ---- */
+
+/* Bytes of workspace that ffg_build_count / ffg_build_fill need for `space`
+ * (0 if the space is invalid). */
+size_t ffg_workspace_bytes(const ffg_space *space, ffg_nbh nbh);
+
+/* Phase 1 of the build.  fitness_raw: DEVICE, n_raw doubles in raw order.
+ * Validates the space, marks valid points, counts degrees.  Writes
+ * g->n_raw, n_nodes, n_edges, n_minima, f_opt (host fields; the device
+ * pointers of g are not touched) and also *n_nodes / *n_edges when those host
+ * pointers are non-NULL.  Synchronises `stream` once to read the counts.
+ * Keeps per-space state in `workspace` for ffg_build_fill.
+ * FFG_ERR_EMPTY if no configuration is valid. */
+ffg_status ffg_build_count(const ffg_space *space, const double *fitness_raw, ffg_nbh nbh,
+                           double fail_thr, ffg_graph *g, int64_t *n_nodes, int64_t *n_edges,
+                           void *workspace, size_t ws_bytes, void *stream);
+
+/* Phase 2: writes every device array of g.  Must follow ffg_build_count with
+ * the same space, fitness, nbh, fail_thr and workspace (untouched in
+ * between); g's host fields must be those written by ffg_build_count.
+ * Fully asynchronous. */
+ffg_status ffg_build_fill(const ffg_space *space, const double *fitness_raw, ffg_nbh nbh,
+                          double fail_thr, ffg_graph *g, void *workspace, size_t ws_bytes,
+                          void *stream);
+
+/* ---- PageRank (Sec. VII-B) ----
+ * Column-stochastic matrix A[v,u] = 1/outdeg(u) for every edge u -> v, with
+ * damping `damping`, uniform teleport, and the mass of nodes without
+ * out-edges spread uniformly:
+ *   x'[v] = damping * sum_{u -> v} x[u]/outdeg[u]
+ *           + (damping * sum_{outdeg(u)=0} x[u] + 1 - damping) / n_nodes.
+ * Starts from x = 1/n_nodes (or from `ranks` when init != 0; it must then
+ * hold a positive vector summing to 1) and stops when
+ * sum_v |x'[v] - x[v]| < tol, returning x'.  FFG_F32 keeps ranks and the
+ * per-row sums in FP32 and every reduction (dangling mass, residual,
+ * normalisation) in FP64, and also stops once the residual stops decreasing
+ * (the FP32 rounding floor).  `ranks` (DEVICE, n_nodes floats or doubles per
+ * `prec`) receives x' normalised to sum 1.
+ * iters_out / residual_out (HOST) receive the iteration count and the last
+ * residual; when both are NULL nothing is synchronised and the result is
+ * read later with pagerank_query.  FFG_ERR_NOT_CONVERGED after max_iter. */
+size_t pagerank_workspace_bytes(int64_t n_nodes, ffg_prec prec);
+
+ffg_status pagerank_solve(const ffg_graph *g, double damping, double tol, int32_t max_iter,
+                          ffg_prec prec, void *ranks, int init, void *workspace,
+                          size_t ws_bytes, int32_t *iters_out, double *residual_out,
+                          void *stream);
+
+/* Reads the outcome of the last pagerank_solve run in `workspace`
+ * (synchronises `stream`).  Returns that run's status. */
+ffg_status pagerank_query(const void *workspace, int32_t *iters_out, double *residual_out,
+                          void *stream);
+
+/* ---- proportion of centrality (Sec. VII-B, Eq. 3) ----
+ * For each p[k] (HOST, 0 <= p[k], fractions such as 0.05, n_p <= 32):
+ *   C_p = sum_{v min, f(v) <= thr_k} x[v] / sum_{v min} x[v],
+ *   thr_k = f_opt * (1 + p[k]) evaluated in FP64 on the host.
+ * fitness_raw is the build's DEVICE fitness; ranks is the DEVICE output of
+ * pagerank_solve in precision `prec`.  Sums are compensated FP64.
+ * cp_out (HOST, n_p doubles).  Synchronises `stream` once.
+ * FFG_ERR_EMPTY if the graph has no local minimum. */
+size_t centrality_workspace_bytes(int32_t n_p);
+
+ffg_status centrality_proportion(const ffg_graph *g, const double *fitness_raw,
+                                 const void *ranks, ffg_prec prec, const double *p,
+                                 int32_t n_p, double *cp_out, void *workspace, size_t ws_bytes,
+                                 void *stream);
+
+/* ---- diagnostics ---- */
+const char *ffg_status_str(ffg_status s);
+/* Detail of the last error raised on the calling thread ("" if none). */
+const char *ffg_last_error(void);
+/* Number of kernels this library has launched in this process. */
+uint64_t ffg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFG_H */

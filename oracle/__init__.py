@@ -119,9 +119,9 @@ class _SpaceHolder:
             c = self.clauses[k]
             c.kind = _KIND[cl.kind]
             c.n_a, c.n_b = len(cl.a), len(cl.b)
-            for t, i in enumerate(cl.a):
+            for t, i in enumerate(sorted(cl.a)):
                 c.a[t] = i
-            for t, i in enumerate(cl.b):
+            for t, i in enumerate(sorted(cl.b)):
                 c.b[t] = i
             c.bound = int(cl.bound)
         self.s = _Space(len(spec.values), self.radix.ctypes.data_as(C.POINTER(C.c_int32)),

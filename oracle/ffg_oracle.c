@@ -76,9 +76,12 @@ static int product(const or_space *s, const int32_t *digit, const int32_t *idx, 
     return OR_OK;
 }
 
-/* 1 if the configuration satisfies every clause, 0 if not, <0 on error */
+/* 1 if the configuration satisfies every clause, 0 if not, <0 on error.
+ * Every clause is evaluated (no early exit), so a product that does not fit
+ * int64 is reported for any space in which it can occur. */
 static int satisfies(const or_space *s, const int32_t *digit)
 {
+    int all = 1;
     for (int c = 0; c < s->n_clauses; ++c) {
         const or_clause *cl = &s->clauses[c];
         int64_t pa, pb;
@@ -92,9 +95,9 @@ static int satisfies(const or_space *s, const int32_t *digit)
         case OR_PROD_LE_PROD: ok = pa <= pb; break;
         default: return -OR_BAD_ARG;
         }
-        if (!ok) return 0;
+        all = all && ok;
     }
-    return 1;
+    return all;
 }
 
 static int check_clauses(const or_space *s)

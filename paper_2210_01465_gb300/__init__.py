@@ -1,0 +1,315 @@
+"""Fitness flow graphs, PageRank and proportion of centrality on GB300.
+
+Python binding of the C ABI in ``include/ffg.h`` (library
+``lib/libffg_gb300.so``, CUDA kernels for sm_103a).  This module only
+marshals arguments: every step of the computation -- the FFG build of
+Sec. VII-B over the neighbourhoods of Sec. III-B, PageRank, and C_p of
+Sec. VII-B (Eq. 3) -- runs in the library's kernels.  PyTorch provides
+device memory and streams.  There is no CPU fallback: if the library is
+missing, loading it raises.
+
+Two layers:
+
+* same-name wrappers of the C functions (``ffg_build_count``,
+  ``ffg_build_fill``, ``pagerank_solve``, ``pagerank_query``,
+  ``centrality_proportion``, the ``*_workspace_bytes`` queries and the
+  diagnostics), taking device pointers as integers;
+* tensor helpers (``Space``, ``build_graph``, ``pagerank``, ``centrality``)
+  that allocate workspaces and outputs with torch and call the wrappers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from ._build import LIB_PATH, build  # noqa: F401
+
+# ---- constants of include/ffg.h -------------------------------------------
+FFG_OK, FFG_ERR_INVALID_ARG, FFG_ERR_OVERFLOW, FFG_ERR_CUDA = 0, 1, 2, 3
+FFG_ERR_EMPTY, FFG_ERR_NOT_CONVERGED, FFG_ERR_TIMEOUT, FFG_ERR_NO_MEMORY = 4, 5, 6, 7
+HAMMING, ADJACENT = 0, 1
+F64, F32 = 0, 1
+PROD_LE, PROD_GE, DIVIDES, PROD_LE_PROD = 0, 1, 2, 3
+MAX_PARAMS, MAX_VALUES, MAX_CONSTRAINTS, MAX_P = 16, 1024, 16, 32
+_KIND = {"prod_le": PROD_LE, "prod_ge": PROD_GE, "divides": DIVIDES,
+         "prod_le_prod": PROD_LE_PROD}
+
+
+class FFGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        detail = ffg_last_error()
+        super().__init__(f"{where}: {ffg_status_str(status)}" + (f" ({detail})" if detail else ""))
+
+
+class ffg_constraint(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("mask_a", C.c_uint32), ("mask_b", C.c_uint32),
+                ("reserved", C.c_int32), ("bound", C.c_int64)]
+
+
+class ffg_space(C.Structure):
+    _fields_ = [("n_params", C.c_int32), ("radix", C.POINTER(C.c_int32)),
+                ("values", C.POINTER(C.c_int64)), ("n_constraints", C.c_int32),
+                ("constraints", C.POINTER(ffg_constraint))]
+
+
+class ffg_graph(C.Structure):
+    _fields_ = [("n_raw", C.c_int64), ("n_nodes", C.c_int64), ("n_edges", C.c_int64),
+                ("n_minima", C.c_int64), ("out_ptr", C.c_void_p), ("out_idx", C.c_void_p),
+                ("in_ptr", C.c_void_p), ("in_idx", C.c_void_p), ("outdeg", C.c_void_p),
+                ("node_raw", C.c_void_p), ("is_min", C.c_void_p), ("f_opt", C.c_double)]
+
+
+# names of include/ffg.h's entry points (the ABI test checks the header)
+ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
+                "pagerank_workspace_bytes", "pagerank_solve", "pagerank_query",
+                "centrality_workspace_bytes", "centrality_proportion", "ffg_status_str",
+                "ffg_last_error", "ffg_launch_count")
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"FFG CUDA library not built: {p} is missing "
+                          "(run paper_2210_01465_gb300.build())")
+    lib = C.CDLL(p)
+    P = C.POINTER
+    vp, i32, i64, f64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+    lib.ffg_workspace_bytes.argtypes = [P(ffg_space), C.c_int]
+    lib.ffg_workspace_bytes.restype = sz
+    lib.ffg_build_count.argtypes = [P(ffg_space), vp, C.c_int, f64, P(ffg_graph), P(i64), P(i64),
+                                    vp, sz, vp]
+    lib.ffg_build_fill.argtypes = [P(ffg_space), vp, C.c_int, f64, P(ffg_graph), vp, sz, vp]
+    lib.pagerank_workspace_bytes.argtypes = [i64, C.c_int]
+    lib.pagerank_workspace_bytes.restype = sz
+    lib.pagerank_solve.argtypes = [P(ffg_graph), f64, f64, i32, C.c_int, vp, C.c_int, vp, sz,
+                                   P(i32), P(f64), vp]
+    lib.pagerank_query.argtypes = [vp, P(i32), P(f64), vp]
+    lib.centrality_workspace_bytes.argtypes = [i32]
+    lib.centrality_workspace_bytes.restype = sz
+    lib.centrality_proportion.argtypes = [P(ffg_graph), vp, vp, C.c_int, vp, i32, vp, vp, sz, vp]
+    lib.ffg_status_str.argtypes = [C.c_int]
+    lib.ffg_status_str.restype = C.c_char_p
+    lib.ffg_last_error.argtypes = []
+    lib.ffg_last_error.restype = C.c_char_p
+    lib.ffg_launch_count.argtypes = []
+    lib.ffg_launch_count.restype = C.c_uint64
+    if path is None:
+        _lib = lib
+    return lib
+
+
+# ---- same-name wrappers ----------------------------------------------------
+
+def ffg_status_str(status: int) -> str:
+    return load().ffg_status_str(int(status)).decode()
+
+
+def ffg_last_error() -> str:
+    return load().ffg_last_error().decode()
+
+
+def ffg_launch_count() -> int:
+    return int(load().ffg_launch_count())
+
+
+def ffg_workspace_bytes(space: "Space", nbh: int) -> int:
+    return int(load().ffg_workspace_bytes(C.byref(space.c), int(nbh)))
+
+
+def ffg_build_count(space, fitness_raw: int, nbh: int, fail_thr: float, g: ffg_graph,
+                    ws: int, ws_bytes: int, stream: int = 0) -> int:
+    return int(load().ffg_build_count(C.byref(space.c), C.c_void_p(fitness_raw), int(nbh),
+                                      float(fail_thr), C.byref(g), None, None, C.c_void_p(ws),
+                                      int(ws_bytes), C.c_void_p(stream)))
+
+
+def ffg_build_fill(space, fitness_raw: int, nbh: int, fail_thr: float, g: ffg_graph, ws: int,
+                   ws_bytes: int, stream: int = 0) -> int:
+    return int(load().ffg_build_fill(C.byref(space.c), C.c_void_p(fitness_raw), int(nbh),
+                                     float(fail_thr), C.byref(g), C.c_void_p(ws), int(ws_bytes),
+                                     C.c_void_p(stream)))
+
+
+def pagerank_workspace_bytes(n_nodes: int, prec: int) -> int:
+    return int(load().pagerank_workspace_bytes(int(n_nodes), int(prec)))
+
+
+def pagerank_solve(g: ffg_graph, damping: float, tol: float, max_iter: int, prec: int,
+                   ranks: int, init: int, ws: int, ws_bytes: int, sync: bool = True,
+                   stream: int = 0):
+    """Returns (status, iters, residual); iters/residual are None when sync=False."""
+    it, res = C.c_int32(-1), C.c_double(float("nan"))
+    st = load().pagerank_solve(C.byref(g), float(damping), float(tol), int(max_iter), int(prec),
+                               C.c_void_p(ranks), int(init), C.c_void_p(ws), int(ws_bytes),
+                               C.byref(it) if sync else None, C.byref(res) if sync else None,
+                               C.c_void_p(stream))
+    return (int(st), int(it.value), float(res.value)) if sync else (int(st), None, None)
+
+
+def pagerank_query(ws: int, stream: int = 0):
+    it, res = C.c_int32(-1), C.c_double(float("nan"))
+    st = load().pagerank_query(C.c_void_p(ws), C.byref(it), C.byref(res), C.c_void_p(stream))
+    return int(st), int(it.value), float(res.value)
+
+
+def centrality_workspace_bytes(n_p: int) -> int:
+    return int(load().centrality_workspace_bytes(int(n_p)))
+
+
+def centrality_proportion(g: ffg_graph, fitness_raw: int, ranks: int, prec: int, p, cp_out,
+                          ws: int, ws_bytes: int, stream: int = 0) -> int:
+    pv = np.ascontiguousarray(p, dtype=np.float64)
+    assert cp_out.dtype == np.float64 and cp_out.flags.c_contiguous and len(cp_out) >= len(pv)
+    return int(load().centrality_proportion(
+        C.byref(g), C.c_void_p(fitness_raw), C.c_void_p(ranks), int(prec),
+        C.c_void_p(pv.ctypes.data), len(pv), C.c_void_p(cp_out.ctypes.data), C.c_void_p(ws),
+        int(ws_bytes), C.c_void_p(stream)))
+
+
+# ---- tensor helpers ----------------------------------------------------------
+
+class Space:
+    """A search space in the C layout (host arrays kept alive here).
+
+    ``values``: list of integer value lists (one per parameter);
+    ``constraints``: list of (kind, params_a, params_b, bound) with kind one of
+    'prod_le', 'prod_ge', 'divides', 'prod_le_prod' (or the integer codes)
+    and params_* iterables of parameter indices.
+    """
+
+    def __init__(self, values, constraints=()):
+        self.radix = np.ascontiguousarray([len(v) for v in values], dtype=np.int32)
+        flat = [int(x) for v in values for x in v]
+        self.values = np.ascontiguousarray(flat if flat else [0], dtype=np.int64)
+        self.constraints = (ffg_constraint * max(len(constraints), 1))()
+        for k, (kind, pa, pb, bound) in enumerate(constraints):
+            ma = mb = 0
+            for i in pa:
+                if ma >> i & 1:
+                    raise ValueError("a parameter appears twice in one product")
+                ma |= 1 << int(i)
+            for i in pb:
+                if mb >> i & 1:
+                    raise ValueError("a parameter appears twice in one product")
+                mb |= 1 << int(i)
+            c = self.constraints[k]
+            c.kind = _KIND[kind] if isinstance(kind, str) else int(kind)
+            c.mask_a, c.mask_b, c.reserved, c.bound = ma, mb, 0, int(bound)
+        self.c = ffg_space(len(values), self.radix.ctypes.data_as(C.POINTER(C.c_int32)),
+                           self.values.ctypes.data_as(C.POINTER(C.c_int64)), len(constraints),
+                           C.cast(self.constraints, C.POINTER(ffg_constraint)))
+        self.n_raw = int(np.prod(self.radix.astype(np.int64))) if len(values) else 0
+
+    @classmethod
+    def from_spec(cls, spec) -> "Space":
+        """From any object with ``values`` and ``clauses`` (kind, a, b, bound)."""
+        return cls(spec.values, [(cl.kind, cl.a, cl.b, cl.bound) for cl in spec.clauses])
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Graph:
+    """An FFG in device tensors plus its ``ffg_graph`` struct."""
+
+    def __init__(self, n_raw, n_nodes, n_edges, n_minima, f_opt, device):
+        torch = _torch()
+        self.out_ptr = torch.empty(n_nodes + 1, dtype=torch.int64, device=device)
+        self.in_ptr = torch.empty(n_nodes + 1, dtype=torch.int64, device=device)
+        self.out_idx = torch.empty(max(n_edges, 1), dtype=torch.int32, device=device)
+        self.in_idx = torch.empty(max(n_edges, 1), dtype=torch.int32, device=device)
+        self.outdeg = torch.empty(n_nodes, dtype=torch.int32, device=device)
+        self.node_raw = torch.empty(n_nodes, dtype=torch.int64, device=device)
+        self.is_min = torch.empty(n_nodes, dtype=torch.uint8, device=device)
+        self.c = ffg_graph(n_raw, n_nodes, n_edges, n_minima, self.out_ptr.data_ptr(),
+                           self.out_idx.data_ptr(), self.in_ptr.data_ptr(),
+                           self.in_idx.data_ptr(), self.outdeg.data_ptr(),
+                           self.node_raw.data_ptr(), self.is_min.data_ptr(), f_opt)
+
+    n_raw = property(lambda self: int(self.c.n_raw))
+    n_nodes = property(lambda self: int(self.c.n_nodes))
+    n_edges = property(lambda self: int(self.c.n_edges))
+    n_minima = property(lambda self: int(self.c.n_minima))
+    f_opt = property(lambda self: float(self.c.f_opt))
+
+
+def _check(st, where, ok=(FFG_OK,)):
+    if st not in ok:
+        raise FFGError(st, where)
+    return st
+
+
+def workspace(nbytes: int, device="cuda"):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def build_graph(space: Space, fitness, nbh: int = HAMMING, fail_thr: float = 1e10, ws=None,
+                stream=None) -> Graph:
+    """Count, allocate, fill.  ``fitness``: CUDA float64 tensor of n_raw values."""
+    torch = _torch()
+    if not (fitness.is_cuda and fitness.dtype == torch.float64 and fitness.is_contiguous()):
+        raise ValueError("fitness must be a contiguous CUDA float64 tensor")
+    sh = _stream_handle(stream)
+    need = ffg_workspace_bytes(space, nbh)
+    if need == 0:
+        raise FFGError(FFG_ERR_INVALID_ARG, "ffg_workspace_bytes")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, fitness.device)
+    g0 = ffg_graph()
+    _check(ffg_build_count(space, fitness.data_ptr(), nbh, fail_thr, g0, ws.data_ptr(), need, sh),
+           "ffg_build_count")
+    g = Graph(g0.n_raw, g0.n_nodes, g0.n_edges, g0.n_minima, g0.f_opt, fitness.device)
+    _check(ffg_build_fill(space, fitness.data_ptr(), nbh, fail_thr, g.c, ws.data_ptr(), need, sh),
+           "ffg_build_fill")
+    g.nbh = nbh
+    return g
+
+
+def pagerank(g: Graph, damping: float = 0.85, tol: float = 1e-12, max_iter: int = 10000,
+             prec: int = F64, init=None, ws=None, out=None, stream=None):
+    """Returns (ranks tensor, iters, residual, converged)."""
+    torch = _torch()
+    dt = torch.float64 if prec == F64 else torch.float32
+    dev = g.out_ptr.device
+    ranks = out if out is not None else torch.empty(g.n_nodes, dtype=dt, device=dev)
+    if init is not None:
+        ranks.copy_(init)
+    need = pagerank_workspace_bytes(g.n_nodes, prec)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    st, it, res = pagerank_solve(g.c, damping, tol, max_iter, prec, ranks.data_ptr(),
+                                 1 if init is not None else 0, ws.data_ptr(), need, True,
+                                 _stream_handle(stream))
+    _check(st, "pagerank_solve", ok=(FFG_OK, FFG_ERR_NOT_CONVERGED))
+    return ranks, it, res, st == FFG_OK
+
+
+def centrality(g: Graph, fitness, ranks, p, ws=None, stream=None) -> np.ndarray:
+    torch = _torch()
+    prec = F64 if ranks.dtype == torch.float64 else F32
+    need = centrality_workspace_bytes(len(p))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, ranks.device)
+    out = np.zeros(len(p), dtype=np.float64)
+    _check(centrality_proportion(g.c, fitness.data_ptr(), ranks.data_ptr(), prec, p, out,
+                                 ws.data_ptr(), need, _stream_handle(stream)),
+           "centrality_proportion")
+    return out

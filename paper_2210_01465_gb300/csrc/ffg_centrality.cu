@@ -1,0 +1,185 @@
+// ffg_centrality.cu -- p-proportion of centrality C_p (Sec. VII-B, Eq. 3).
+//
+// C_p = sum_{v in L_p} x[v] / sum_{v in L} x[v], L = local minima, L_p = the
+// minima with f(v) <= (1 + p) f_opt.  With the thresholds sorted ascending,
+// a minimum with fitness f falls in bucket b = the first threshold k with
+// f <= thr_k (b = n_p if none); S_p(k) is then the sum of buckets 0..k and
+// S_L the sum of all buckets.  One pass over the nodes fills per-block
+// bucket sums (FP64: per thread, then a warp tree, then compensated across
+// warps), a second one-block launch adds the blocks' buckets in a fixed
+// order with Neumaier's compensated sum, and the host forms the prefix sums
+// and the ratios in FP64.  The threshold decision f <= thr_k is taken in FP64
+// with thr_k computed on the host as f_opt * (1 + p_k).
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "ffg_internal.cuh"
+
+namespace ffg {
+
+namespace {
+
+constexpr int kCpThreads = 256;
+constexpr int kMaxCpBlocks = 1024;
+constexpr int kBuckets = FFG_MAX_P + 1;
+
+struct Thresholds {
+    double thr[FFG_MAX_P];
+    int n;
+};
+
+struct CpWs {
+    double *partials;  // [kMaxCpBlocks][kBuckets][2] (sum, compensation)
+    double *buckets;   // [kBuckets]
+    size_t bytes;
+};
+
+CpWs carve(void *base) {
+    Carver c(base);
+    CpWs w;
+    w.partials = c.take<double>(size_t(kMaxCpBlocks) * kBuckets * 2);
+    w.buckets = c.take<double>(kBuckets);
+    w.bytes = c.off;
+    return w;
+}
+
+__device__ __forceinline__ void neumaier(double &s, double &c, double v) {
+    const double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCpThreads) k_cp_partial(
+    int64_t n, const uint8_t *__restrict__ is_min, const int64_t *__restrict__ node_raw,
+    const double *__restrict__ fit, const T *__restrict__ x, const Thresholds th,
+    double *__restrict__ partials) {
+    double acc[kBuckets];
+    for (int b = 0; b <= th.n; ++b) acc[b] = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (!is_min[v]) continue;
+        const double f = fit[node_raw[v]];
+        int b = 0;
+        while (b < th.n && !(f <= th.thr[b])) ++b;
+        acc[b] += static_cast<double>(x[v]);
+    }
+    __shared__ double red[kCpThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b = 0; b <= th.n; ++b) {
+        double v = acc[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0, c = 0.0;
+            for (int k = 0; k < kCpThreads / 32; ++k) neumaier(s, c, red[k]);
+            partials[(size_t(blockIdx.x) * kBuckets + b) * 2 + 0] = s;
+            partials[(size_t(blockIdx.x) * kBuckets + b) * 2 + 1] = c;
+        }
+    }
+}
+
+__global__ void k_cp_final(const double *__restrict__ partials, int nblocks, int nb,
+                           double *__restrict__ buckets) {
+    const int b = threadIdx.x;
+    if (b > nb) return;
+    double s = 0.0, c = 0.0;
+    for (int k = 0; k < nblocks; ++k) {
+        neumaier(s, c, partials[(size_t(k) * kBuckets + b) * 2 + 0]);
+        neumaier(s, c, partials[(size_t(k) * kBuckets + b) * 2 + 1]);
+    }
+    buckets[b] = s + c;
+}
+
+double host_neumaier(const double *v, int n) {
+    double s = 0.0, c = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double t = s + v[k];
+        if (std::fabs(s) >= std::fabs(v[k])) c += (s - t) + v[k];
+        else c += (v[k] - t) + s;
+        s = t;
+    }
+    return s + c;
+}
+
+}  // namespace
+
+}  // namespace ffg
+
+using namespace ffg;
+
+extern "C" size_t centrality_workspace_bytes(int32_t n_p) {
+    (void)n_p;
+    return carve(nullptr).bytes;
+}
+
+extern "C" ffg_status centrality_proportion(const ffg_graph *g, const double *fitness_raw,
+                                            const void *ranks, ffg_prec prec, const double *p,
+                                            int32_t n_p, double *cp_out, void *workspace,
+                                            size_t ws_bytes, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!g || g->n_nodes <= 0 || !g->is_min || !g->node_raw)
+        return set_error("graph is empty or incomplete"), FFG_ERR_INVALID_ARG;
+    if (!fitness_raw || !ranks || !p || !cp_out || !workspace)
+        return set_error("a pointer argument is NULL"), FFG_ERR_INVALID_ARG;
+    if (n_p < 1 || n_p > FFG_MAX_P)
+        return set_error("n_p must lie in [1,%d]", FFG_MAX_P), FFG_ERR_INVALID_ARG;
+    if (prec != FFG_F64 && prec != FFG_F32)
+        return set_error("unknown precision"), FFG_ERR_INVALID_ARG;
+    for (int k = 0; k < n_p; ++k)
+        if (!(p[k] >= 0.0) || p[k] == __builtin_inf())
+            return set_error("p[%d] must be finite and >= 0", k), FFG_ERR_INVALID_ARG;
+    if (!aligned256(workspace))
+        return set_error("workspace not 256-byte aligned"), FFG_ERR_INVALID_ARG;
+    CpWs w = carve(workspace);
+    if (ws_bytes < w.bytes)
+        return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
+    if (g->n_minima <= 0) return set_error("the graph has no local minimum"), FFG_ERR_EMPTY;
+
+    // thresholds in FP64 on the host: (1 + p) first, then the product
+    std::vector<int> order(n_p);
+    std::vector<double> thr(n_p);
+    for (int k = 0; k < n_p; ++k) {
+        volatile double onep = 1.0 + p[k];
+        thr[k] = g->f_opt * onep;
+    }
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return thr[a] < thr[b]; });
+    Thresholds th;
+    th.n = n_p;
+    for (int k = 0; k < n_p; ++k) th.thr[k] = thr[order[k]];
+
+    int dev = 0, sms = 0;
+    FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
+    FFG_TRY(check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
+    int64_t want = (g->n_nodes + kCpThreads - 1) / kCpThreads;
+    int nblocks = static_cast<int>(std::min<int64_t>(want, std::min(kMaxCpBlocks, sms * 4)));
+    if (nblocks < 1) nblocks = 1;
+    if (prec == FFG_F64)
+        k_cp_partial<double><<<nblocks, kCpThreads, 0, stream>>>(
+            g->n_nodes, g->is_min, g->node_raw, fitness_raw, static_cast<const double *>(ranks), th,
+            w.partials);
+    else
+        k_cp_partial<float><<<nblocks, kCpThreads, 0, stream>>>(
+            g->n_nodes, g->is_min, g->node_raw, fitness_raw, static_cast<const float *>(ranks), th,
+            w.partials);
+    FFG_TRY(check_launch("k_cp_partial"));
+    k_cp_final<<<1, 64, 0, stream>>>(w.partials, nblocks, n_p, w.buckets);
+    count_launch(2);
+    FFG_TRY(check_launch("k_cp_final"));
+    double h[kBuckets];
+    FFG_TRY(check_cuda(cudaMemcpyAsync(h, w.buckets, sizeof(double) * (n_p + 1),
+                                       cudaMemcpyDeviceToHost, stream),
+                       "read buckets"));
+    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync centrality"));
+    const double sl = host_neumaier(h, n_p + 1);
+    if (!(sl > 0.0)) return set_error("minima hold no centrality"), FFG_ERR_EMPTY;
+    for (int k = 0; k < n_p; ++k) cp_out[order[k]] = host_neumaier(h, k + 1) / sl;
+    return FFG_OK;
+}

@@ -1,0 +1,114 @@
+"""The C-ABI library loads, exports every function include/ffg.h declares, and
+rejects bad arguments on the host (no GPU needed: argument errors are found
+before any CUDA call)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import ffg_inputs as fi
+import paper_2210_01465_gb300 as ffg
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "ffg.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ffg.build()
+    return ffg.load()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("defined",)))
+
+
+def test_header_declares_entry_points():
+    names = _declared_functions()
+    assert set(names) == set(ffg.ENTRY_POINTS), names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert ffg.ffg_status_str(s) not in ("", "unknown status")
+    assert ffg.ffg_status_str(99) == "unknown status"
+
+
+def test_space_validation_on_host(lib):
+    ok = ffg.Space.from_spec(fi.single_small())
+    assert ffg.ffg_workspace_bytes(ok, ffg.HAMMING) > 0
+    bad = [
+        ffg.Space([[1, 2]] * 17),                                  # too many parameters
+        ffg.Space([[1, 2], []]),                                   # empty list
+        ffg.Space([[1, 2]], [("prod_le", (3,), (), 4)]),           # mask beyond n_params
+        ffg.Space([list(range(2000))]),                            # too many values
+        ffg.Space([list(range(1, 50))] * 6),                       # more than 2^31-1 points
+        ffg.Space([[1 << 40, 2], [1 << 40, 3]], [("prod_le", (0, 1), (), 5)]),  # int64 overflow
+    ]
+    for sp in bad:
+        assert ffg.ffg_workspace_bytes(sp, ffg.HAMMING) == 0
+
+
+def test_argument_errors_before_cuda(lib):
+    sp = ffg.Space.from_spec(fi.single_small())
+    g = ffg.ffg_graph()
+    # NULL fitness / workspace
+    assert ffg.ffg_build_count(sp, 0, ffg.HAMMING, 1e10, g, 0, 0) == ffg.FFG_ERR_INVALID_ARG
+    # unknown neighbourhood
+    assert ffg.ffg_build_count(sp, 256, 7, 1e10, g, 256, 1 << 30) == ffg.FFG_ERR_INVALID_ARG
+    # misaligned workspace
+    assert ffg.ffg_build_count(sp, 256, 0, 1e10, g, 258, 1 << 30) == ffg.FFG_ERR_INVALID_ARG
+    # workspace too small
+    assert ffg.ffg_build_count(sp, 256, 0, 1e10, g, 256, 16) == ffg.FFG_ERR_NO_MEMORY
+    # overflow
+    big = ffg.Space([list(range(1, 50))] * 6)
+    assert ffg.ffg_build_count(big, 256, 0, 1e10, g, 256, 1 << 30) == ffg.FFG_ERR_OVERFLOW
+    # fill without a count
+    assert ffg.ffg_build_fill(sp, 256, 0, 1e10, g, 256, 1 << 30) == ffg.FFG_ERR_INVALID_ARG
+    # pagerank: empty graph, bad damping, bad precision
+    g.n_nodes, g.n_edges, g.in_ptr, g.in_idx, g.outdeg = 10, 5, 256, 256, 256
+    e = ffg.ffg_graph()
+    assert ffg.pagerank_solve(e, 0.85, 1e-9, 10, 0, 256, 0, 256, 1 << 20)[0] == 1
+    for damping in (0.0, 1.0, -0.5, float("nan")):
+        assert ffg.pagerank_solve(g, damping, 1e-9, 10, 0, 256, 0, 256, 1 << 20)[0] == 1
+    assert ffg.pagerank_solve(g, 0.85, 1e-9, 0, 0, 256, 0, 256, 1 << 20)[0] == 1
+    assert ffg.pagerank_solve(g, 0.85, 1e-9, 10, 5, 256, 0, 256, 1 << 20)[0] == 1
+    assert ffg.pagerank_solve(g, 0.85, 1e-9, 10, 0, 256, 0, 256, 8)[0] == ffg.FFG_ERR_NO_MEMORY
+    # centrality: n_p out of range, negative p
+    g.is_min, g.node_raw, g.n_minima = 256, 256, 1
+    out = np.zeros(40)
+    assert ffg.centrality_proportion(g, 256, 256, 0, [], out, 256, 1 << 20) == 1
+    assert ffg.centrality_proportion(g, 256, 256, 0, [0.1] * 33, out, 256, 1 << 20) == 1
+    assert ffg.centrality_proportion(g, 256, 256, 0, [-0.1], out, 256, 1 << 20) == 1
+    assert ffg.centrality_proportion(g, 256, 256, 0, [np.inf], out, 256, 1 << 20) == 1
+    g.n_minima = 0
+    assert ffg.centrality_proportion(g, 256, 256, 0, [0.1], out, 256, 1 << 20) == \
+        ffg.FFG_ERR_EMPTY
+    assert "workspace" in ffg.ffg_last_error() or ffg.ffg_last_error() != ""
+
+
+def test_workspace_sizes_monotone(lib):
+    small = ffg.Space.from_spec(fi.single_small())
+    large = ffg.Space.from_spec(fi.single_large())
+    assert ffg.ffg_workspace_bytes(large, 0) > ffg.ffg_workspace_bytes(small, 0)
+    assert ffg.pagerank_workspace_bytes(10**6, ffg.F64) > ffg.pagerank_workspace_bytes(10**6, ffg.F32)
+    assert ffg.centrality_workspace_bytes(5) > 0
+
+
+def test_product_path_has_no_oracle_import():
+    """The library package neither imports nor names the oracle."""
+    pkg = os.path.dirname(ffg.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(root, f)).read()
+                assert "import oracle" not in src and "ffg_oracle" not in src, f

@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Bars: FFG arrays and local-minimum sets bit-exact; FP64 ranks within L1 1e-9
+of the oracle's exact solve; FP32 proportions of centrality within 1e-5
+absolute (rank L1 error reported).  Sizes span several thread blocks and
+ragged tails; the single-space workloads run at full size.
+"""
+import numpy as np
+import pytest
+
+import ffg_inputs as fi
+import oracle
+
+torch = pytest.importorskip("torch")
+ffg = pytest.importorskip("paper_2210_01465_gb300")
+
+pytestmark = pytest.mark.gpu
+
+NBH = {"hamming": (ffg.HAMMING, oracle.HAMMING), "adjacent": (ffg.ADJACENT, oracle.ADJACENT)}
+F64_L1 = 1e-9      # FP64 rank L1 error bar
+F64_CP = 1e-9      # FP64 C_p: |dC_p| <= 2 ||dx||_1 / S_L, well inside this
+F32_CP = 1e-5      # FP32 C_p bar
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ffg.build()
+    ffg.load()
+
+
+def _np(t, n=None):
+    a = t.cpu().numpy()
+    return a if n is None else a[:n]
+
+
+def run_build(spec, f, nbh):
+    sp = ffg.Space.from_spec(spec)
+    fd = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+    return ffg.build_graph(sp, fd, NBH[nbh][0]), fd
+
+
+def assert_same_graph(g, og):
+    assert (g.n_raw, g.n_nodes, g.n_edges) == (og.n_raw, og.n_nodes, og.n_edges)
+    E = og.n_edges
+    np.testing.assert_array_equal(_np(g.node_raw), og.node_raw)
+    np.testing.assert_array_equal(_np(g.out_ptr), og.out_ptr)
+    np.testing.assert_array_equal(_np(g.in_ptr), og.in_ptr)
+    np.testing.assert_array_equal(_np(g.out_idx, E), og.out_idx)
+    np.testing.assert_array_equal(_np(g.in_idx, E), og.in_idx)
+    np.testing.assert_array_equal(_np(g.outdeg), og.outdeg)
+    np.testing.assert_array_equal(_np(g.is_min).astype(bool), og.is_min)
+    assert g.n_minima == int(og.is_min.sum())
+    assert g.f_opt == og.f_opt
+
+
+@pytest.mark.parametrize("nbh", ["hamming", "adjacent"])
+def test_tiny_spaces_bit_exact(nbh):
+    for k, spec in enumerate(fi.tiny_spaces(16, seed0=11000, max_raw=5000)):
+        f = fi.runtimes(spec, seed=k + 1, fail_frac=(0.03, 0.3, 0.7)[k % 3],
+                        quantum=0.25 if k % 4 == 0 else None)
+        og = oracle.build(spec, f, NBH[nbh][1])
+        g, _ = run_build(spec, f, nbh)
+        assert_same_graph(g, og)
+
+
+@pytest.mark.parametrize("nbh", ["hamming", "adjacent"])
+def test_paper_shaped_spaces(nbh):
+    for name, (make, _) in fi.PAPER_SPACES.items():
+        spec = make()
+        f = fi.runtimes(spec, seed=5, fail_frac=0.7 if name in ("convolution", "gemm") else 0.05)
+        og = oracle.build(spec, f, NBH[nbh][1])
+        g, fd = run_build(spec, f, nbh)
+        assert_same_graph(g, og)
+        x, it, res, conv = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64)
+        assert conv
+        xe = oracle.pagerank_exact(og, 0.85)
+        assert np.abs(_np(x) - xe).sum() <= F64_L1
+
+
+@pytest.mark.parametrize("nbh", ["hamming", "adjacent"])
+@pytest.mark.parametrize("alpha", [0.5, 0.85, 0.95])
+def test_single_small_full_path(nbh, alpha):
+    spec = fi.single_small()
+    p = [0.0, 0.01, 0.05, 0.1, 0.2]
+    for seed in (1, 2, 3):
+        f = fi.runtimes(spec, seed)
+        og = oracle.build(spec, f, NBH[nbh][1])
+        g, fd = run_build(spec, f, nbh)
+        assert_same_graph(g, og)
+        xe = oracle.pagerank_exact(og, alpha)
+        cpe = oracle.centrality(og, xe, p)
+        x64, it, res, conv = ffg.pagerank(g, alpha, 1e-12, prec=ffg.F64)
+        assert conv and res < 1e-12
+        assert np.abs(_np(x64) - xe).sum() <= F64_L1
+        assert np.abs(ffg.centrality(g, fd, x64, p) - cpe).max() <= F64_CP
+        x32, it32, res32, conv32 = ffg.pagerank(g, alpha, 1e-12, prec=ffg.F32)
+        assert conv32 and x32.dtype == torch.float32
+        assert np.abs(ffg.centrality(g, fd, x32, p) - cpe).max() <= F32_CP
+        assert np.abs(_np(x32).astype(np.float64) - xe).sum() < 1e-4
+
+
+@pytest.mark.parametrize("nbh", ["hamming", "adjacent"])
+def test_single_large_full_size(nbh):
+    """2,162,688 raw / 1,419,392 valid points at full size: bit-exact FFG,
+    FP64 and FP32 ranks and C_p against the oracle."""
+    spec = fi.single_large()
+    f = fi.runtimes(spec, 1)
+    p = [0.01, 0.05, 0.1]
+    og = oracle.build(spec, f, NBH[nbh][1])
+    g, fd = run_build(spec, f, nbh)
+    assert g.n_nodes == 1419392
+    assert_same_graph(g, og)
+    xe = oracle.pagerank_exact(og, 0.85)
+    cpe = oracle.centrality(og, xe, p)
+    x64, it, res, conv = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64)
+    assert conv
+    l1_64 = np.abs(_np(x64) - xe).sum()
+    assert l1_64 <= F64_L1
+    assert np.abs(ffg.centrality(g, fd, x64, p) - cpe).max() <= F64_CP
+    x32, it32, res32, conv32 = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F32)
+    l1_32 = np.abs(_np(x32).astype(np.float64) - xe).sum()
+    cp_err = np.abs(ffg.centrality(g, fd, x32, p) - cpe).max()
+    print(f"\n{nbh}: FP64 iters {it} L1 {l1_64:.3e}; FP32 iters {it32} L1 {l1_32:.3e} "
+          f"C_p err {cp_err:.3e}")
+    assert cp_err <= F32_CP
+
+
+def test_load_balance_groups():
+    """Spaces whose mean degree selects each lanes-per-row variant (2/4/8/16)."""
+    from ffg_inputs import SpaceSpec
+    cases = [
+        SpaceSpec("deg2", ("a", "b"), ((1, 2, 3), (1, 2, 3, 4))),                   # mean < 6
+        SpaceSpec("deg8", ("a", "b", "c"), (tuple(range(5)), tuple(range(6)), tuple(range(7)))),
+        SpaceSpec("deg21", ("a", "b", "c"), (tuple(range(31)), tuple(range(11)), (0, 1, 2, 3))),
+        SpaceSpec("deg54", ("a", "b"), (tuple(range(100)), tuple(range(10)))),
+    ]
+    for spec in cases:
+        f = fi.runtimes(spec, 9, fail_frac=0.0, noise_sd=0.3)
+        og = oracle.build(spec, f, oracle.HAMMING)
+        g, fd = run_build(spec, f, "hamming")
+        assert_same_graph(g, og)
+        xe = oracle.pagerank_exact(og, 0.85)
+        x, it, res, conv = ffg.pagerank(g, 0.85, 1e-13, prec=ffg.F64)
+        assert conv and np.abs(_np(x) - xe).sum() <= F64_L1, spec.name
+
+
+def test_chain_closed_form_on_gpu():
+    n, a = 40, 0.85
+    spec = fi.SpaceSpec("chain", ("p",), (tuple(range(n)),))
+    g, fd = run_build(spec, np.arange(n, 0, -1, dtype=np.float64), "adjacent")
+    y = np.array([(1 - a ** (k + 1)) / (1 - a) for k in range(n)])
+    x, it, res, conv = ffg.pagerank(g, a, 1e-14, prec=ffg.F64)
+    assert np.abs(_np(x) - y / y.sum()).max() < 1e-14
+    assert list(ffg.centrality(g, fd, x, [0.0, 1.0])) == [1.0, 1.0]
+
+
+def test_edge_cases():
+    from ffg_inputs import Clause, SpaceSpec
+    # no valid configuration
+    spec = SpaceSpec("none", ("a",), ((5, 6, 7),), (Clause("prod_le", (0,), (), 1),))
+    sp = ffg.Space.from_spec(spec)
+    with pytest.raises(ffg.FFGError) as e:
+        ffg.build_graph(sp, torch.ones(3, dtype=torch.float64, device="cuda"))
+    assert e.value.status == ffg.FFG_ERR_EMPTY
+    # one point: a single node without edges, rank 1, C_p 1
+    spec = SpaceSpec("one", ("a",), ((3,),))
+    g, fd = run_build(spec, np.array([2.0]), "hamming")
+    assert (g.n_nodes, g.n_edges, g.n_minima, g.f_opt) == (1, 0, 1, 2.0)
+    x, it, res, conv = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64)
+    assert _np(x)[0] == 1.0 and conv
+    assert ffg.centrality(g, fd, x, [0.0])[0] == 1.0
+    # everything failed (NaN and 1e10): no edges, no minimum, uniform ranks
+    spec = SpaceSpec("fail", ("a", "b"), ((1, 2, 3), (1, 2)))
+    f = np.array([1e10, np.nan, 1e10, 2e10, np.nan, 1e10])
+    og = oracle.build(spec, f, oracle.HAMMING)
+    g, fd = run_build(spec, f, "hamming")
+    assert_same_graph(g, og)
+    assert g.n_minima == 0 and g.f_opt == np.inf
+    x, it, res, conv = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64)
+    assert np.allclose(_np(x), 1.0 / 6, rtol=0, atol=1e-16)
+    with pytest.raises(ffg.FFGError) as e:
+        ffg.centrality(g, fd, x, [0.1])
+    assert e.value.status == ffg.FFG_ERR_EMPTY
+    # 16 parameters (the maximum), negative values, every clause kind
+    vals = tuple((-2, 1, 3) if i % 3 == 0 else (1, 2) for i in range(16))
+    spec = SpaceSpec("p16", tuple(f"p{i}" for i in range(16)), vals,
+                     (Clause("prod_le", (0, 3, 6), (), 4), Clause("prod_ge", (1, 2), (), 2),
+                      Clause("divides", (4, 5), (7,)), Clause("prod_le_prod", (9,), (12, 15))))
+    for nbh in ("hamming", "adjacent"):
+        f = fi.runtimes(spec, 3, fail_frac=0.1)
+        og = oracle.build(spec, f, NBH[nbh][1])
+        g, fd = run_build(spec, f, nbh)
+        assert_same_graph(g, og)
+    # products close to the int64 limit
+    spec = SpaceSpec("big", ("a", "b", "c"), ((1, 1 << 20, 1 << 31), (1, 3, 1 << 31), (0, 1)),
+                     (Clause("prod_le", (0, 1), (), 1 << 40), Clause("divides", (0,), (1,))))
+    f = fi.runtimes(spec, 2, fail_frac=0.0)
+    og = oracle.build(spec, f, oracle.HAMMING)
+    g, fd = run_build(spec, f, "hamming")
+    assert_same_graph(g, og)
+
+
+def test_not_converged_and_warm_start():
+    spec = fi.single_small()
+    f = fi.runtimes(spec, 4)
+    og = oracle.build(spec, f, oracle.HAMMING)
+    g, fd = run_build(spec, f, "hamming")
+    # three iterations only: status NOT_CONVERGED, ranks = three power steps
+    x, it, res, conv = ffg.pagerank(g, 0.85, 1e-12, max_iter=3, prec=ffg.F64)
+    assert not conv and it == 3
+    xo, ito, reso, convo = oracle.pagerank_power(og, 0.85, 1e-12, max_iter=3)
+    assert ito == 3 and abs(res - reso) < 1e-14
+    assert np.abs(_np(x) - xo / xo.sum()).sum() < 1e-14
+    # warm start from the exact solution: converges at once
+    xe = oracle.pagerank_exact(og, 0.85)
+    x, it, res, conv = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64,
+                                    init=torch.from_numpy(xe).cuda())
+    assert conv and it <= 2 and np.abs(_np(x) - xe).sum() <= F64_L1
+
+
+def test_deterministic():
+    spec = fi.single_large()
+    f = fi.runtimes(spec, 2)
+    g, fd = run_build(spec, f, "hamming")
+    a = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F32)[0].clone()
+    b = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F32)[0]
+    assert torch.equal(a, b)
+    g2, _ = run_build(spec, f, "hamming")
+    assert torch.equal(g.in_idx, g2.in_idx) and torch.equal(g.out_idx, g2.out_idx)
+
+
+def test_async_solve_and_query():
+    spec = fi.single_small()
+    f = fi.runtimes(spec, 6)
+    g, fd = run_build(spec, f, "hamming")
+    need = ffg.pagerank_workspace_bytes(g.n_nodes, ffg.F64)
+    ws = ffg.workspace(need)
+    x = torch.empty(g.n_nodes, dtype=torch.float64, device="cuda")
+    st, it, res = ffg.pagerank_solve(g.c, 0.85, 1e-12, 1000, ffg.F64, x.data_ptr(), 0,
+                                     ws.data_ptr(), need, sync=False,
+                                     stream=torch.cuda.current_stream().cuda_stream)
+    assert st == 0 and it is None
+    st, it, res = ffg.pagerank_query(ws.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert st == 0 and it > 10 and res < 1e-12
