@@ -231,7 +231,7 @@ def run_gpu(args):
     for n in nbhs:
         graphs[n] = ffg.build_graph(space, fd, n, ws=ws_b[n])
     N = graphs[ffg.HAMMING].n_nodes
-    pr_need = ffg.pagerank_workspace_bytes(N, ffg.F64)
+    pr_need = max(ffg.pagerank_workspace_bytes(N, graphs[n].n_edges, ffg.F64) for n in nbhs)
     pr_ws = {n: ffg.workspace(pr_need, dev) for n in nbhs}
     ranks32 = {n: torch.empty(N, dtype=torch.float32, device=dev) for n in nbhs}
     ranks64 = {n: torch.empty(N, dtype=torch.float64, device=dev) for n in nbhs}

@@ -162,7 +162,7 @@ ffg_status ffg_build_fill(const ffg_space *space, const double *fitness_raw, ffg
  * iters_out / residual_out (HOST) receive the iteration count and the last
  * residual; when both are NULL nothing is synchronised and the result is
  * read later with pagerank_query.  FFG_ERR_NOT_CONVERGED after max_iter. */
-size_t pagerank_workspace_bytes(int64_t n_nodes, ffg_prec prec);
+size_t pagerank_workspace_bytes(int64_t n_nodes, int64_t n_edges, ffg_prec prec);
 
 ffg_status pagerank_solve(const ffg_graph *g, double damping, double tol, int32_t max_iter,
                           ffg_prec prec, void *ranks, int init, void *workspace,

@@ -88,7 +88,7 @@ def load(path: str | None = None):
     lib.ffg_build_count.argtypes = [P(ffg_space), vp, C.c_int, f64, P(ffg_graph), P(i64), P(i64),
                                     vp, sz, vp]
     lib.ffg_build_fill.argtypes = [P(ffg_space), vp, C.c_int, f64, P(ffg_graph), vp, sz, vp]
-    lib.pagerank_workspace_bytes.argtypes = [i64, C.c_int]
+    lib.pagerank_workspace_bytes.argtypes = [i64, i64, C.c_int]
     lib.pagerank_workspace_bytes.restype = sz
     lib.pagerank_solve.argtypes = [P(ffg_graph), f64, f64, i32, C.c_int, vp, C.c_int, vp, sz,
                                    P(i32), P(f64), vp]
@@ -139,8 +139,8 @@ def ffg_build_fill(space, fitness_raw: int, nbh: int, fail_thr: float, g: ffg_gr
                                      C.c_void_p(stream)))
 
 
-def pagerank_workspace_bytes(n_nodes: int, prec: int) -> int:
-    return int(load().pagerank_workspace_bytes(int(n_nodes), int(prec)))
+def pagerank_workspace_bytes(n_nodes: int, n_edges: int, prec: int) -> int:
+    return int(load().pagerank_workspace_bytes(int(n_nodes), int(n_edges), int(prec)))
 
 
 def pagerank_solve(g: ffg_graph, damping: float, tol: float, max_iter: int, prec: int,
@@ -292,7 +292,7 @@ def pagerank(g: Graph, damping: float = 0.85, tol: float = 1e-12, max_iter: int 
     ranks = out if out is not None else torch.empty(g.n_nodes, dtype=dt, device=dev)
     if init is not None:
         ranks.copy_(init)
-    need = pagerank_workspace_bytes(g.n_nodes, prec)
+    need = pagerank_workspace_bytes(g.n_nodes, g.n_edges, prec)
     if ws is None or ws.numel() < need:
         ws = workspace(need, dev)
     st, it, res = pagerank_solve(g.c, damping, tol, max_iter, prec, ranks.data_ptr(),

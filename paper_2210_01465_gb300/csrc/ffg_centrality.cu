@@ -84,16 +84,32 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_partial(
     }
 }
 
+// one warp per bucket: lanes add strided blocks with Neumaier's sum, then the
+// 32 (sum, compensation) pairs are combined by lane 0 in lane order
 __global__ void k_cp_final(const double *__restrict__ partials, int nblocks, int nb,
                            double *__restrict__ buckets) {
-    const int b = threadIdx.x;
-    if (b > nb) return;
-    double s = 0.0, c = 0.0;
-    for (int k = 0; k < nblocks; ++k) {
-        neumaier(s, c, partials[(size_t(k) * kBuckets + b) * 2 + 0]);
-        neumaier(s, c, partials[(size_t(k) * kBuckets + b) * 2 + 1]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    __shared__ double red[32][32][2];
+    for (int b = warp; b <= nb; b += nwarps) {
+        double s = 0.0, c = 0.0;
+        for (int k = lane; k < nblocks; k += 32) {
+            neumaier(s, c, partials[(size_t(k) * kBuckets + b) * 2 + 0]);
+            neumaier(s, c, partials[(size_t(k) * kBuckets + b) * 2 + 1]);
+        }
+        red[warp][lane][0] = s;
+        red[warp][lane][1] = c;
+        __syncwarp();
+        if (lane == 0) {
+            double ts = 0.0, tc = 0.0;
+            for (int k = 0; k < 32; ++k) {
+                neumaier(ts, tc, red[warp][k][0]);
+                neumaier(ts, tc, red[warp][k][1]);
+            }
+            buckets[b] = ts + tc;
+        }
+        __syncwarp();
     }
-    buckets[b] = s + c;
 }
 
 double host_neumaier(const double *v, int n) {
@@ -170,7 +186,7 @@ extern "C" ffg_status centrality_proportion(const ffg_graph *g, const double *fi
             g->n_nodes, g->is_min, g->node_raw, fitness_raw, static_cast<const float *>(ranks), th,
             w.partials);
     FFG_TRY(check_launch("k_cp_partial"));
-    k_cp_final<<<1, 64, 0, stream>>>(w.partials, nblocks, n_p, w.buckets);
+    k_cp_final<<<1, 32 * std::min(n_p + 1, 32), 0, stream>>>(w.partials, nblocks, n_p, w.buckets);
     count_launch(2);
     FFG_TRY(check_launch("k_cp_final"));
     double h[kBuckets];

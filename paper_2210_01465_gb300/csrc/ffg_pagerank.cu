@@ -7,19 +7,41 @@
 //   x'[v] = alpha * sum_{u in in(v)} w[u] + (alpha * D + 1 - alpha) / N,
 //   w[u]  = x[u] / outdeg[u],   D = sum_{outdeg(u) = 0} x[u].
 //
-// One cooperative persistent launch runs every iteration.  Each block owns a
-// contiguous range of rows, balanced by in-edges plus a per-row cost; rows
-// are processed by groups of G lanes that stream the row's in_idx segment
-// (4 loads in flight per lane) and gather w.  Only w is kept between
-// iterations (ping-pong): x[v] = w[v] * outdeg[v] (or w[v] for a node
-// without out-edges), so an iteration moves in_idx (4 B/edge), in_ptr and
-// outdeg (12 B/row), the own w (read) and the new w (write).  Residual
-// sum |x'-x|, next D and sum x' are reduced in FP64 per block, written to a
-// double-buffered partials array, and after a grid barrier every block sums
-// the partials in the same fixed order, so all blocks take the same
-// stopping decision and the result is deterministic for a given grid.
-// Barrier waits are bounded (globaltimer); on expiry the kernel records
-// FFG_ERR_TIMEOUT and returns.
+// Two launches per solve.
+//
+// k_pr_layout builds, in the workspace, a gather-friendly copy of the
+// in-edges.  Rows are grouped in tiles of 32 consecutive nodes; a tile's
+// in-edges are ordered by (src - dst, dst), i.e. grouped by neighbourhood
+// offset.  For an FFG a tile has few distinct offsets (about one per stencil
+// slot of the Hamming or adjacent neighbourhood) and each group holds
+// consecutive sources, so 32 consecutive entries (a chunk, one per lane)
+// gather few 32-byte sectors.  No sort is needed: each row's list is already
+// ascending, so a warp merge over the distinct offsets emits the groups in
+// order.  Each entry carries the shared-memory offset of its accumulator:
+// slot = number of earlier entries of the same chunk with the same row, and
+// the accumulator of (slot, row) lives at (slot << 5) | (row ^ slot) (the
+// XOR spreads one row's slots over distinct banks).  Within a chunk no two
+// lanes share an accumulator and the summation order is fixed.  Entry =
+// (src << 8) | offset; padding entries gather node 0 into a dummy slot.
+// Tile t's chunks start at chunk floor(in_ptr[32t] / 32) + t.  Tiles that do
+// not fit (more than kSortCap edges, a row with more than kMaxSlots entries
+// in one chunk, or 2^24 nodes and more) keep the plain CSR path.
+//
+// k_pagerank is one cooperative persistent launch for every iteration.
+// Each warp owns a contiguous range of tiles of about equal cost; lane t
+// owns row 32*tile + t, so per-row loads and stores are coalesced.  One
+// lane streams the tile's chunks into a double-buffered shared-memory stage
+// with TMA bulk copies (cp.async.bulk, completion on an mbarrier), one
+// segment ahead, while the warp gathers w for the current segment and adds
+// into its accumulators.  Only w is kept between iterations (ping-pong):
+// x[v] = w[v] * outdeg[v] (or w[v] for a node without out-edges).  Residual
+// sum |x'-x|, next D and sum x' are accumulated per thread
+// (Kahan-compensated FP32 in the FP32 path, FP64 otherwise), reduced in FP64
+// per block into a double-buffered partials array, and after a grid barrier
+// every block sums the partials in the same fixed order, so all blocks take
+// the same stopping decision and results are deterministic for a given grid.
+// Every wait (grid barrier, mbarrier) is bounded; on expiry the kernel
+// records FFG_ERR_TIMEOUT, lets its own copies land, and returns.
 #include "ffg_internal.cuh"
 
 namespace ffg {
@@ -27,9 +49,19 @@ namespace ffg {
 namespace {
 
 constexpr int kPrThreads = 256;
+constexpr int kWarps = kPrThreads / 32;
 constexpr int kMaxBlocks = 4096;
-constexpr int64_t kRowCost = 4;            // row cost in units of one in-edge
 constexpr uint64_t kTimeoutNs = 2000000000ULL;
+constexpr int kSortCap = 2048;          // in-edges per tile staged by the layout kernel
+constexpr int kMaxSlots = 7;            // entries of one row within one chunk
+constexpr uint32_t kDummyOff = (7u << 5) | 7u;  // accumulator of padding entries
+constexpr uint32_t kPadEntry = kDummyOff;       // source 0, dummy accumulator
+constexpr int kAccElems = 8 * 32;       // accumulators per warp (7 slots + dummy)
+constexpr int kSeg = 16;                // chunks per TMA segment
+constexpr int kGroup = 8;               // gathers in flight per lane
+constexpr int64_t kMaxPackedNodes = int64_t(1) << 24;
+constexpr int kLayoutThreads = 64;
+constexpr int64_t kRowCost = 8;         // per-row cost in in-edge units (warp split)
 
 struct PrCtl {
     unsigned int barrier;
@@ -45,20 +77,29 @@ struct PrWs {
     PrCtl *ctl;
     double *partials;  // [2][kMaxBlocks][4]
     void *w0, *w1;
+    uint32_t *layout;  // packed chunks
+    uint8_t *meta;     // per tile: accumulator slots used (1..kMaxSlots), 0 = CSR path
     size_t bytes;
 };
 
-PrWs carve(void *base, int64_t n, size_t elem) {
+inline int64_t layout_chunks(int64_t n, int64_t e) { return e / 32 + (n + 31) / 32 + 1; }
+
+PrWs carve(void *base, int64_t n, int64_t e, size_t elem) {
     Carver c(base);
     PrWs w;
     w.ctl = c.take<PrCtl>(1);
     w.partials = c.take<double>(size_t(2) * kMaxBlocks * 4);
     w.w0 = c.take<char>(size_t(n) * elem);
     w.w1 = c.take<char>(size_t(n) * elem);
+    w.layout = c.take<uint32_t>(size_t(layout_chunks(n, e)) * 32);
+    w.meta = c.take<uint8_t>(size_t((n + 31) / 32));
     w.bytes = c.off;
     return w;
 }
 
+// ---------------------------------------------------------------------------
+// synchronisation primitives (all waits bounded)
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -71,6 +112,50 @@ __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// one lane: expect `bytes` on `bar` and start the bulk copy global -> shared
+__device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "{\n .reg .b64 state;\n mbarrier.arrive.expect_tx.shared::cta.b64 state, [%0], %1;\n}" ::
+            "r"(smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the completion of phase `parity`; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t polls = 0;; ++polls) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (polls > (1u << 22) || global_ns() - t0 > kTimeoutNs) return false;
+    }
 }
 
 // Grid-wide barrier over a cooperative launch.  Bounded: gives up after
@@ -103,6 +188,9 @@ __device__ bool grid_barrier(PrCtl *ctl, unsigned target) {
     return s_ok != 0;
 }
 
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -111,7 +199,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // block sums of three doubles; valid in thread 0
 __device__ __forceinline__ void block_sum3(double &a, double &b, double &c) {
-    __shared__ double red[3][kPrThreads / 32];
+    __shared__ double red[3][kWarps];
     a = warp_sum(a);
     b = warp_sum(b);
     c = warp_sum(c);
@@ -125,7 +213,7 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c) {
     __syncthreads();
     if (threadIdx.x == 0) {
         a = b = c = 0.0;
-        for (int k = 0; k < kPrThreads / 32; ++k) {
+        for (int k = 0; k < kWarps; ++k) {
             a += red[0][k];
             b += red[1][k];
             c += red[2][k];
@@ -133,8 +221,12 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c) {
     }
 }
 
+struct Tot {
+    double r, d, s;
+};
+
 // every block sums the partials of all blocks in the same order (warp 0)
-__device__ __forceinline__ void sum_partials(const double *part, int nb, double out[3]) {
+__device__ __forceinline__ Tot sum_partials(const double *part, int nb) {
     __shared__ double s_out[3];
     if (threadIdx.x < 32) {
         double a = 0, b = 0, c = 0;
@@ -153,131 +245,431 @@ __device__ __forceinline__ void sum_partials(const double *part, int nb, double 
         }
     }
     __syncthreads();
-    out[0] = s_out[0];
-    out[1] = s_out[1];
-    out[2] = s_out[2];
+    Tot t{s_out[0], s_out[1], s_out[2]};
     __syncthreads();
+    return t;
 }
 
-__device__ __forceinline__ int64_t row_split(const int64_t *in_ptr, int64_t n, int b, int nb) {
-    if (b <= 0) return 0;
-    if (b >= nb) return n;
+// per-thread accumulation of the residual / dangling mass / sum: FP32 values
+// are added with Kahan compensation (no FP64 instruction per row); FP64
+// values are added in FP64.  The block reduction is FP64 in both cases.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const {
+        return static_cast<double>(s) - static_cast<double>(c);
+    }
+};
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// ---------------------------------------------------------------------------
+// gather-friendly layout of the in-edges (built once per solve)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kLayoutThreads) k_pr_layout(
+    const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx, int64_t n,
+    uint32_t *__restrict__ layout, uint8_t *__restrict__ meta) {
+    __shared__ int32_t s_src[kLayoutThreads / 32][kSortCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *src = s_src[warp];
+    const int64_t ntiles = (n + 31) >> 5;
+    const int64_t step = int64_t(gridDim.x) * (kLayoutThreads / 32);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int64_t t = int64_t(blockIdx.x) * (kLayoutThreads / 32) + warp; t < ntiles; t += step) {
+        const int64_t r0 = t << 5;
+        const int64_t rend = r0 + 32 < n ? r0 + 32 : n;
+        const int64_t ip0 = in_ptr[r0], ip1 = in_ptr[rend];
+        const int64_t et = ip1 - ip0;
+        if (et > kSortCap || n >= kMaxPackedNodes) {
+            if (lane == 0) meta[t] = 0;
+            continue;
+        }
+        for (int64_t k = lane; k < et; k += 32) src[k] = in_idx[ip0 + k];
+        const int64_t v = r0 + lane;
+        int cur = 0, end = 0;
+        if (v < rend) {
+            cur = static_cast<int>(in_ptr[v] - ip0);
+            end = static_cast<int>(in_ptr[v + 1] - ip0);
+        }
+        __syncwarp();
+        const int64_t base = ((ip0 >> 5) + t) * 32;  // first entry of the tile
+        int pos = 0, last_chunk = -1, count = 0, maxslot = 0;
+        // merge the 32 ascending lists by offset src - dst; one group per offset
+        while (true) {
+            const int32_t head = cur < end ? src[cur] - static_cast<int32_t>(v) : INT32_MAX;
+            int32_t m = head;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int32_t y = __shfl_xor_sync(0xffffffffu, m, o);
+                m = y < m ? y : m;
+            }
+            if (m == INT32_MAX) break;
+            const bool hit = head == m;
+            const unsigned mask = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int p = pos + __popc(mask & lt_mask);
+                const int chunk = p >> 5;
+                if (chunk != last_chunk) {
+                    last_chunk = chunk;
+                    count = 0;
+                }
+                const int slot = count++;
+                if (slot > maxslot) maxslot = slot;
+                const uint32_t sl = static_cast<uint32_t>(slot < kMaxSlots ? slot : 0);
+                layout[base + p] = (static_cast<uint32_t>(src[cur]) << 8) | (sl << 5) |
+                                   (static_cast<uint32_t>(lane) ^ sl);
+                ++cur;
+            }
+            pos += __popc(mask);
+        }
+        const int padded = (pos + 31) & ~31;
+        if (pos + lane < padded) layout[base + pos + lane] = kPadEntry;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int y = __shfl_xor_sync(0xffffffffu, maxslot, o);
+            maxslot = y > maxslot ? y : maxslot;
+        }
+        if (lane == 0) meta[t] = maxslot < kMaxSlots ? static_cast<uint8_t>(maxslot + 1) : 0;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-iteration tile work
+// ---------------------------------------------------------------------------
+template <typename T>
+struct TileInfo {
+    int64_t t, e0, e1;  // tile index, in-edge range
+    int nslots;         // accumulator slots (0 = CSR path)
+    int32_t od;         // out-degree of this lane's row
+    T wv;               // w of this lane's row
+    __device__ __forceinline__ int nch() const { return static_cast<int>((e1 - e0 + 31) >> 5); }
+    __device__ __forceinline__ int64_t chunk0() const { return (e0 >> 5) + t; }
+};
+
+template <typename T>
+__device__ __forceinline__ TileInfo<T> load_info(int64_t t, int64_t n,
+                                                 const int64_t *__restrict__ in_ptr,
+                                                 const uint8_t *__restrict__ meta,
+                                                 const int32_t *__restrict__ outdeg, const T *wc,
+                                                 int lane) {
+    TileInfo<T> ti;
+    const int64_t r0 = t << 5;
+    const int64_t rend = r0 + 32 < n ? r0 + 32 : n;
+    const int64_t v = r0 + lane;
+    ti.t = t;
+    ti.e0 = __ldg(in_ptr + r0);
+    ti.e1 = __ldg(in_ptr + rend);
+    ti.nslots = __ldg(meta + t);
+    ti.od = v < rend ? __ldg(outdeg + v) : 0;
+    ti.wv = v < rend ? wc[v] : T(0);
+    return ti;
+}
+
+// Per-warp TMA stream of packed chunk segments into a two-buffer stage.
+// `pending` has bit b set while a copy into buffer b is outstanding.
+struct Stream {
+    uint32_t *stage;   // [2][kSeg * 32]
+    uint64_t *bar;     // [2]
+    uint32_t phase;    // bit b = parity of the next completion on buffer b
+    uint32_t pending;  // bit b = a copy into buffer b is outstanding
+    int buf;           // buffer of the segment to process next
+    bool issued;       // the segment for `buf` has been issued
+    __device__ __forceinline__ void issue(const uint32_t *layout, int64_t chunk, int cnt, int b,
+                                          int lane) {
+        if (lane == 0) {
+            fence_proxy_async();
+            tma_load(stage + b * (kSeg * 32), layout + chunk * 32, static_cast<uint32_t>(cnt) * 128u,
+                     bar + b);
+        }
+        pending |= 1u << b;
+    }
+    // bounded wait on buffer b, uniform over the warp; false on timeout
+    __device__ __forceinline__ bool wait(int b) {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(bar + b, (phase >> b) & 1u));
+        if (ok) {
+            phase ^= 1u << b;
+            pending &= ~(1u << b);
+        }
+        return ok;
+    }
+    // after a failure: let every outstanding copy of this warp land (bounded)
+    __device__ __forceinline__ void drain() {
+        for (int b = 0; b < 2; ++b)
+            if (pending & (1u << b)) wait(b);
+    }
+};
+
+// Sum over the rows of a packed tile (lane = row), streaming its chunks in
+// segments of kSeg; the segment after the current one (or the first segment
+// of the next tile) is copied while the current one is gathered.
+template <typename T>
+__device__ __forceinline__ bool tile_sum_packed(const uint32_t *__restrict__ layout,
+                                                const TileInfo<T> &cur, const TileInfo<T> &nxt,
+                                                bool has_next, Stream &st, const T *wc, T *acc,
+                                                int lane, T &sum) {
+    const int nch = cur.nch();
+    for (int k = 0; k < cur.nslots; ++k) acc[(k << 5) | (lane ^ k)] = T(0);
+    __syncwarp();
+    const int nseg = (nch + kSeg - 1) / kSeg;
+    const bool next_packed = has_next && nxt.nslots > 0 && nxt.nch() > 0;
+    for (int s = 0; s < nseg; ++s) {
+        const int c0 = s * kSeg;
+        const int cnt = nch - c0 < kSeg ? nch - c0 : kSeg;
+        if (!st.issued) st.issue(layout, cur.chunk0() + c0, cnt, st.buf, lane);
+        // prefetch the following segment into the other buffer
+        if (s + 1 < nseg) {
+            const int c1 = c0 + kSeg;
+            st.issue(layout, cur.chunk0() + c1, nch - c1 < kSeg ? nch - c1 : kSeg, st.buf ^ 1,
+                     lane);
+            st.issued = true;
+        } else if (next_packed) {
+            const int n1 = nxt.nch();
+            st.issue(layout, nxt.chunk0(), n1 < kSeg ? n1 : kSeg, st.buf ^ 1, lane);
+            st.issued = true;
+        } else {
+            st.issued = false;
+        }
+        if (!st.wait(st.buf)) return false;
+        const uint32_t *ent = st.stage + st.buf * (kSeg * 32) + lane;
+        for (int g0 = 0; g0 < cnt; g0 += kGroup) {
+            uint32_t e[kGroup];
+            T val[kGroup];
+#pragma unroll
+            for (int g = 0; g < kGroup; ++g) e[g] = g0 + g < cnt ? ent[(g0 + g) * 32] : kPadEntry;
+#pragma unroll
+            for (int g = 0; g < kGroup; ++g) val[g] = wc[e[g] >> 8];
+#pragma unroll
+            for (int g = 0; g < kGroup; ++g) {
+                acc[e[g] & 0xffu] += val[g];
+                __syncwarp();
+            }
+        }
+        st.buf ^= 1;
+    }
+    if (nseg == 0 && !st.issued && next_packed) {
+        const int n1 = nxt.nch();
+        st.issue(layout, nxt.chunk0(), n1 < kSeg ? n1 : kSeg, st.buf, lane);
+        st.issued = true;
+    }
+    T s = T(0);
+    for (int k = 0; k < cur.nslots; ++k) s += acc[(k << 5) | (lane ^ k)];
+    __syncwarp();
+    sum = s;
+    return true;
+}
+
+// CSR path of one tile: the tile's in-edges [e0, e1) are streamed in windows
+// with coalesced in_idx loads, gathered into shared memory, and each lane
+// adds the part of its own row [p, p_next) that lies in the window.
+template <typename T>
+__device__ __forceinline__ T tile_sum_csr(const int32_t *__restrict__ in_idx, const T *wc,
+                                          T *buf, int64_t p, int64_t p_next, int64_t e0,
+                                          int64_t e1, int lane) {
+    T s = T(0);
+    for (int64_t ws = e0; ws < e1; ws += kAccElems) {
+        const int n = static_cast<int>(e1 - ws < kAccElems ? e1 - ws : kAccElems);
+        const int32_t *src = in_idx + ws;
+        int i = lane;
+        for (; i + 96 < n; i += 128) {
+            const int32_t j0 = __ldg(src + i), j1 = __ldg(src + i + 32);
+            const int32_t j2 = __ldg(src + i + 64), j3 = __ldg(src + i + 96);
+            const T a0 = wc[j0], a1 = wc[j1], a2 = wc[j2], a3 = wc[j3];
+            buf[i] = a0;
+            buf[i + 32] = a1;
+            buf[i + 64] = a2;
+            buf[i + 96] = a3;
+        }
+        for (; i < n; i += 32) buf[i] = wc[__ldg(src + i)];
+        __syncwarp();
+        const int64_t a = p > ws ? p : ws;
+        const int64_t b = p_next < ws + n ? p_next : ws + n;
+        for (int64_t e = a; e < b; ++e) s += buf[e - ws];
+        __syncwarp();
+    }
+    return s;
+}
+
+// First tile of warp w when the tiles are split into nw contiguous ranges of
+// about equal cost (in-edges plus kRowCost per row).
+__device__ __forceinline__ int64_t tile_split(const int64_t *__restrict__ in_ptr, int64_t n,
+                                              int64_t ntiles, int64_t w, int64_t nw) {
+    if (w <= 0) return 0;
+    if (w >= nw) return ntiles;
     const int64_t total = __ldg(in_ptr + n) + kRowCost * n;
-    const int64_t target = total / nb * b + (total % nb) * b / nb;  // floor(total*b/nb)
-    int64_t lo = 0, hi = n;  // smallest v with cost(v) >= target
+    const int64_t target = total / nw * w + (total % nw) * w / nw;
+    int64_t lo = 0, hi = ntiles;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if (__ldg(in_ptr + mid) + kRowCost * mid >= target) hi = mid;
+        const int64_t r = mid << 5 < n ? mid << 5 : n;
+        if (__ldg(in_ptr + r) + kRowCost * r >= target) hi = mid;
         else lo = mid + 1;
     }
     return lo;
 }
 
-template <typename T, int G>
-__global__ void __launch_bounds__(kPrThreads) k_pagerank(
+template <typename T>
+constexpr size_t pr_smem_bytes() {
+    return size_t(kWarps) * (2 * kSeg * 32 * sizeof(uint32_t) + kAccElems * sizeof(T) + 16);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPrThreads, 3) k_pagerank(
     const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx,
-    const int32_t *__restrict__ outdeg, int64_t n, double alpha, double tol, int max_iter,
+    const int32_t *__restrict__ outdeg, const uint32_t *__restrict__ layout,
+    const uint8_t *__restrict__ meta, int64_t n, double alpha, double tol, int max_iter,
     int init, T *ranks, T *w0, T *w1, double *partials, PrCtl *ctl) {
+    extern __shared__ __align__(128) unsigned char s_dyn[];
     const int nb = gridDim.x;
-    __shared__ int64_t s_range[2];
-    if (threadIdx.x == 0) {
-        s_range[0] = row_split(in_ptr, n, blockIdx.x, nb);
-        s_range[1] = row_split(in_ptr, n, blockIdx.x + 1, nb);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // shared memory: per-warp stages, then accumulators, then mbarriers
+    Stream st;
+    st.stage = reinterpret_cast<uint32_t *>(s_dyn) + size_t(warp) * 2 * kSeg * 32;
+    T *acc = reinterpret_cast<T *>(s_dyn + size_t(kWarps) * 2 * kSeg * 32 * sizeof(uint32_t)) +
+             size_t(warp) * kAccElems;
+    st.bar = reinterpret_cast<uint64_t *>(s_dyn + size_t(kWarps) * 2 * kSeg * 32 * sizeof(uint32_t) +
+                                          size_t(kWarps) * kAccElems * sizeof(T)) +
+             2 * warp;
+    st.phase = 0;
+    st.pending = 0;
+    st.buf = 0;
+    st.issued = false;
+    if (lane == 0) {
+        mbar_init(st.bar);
+        mbar_init(st.bar + 1);
+        fence_mbar_init();
     }
-    __syncthreads();
-    const int64_t lo = s_range[0], hi = s_range[1];
-    const int sub = threadIdx.x & (G - 1);
-    const int group = threadIdx.x / G;
-    constexpr int kGroups = kPrThreads / G;
+    __syncwarp();
+
+    const int64_t gwarp = int64_t(blockIdx.x) * kWarps + warp;
+    const int64_t nwarps = int64_t(nb) * kWarps;
+    const int64_t ntiles = (n + 31) >> 5;
+    int64_t ta = 0, tb = 0;
+    if (lane == 0) {
+        ta = tile_split(in_ptr, n, ntiles, gwarp, nwarps);
+        tb = tile_split(in_ptr, n, ntiles, gwarp + 1, nwarps);
+    }
+    ta = __shfl_sync(0xffffffffu, ta, 0);
+    tb = __shfl_sync(0xffffffffu, tb, 0);
     const double inv_n = 1.0 / static_cast<double>(n);
 
-    // prologue: w from the start vector, D_0 and sum x_0
+    // prologue: w from the start vector, D_0 and sum x_0 (grid-stride)
     {
-        double dsum = 0.0, xsum = 0.0, unused = 0.0;
-        for (int64_t v = lo + threadIdx.x; v < hi; v += kPrThreads) {
+        Acc<double> dsum, xsum;
+        const int64_t stride = int64_t(nb) * kPrThreads;
+        for (int64_t v = int64_t(blockIdx.x) * kPrThreads + threadIdx.x; v < n; v += stride) {
             const double x0 = init ? static_cast<double>(ranks[v]) : inv_n;
             const int32_t od = __ldg(outdeg + v);
             w0[v] = static_cast<T>(od ? x0 / od : x0);
-            if (od == 0) dsum += x0;
-            xsum += x0;
+            if (od == 0) dsum.add(x0);
+            xsum.add(x0);
         }
-        block_sum3(unused, dsum, xsum);
+        double unused = 0.0, d = dsum.value(), x = xsum.value();
+        block_sum3(unused, d, x);
         if (threadIdx.x == 0) {
             double *p = partials + 4 * blockIdx.x;
             p[0] = 0.0;
-            p[1] = dsum;
-            p[2] = xsum;
+            p[1] = d;
+            p[2] = x;
         }
     }
     unsigned phase = 1;
     if (!grid_barrier(ctl, phase * nb)) return;
-    double tot[3];
-    sum_partials(partials, nb, tot);
-    double dang = tot[1], xs = tot[2];
+    Tot tot = sum_partials(partials, nb);
+    double dang = tot.d, xs = tot.s;
     double res = __longlong_as_double(0x7ff0000000000000LL), prev_res = res;
     int it = 0, converged = 0;
     T *wc = w0, *wn = w1;
     int par = 0;
+    const T a = static_cast<T>(alpha);
+    int failed = 0;
     while (true) {
         const T c = static_cast<T>((alpha * dang + 1.0 - alpha) * inv_n);
-        const T a = static_cast<T>(alpha);
-        double r_acc = 0.0, d_acc = 0.0, s_acc = 0.0;
-        for (int64_t base = lo; base < hi; base += kGroups) {
-            const int64_t v = base + group;
-            const bool active = v < hi;
-            int64_t e = 0, end = 0;
-            if (active) {
-                e = __ldg(in_ptr + v) + sub;
-                end = __ldg(in_ptr + v + 1);
-            }
-            T s = T(0);
-            for (; e + 3 * G < end; e += 4 * G) {
-                const int32_t i0 = __ldg(in_idx + e), i1 = __ldg(in_idx + e + G);
-                const int32_t i2 = __ldg(in_idx + e + 2 * G), i3 = __ldg(in_idx + e + 3 * G);
-                const T a0 = wc[i0], a1 = wc[i1], a2 = wc[i2], a3 = wc[i3];
-                s += (a0 + a1) + (a2 + a3);
-            }
-            for (; e < end; e += G) s += wc[__ldg(in_idx + e)];
-#pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (active && sub == 0) {
-                const int32_t od = __ldg(outdeg + v);
-                const T wv = wc[v];
-                const T xo = od ? wv * static_cast<T>(od) : wv;
-                const T xn = a * s + c;
-                r_acc += fabs(static_cast<double>(xn) - static_cast<double>(xo));
-                if (od == 0) d_acc += static_cast<double>(xn);
-                s_acc += static_cast<double>(xn);
-                wn[v] = od ? xn / static_cast<T>(od) : xn;
+        Acc<T> r_acc, d_acc, s_acc;
+        if (ta < tb && !failed) {
+            TileInfo<T> cur = load_info<T>(ta, n, in_ptr, meta, outdeg, wc, lane);
+            for (int64_t t = ta; t < tb; ++t) {
+                const bool has_next = t + 1 < tb;
+                TileInfo<T> nxt = cur;
+                if (has_next) nxt = load_info<T>(t + 1, n, in_ptr, meta, outdeg, wc, lane);
+                const int64_t v = (t << 5) + lane;
+                const bool row_ok = v < n;
+                T s = T(0);
+                if (cur.nslots > 0) {
+                    if (!tile_sum_packed<T>(layout, cur, nxt, has_next, st, wc, acc, lane, s)) {
+                        failed = 1;
+                        break;
+                    }
+                } else {
+                    const int64_t p = row_ok ? __ldg(in_ptr + v) : cur.e1;
+                    int64_t p_next = __shfl_down_sync(0xffffffffu, p, 1);
+                    if (lane == 31 || v + 1 >= n) p_next = cur.e1;
+                    // the next packed tile's first segment streams in meanwhile
+                    if (!st.issued && has_next && nxt.nslots > 0 && nxt.nch() > 0) {
+                        const int n1 = nxt.nch();
+                        st.issue(layout, nxt.chunk0(), n1 < kSeg ? n1 : kSeg, st.buf, lane);
+                        st.issued = true;
+                    }
+                    s = tile_sum_csr<T>(in_idx, wc, acc, p, p_next, cur.e0, cur.e1, lane);
+                }
+                if (row_ok) {
+                    const T xo = cur.od ? cur.wv * static_cast<T>(cur.od) : cur.wv;
+                    const T xn = a * s + c;
+                    r_acc.add(xn > xo ? xn - xo : xo - xn);
+                    if (cur.od == 0) d_acc.add(xn);
+                    s_acc.add(xn);
+                    wn[v] = cur.od ? xn / static_cast<T>(cur.od) : xn;
+                }
+                cur = nxt;
             }
         }
-        block_sum3(r_acc, d_acc, s_acc);
+        if (failed == 1) {
+            // let this warp's own copies land (bounded), then report
+            st.drain();
+            if (lane == 0) atomicCAS(&ctl->status, 0, (int)FFG_ERR_TIMEOUT);
+            failed = 2;
+        }
+        double r_b = r_acc.value(), d_b = d_acc.value(), s_b = s_acc.value();
+        block_sum3(r_b, d_b, s_b);
         par ^= 1;
         double *pp = partials + size_t(par) * kMaxBlocks * 4;
         if (threadIdx.x == 0) {
             double *p = pp + 4 * blockIdx.x;
-            p[0] = r_acc;
-            p[1] = d_acc;
-            p[2] = s_acc;
+            p[0] = r_b;
+            p[1] = d_b;
+            p[2] = s_b;
         }
         ++phase;
         if (!grid_barrier(ctl, phase * nb)) return;
-        sum_partials(pp, nb, tot);
+        tot = sum_partials(pp, nb);
         prev_res = res;
-        res = tot[0];
-        dang = tot[1];
-        xs = tot[2];
+        res = tot.r;
+        dang = tot.d;
+        xs = tot.s;
         ++it;
-        T *t = wc;
+        T *tmp = wc;
         wc = wn;
-        wn = t;
+        wn = tmp;
         if (res < tol) { converged = 1; break; }
         if (sizeof(T) == 4 && res >= prev_res) { converged = 1; break; }  // FP32 rounding floor
         if (it >= max_iter) break;
     }
     // epilogue: x' normalised to sum 1
     const double inv_s = 1.0 / xs;
-    for (int64_t v = lo + threadIdx.x; v < hi; v += kPrThreads) {
+    const int64_t stride = int64_t(nb) * kPrThreads;
+    for (int64_t v = int64_t(blockIdx.x) * kPrThreads + threadIdx.x; v < n; v += stride) {
         const int32_t od = __ldg(outdeg + v);
         const double x = od ? static_cast<double>(wc[v]) * od : static_cast<double>(wc[v]);
         ranks[v] = static_cast<T>(x * inv_s);
@@ -290,48 +682,53 @@ __global__ void __launch_bounds__(kPrThreads) k_pagerank(
     }
 }
 
-template <typename T, int G>
-ffg_status launch_g(const ffg_graph *g, double alpha, double tol, int max_iter, int init,
-                    T *ranks, PrWs &w, cudaStream_t stream) {
-    auto kern = k_pagerank<T, G>;
+template <typename T>
+ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, int init,
+                  T *ranks, PrWs &w, cudaStream_t stream) {
     int dev = 0, sms = 0, per_sm = 0;
     FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
     FFG_TRY(check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
-    FFG_TRY(check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPrThreads, 0),
-                       "occupancy"));
+    const int64_t n = g->n_nodes;
+    const int64_t tiles = (n + 31) / 32;
+    {   // layout of the in-edges
+        const int64_t want = (tiles + kLayoutThreads / 32 - 1) / (kLayoutThreads / 32);
+        const int64_t cap = int64_t(sms) * 32;
+        const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
+        k_pr_layout<<<grid, kLayoutThreads, 0, stream>>>(g->in_ptr, g->in_idx, n, w.layout, w.meta);
+        count_launch();
+        FFG_TRY(check_launch("k_pr_layout"));
+    }
+    auto kern = k_pagerank<T>;
+    const size_t smem = pr_smem_bytes<T>();
+    FFG_TRY(check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(smem)),
+                       "smem attribute"));
+    FFG_TRY(check_cuda(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPrThreads, smem),
+        "occupancy"));
     int64_t max_res = int64_t(sms) * per_sm;
     if (max_res > kMaxBlocks) max_res = kMaxBlocks;
-    // at least ~8 row batches per block
-    const int64_t rows_per_block = int64_t(kPrThreads / G) * 8;
-    int64_t want = (g->n_nodes + rows_per_block - 1) / rows_per_block;
+    const int64_t want = (tiles + 4 * kWarps - 1) / (4 * kWarps);  // >= ~4 tiles per warp
     int nb = static_cast<int>(want < 1 ? 1 : (want > max_res ? max_res : want));
     if (nb < 1) return set_error("kernel does not fit on the device"), FFG_ERR_CUDA;
     const int64_t *in_ptr = g->in_ptr;
     const int32_t *in_idx = g->in_idx;
     const int32_t *outdeg = g->outdeg;
-    int64_t n = g->n_nodes;
+    const uint32_t *layout = w.layout;
+    const uint8_t *meta = w.meta;
+    int64_t nn = n;
     T *w0 = static_cast<T *>(w.w0), *w1 = static_cast<T *>(w.w1);
     double *partials = w.partials;
     PrCtl *ctl = w.ctl;
-    void *args[] = {(void *)&in_ptr, (void *)&in_idx, (void *)&outdeg, (void *)&n,
-                    (void *)&alpha, (void *)&tol, (void *)&max_iter, (void *)&init,
-                    (void *)&ranks, (void *)&w0, (void *)&w1, (void *)&partials,
-                    (void *)&ctl};
+    void *args[] = {(void *)&in_ptr, (void *)&in_idx, (void *)&outdeg, (void *)&layout,
+                    (void *)&meta, (void *)&nn, (void *)&alpha, (void *)&tol,
+                    (void *)&max_iter, (void *)&init, (void *)&ranks, (void *)&w0, (void *)&w1,
+                    (void *)&partials, (void *)&ctl};
     FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)kern, dim3(nb), dim3(kPrThreads),
-                                                   args, 0, stream),
+                                                   args, smem, stream),
                        "k_pagerank"));
     count_launch();
     return FFG_OK;
-}
-
-template <typename T>
-ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, int init,
-                  T *ranks, PrWs &w, cudaStream_t stream) {
-    const double avg = g->n_nodes ? double(g->n_edges) / double(g->n_nodes) : 0.0;
-    if (avg >= 48) return launch_g<T, 16>(g, alpha, tol, max_iter, init, ranks, w, stream);
-    if (avg >= 20) return launch_g<T, 8>(g, alpha, tol, max_iter, init, ranks, w, stream);
-    if (avg >= 6) return launch_g<T, 4>(g, alpha, tol, max_iter, init, ranks, w, stream);
-    return launch_g<T, 2>(g, alpha, tol, max_iter, init, ranks, w, stream);
 }
 
 ffg_status read_result(const PrCtl *dctl, int32_t *iters_out, double *residual_out,
@@ -343,7 +740,7 @@ ffg_status read_result(const PrCtl *dctl, int32_t *iters_out, double *residual_o
     if (iters_out) *iters_out = h.iters;
     if (residual_out) *residual_out = h.residual;
     if (h.status != 0) {
-        set_error("pagerank: device barrier timed out");
+        set_error("pagerank: a bounded device wait timed out");
         return static_cast<ffg_status>(h.status);
     }
     return h.converged ? FFG_OK : FFG_ERR_NOT_CONVERGED;
@@ -355,9 +752,9 @@ ffg_status read_result(const PrCtl *dctl, int32_t *iters_out, double *residual_o
 
 using namespace ffg;
 
-extern "C" size_t pagerank_workspace_bytes(int64_t n_nodes, ffg_prec prec) {
-    if (n_nodes < 0) return 0;
-    return carve(nullptr, n_nodes, prec == FFG_F32 ? 4 : 8).bytes;
+extern "C" size_t pagerank_workspace_bytes(int64_t n_nodes, int64_t n_edges, ffg_prec prec) {
+    if (n_nodes < 0 || n_edges < 0) return 0;
+    return carve(nullptr, n_nodes, n_edges, prec == FFG_F32 ? 4 : 8).bytes;
 }
 
 extern "C" ffg_status pagerank_solve(const ffg_graph *g, double damping, double tol,
@@ -378,7 +775,7 @@ extern "C" ffg_status pagerank_solve(const ffg_graph *g, double damping, double 
     if (!ranks || !workspace) return set_error("ranks/workspace NULL"), FFG_ERR_INVALID_ARG;
     if (!aligned256(workspace))
         return set_error("workspace not 256-byte aligned"), FFG_ERR_INVALID_ARG;
-    PrWs w = carve(workspace, g->n_nodes, prec == FFG_F32 ? 4 : 8);
+    PrWs w = carve(workspace, g->n_nodes, g->n_edges, prec == FFG_F32 ? 4 : 8);
     if (ws_bytes < w.bytes)
         return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
     FFG_TRY(check_cuda(cudaMemsetAsync(w.ctl, 0, sizeof(PrCtl), stream), "memset"));

@@ -100,7 +100,7 @@ def test_workspace_sizes_monotone(lib):
     small = ffg.Space.from_spec(fi.single_small())
     large = ffg.Space.from_spec(fi.single_large())
     assert ffg.ffg_workspace_bytes(large, 0) > ffg.ffg_workspace_bytes(small, 0)
-    assert ffg.pagerank_workspace_bytes(10**6, ffg.F64) > ffg.pagerank_workspace_bytes(10**6, ffg.F32)
+    assert ffg.pagerank_workspace_bytes(10**6, 10**7, ffg.F64) > ffg.pagerank_workspace_bytes(10**6, 10**7, ffg.F32)
     assert ffg.centrality_workspace_bytes(5) > 0
 
 

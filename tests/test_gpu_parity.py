@@ -233,7 +233,7 @@ def test_async_solve_and_query():
     spec = fi.single_small()
     f = fi.runtimes(spec, 6)
     g, fd = run_build(spec, f, "hamming")
-    need = ffg.pagerank_workspace_bytes(g.n_nodes, ffg.F64)
+    need = ffg.pagerank_workspace_bytes(g.n_nodes, g.n_edges, ffg.F64)
     ws = ffg.workspace(need)
     x = torch.empty(g.n_nodes, dtype=torch.float64, device="cuda")
     st, it, res = ffg.pagerank_solve(g.c, 0.85, 1e-12, 1000, ffg.F64, x.data_ptr(), 0,
@@ -242,3 +242,15 @@ def test_async_solve_and_query():
     assert st == 0 and it is None
     st, it, res = ffg.pagerank_query(ws.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert st == 0 and it > 10 and res < 1e-12
+
+
+def test_centrality_many_thresholds():
+    """The largest threshold list (32 values, unsorted, with repeats)."""
+    spec = fi.single_small()
+    f = fi.runtimes(spec, 8, fail_frac=0.1)
+    og = oracle.build(spec, f, oracle.HAMMING)
+    g, fd = run_build(spec, f, "hamming")
+    p = list(np.linspace(0.3, 0.0, 30)) + [0.05, 0.05]
+    xe = oracle.pagerank_exact(og, 0.85)
+    x, *_ = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64)
+    assert np.abs(ffg.centrality(g, fd, x, p) - oracle.centrality(og, xe, p)).max() <= F64_CP
