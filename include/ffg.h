@@ -169,6 +169,26 @@ ffg_status pagerank_solve(const ffg_graph *g, double damping, double tol, int32_
                           size_t ws_bytes, int32_t *iters_out, double *residual_out,
                           void *stream);
 
+/* pagerank_solve for callers that cannot allocate device memory (for
+ * example code running while another component owns the device memory, or
+ * where cudaMalloc is not allowed or would synchronise the device).  The
+ * paper has no counterpart; this is a convenience of this library.
+ * Same arguments and results as pagerank_solve minus the workspace: the
+ * scratch space is a file-scope device array of 8 MiB that every device
+ * holds from the moment the library is loaded until the process exits.
+ * Graphs whose pagerank_workspace_bytes exceeds 8 MiB are rejected with
+ * FFG_ERR_NO_MEMORY (about 85,000 nodes at 20 in-edges per node in FP32).
+ * The first call on a device looks up the array's device address; make
+ * that first call before any stream capture.  Every call shares the one
+ * array (the parts that must start at zero are cleared by each call), so
+ * calls that overlap on the GPU -- from other streams or host threads --
+ * race and must be serialised by the caller.  Always synchronises `stream`
+ * once and returns the solve's status; iters_out / residual_out may be
+ * NULL. */
+ffg_status pagerank_solve_static(const ffg_graph *g, double damping, double tol,
+                                 int32_t max_iter, ffg_prec prec, void *ranks, int init,
+                                 int32_t *iters_out, double *residual_out, void *stream);
+
 /* Reads the outcome of the last pagerank_solve run in `workspace`
  * (synchronises `stream`).  Returns that run's status. */
 ffg_status pagerank_query(const void *workspace, int32_t *iters_out, double *residual_out,

@@ -64,7 +64,8 @@ class ffg_graph(C.Structure):
 
 # names of include/ffg.h's entry points (the ABI test checks the header)
 ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
-                "pagerank_workspace_bytes", "pagerank_solve", "pagerank_query",
+                "pagerank_workspace_bytes", "pagerank_solve", "pagerank_solve_static",
+                "pagerank_query",
                 "centrality_workspace_bytes", "centrality_proportion", "ffg_status_str",
                 "ffg_last_error", "ffg_launch_count")
 
@@ -92,6 +93,8 @@ def load(path: str | None = None):
     lib.pagerank_workspace_bytes.restype = sz
     lib.pagerank_solve.argtypes = [P(ffg_graph), f64, f64, i32, C.c_int, vp, C.c_int, vp, sz,
                                    P(i32), P(f64), vp]
+    lib.pagerank_solve_static.argtypes = [P(ffg_graph), f64, f64, i32, C.c_int, vp, C.c_int,
+                                          P(i32), P(f64), vp]
     lib.pagerank_query.argtypes = [vp, P(i32), P(f64), vp]
     lib.centrality_workspace_bytes.argtypes = [i32]
     lib.centrality_workspace_bytes.restype = sz
@@ -153,6 +156,18 @@ def pagerank_solve(g: ffg_graph, damping: float, tol: float, max_iter: int, prec
                                C.byref(it) if sync else None, C.byref(res) if sync else None,
                                C.c_void_p(stream))
     return (int(st), int(it.value), float(res.value)) if sync else (int(st), None, None)
+
+
+def pagerank_solve_static(g: ffg_graph, damping: float, tol: float, max_iter: int, prec: int,
+                          ranks: int, init: int = 0, stream: int = 0):
+    """PageRank without a workspace (scratch in the library's static device
+    array, 8 MiB).  For callers that cannot allocate device memory.
+    Returns (status, iters, residual)."""
+    it, res = C.c_int32(-1), C.c_double(float("nan"))
+    st = load().pagerank_solve_static(C.byref(g), float(damping), float(tol), int(max_iter),
+                                      int(prec), C.c_void_p(ranks), int(init), C.byref(it),
+                                      C.byref(res), C.c_void_p(stream))
+    return int(st), int(it.value), float(res.value)
 
 
 def pagerank_query(ws: int, stream: int = 0):
