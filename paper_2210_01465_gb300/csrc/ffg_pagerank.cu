@@ -682,6 +682,20 @@ __global__ void __launch_bounds__(kPrThreads, 3) k_pagerank(
     }
 }
 
+ffg_status launch_layout(const ffg_graph *g, PrWs &w, cudaStream_t stream) {
+    int dev = 0, sms = 0;
+    FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
+    FFG_TRY(check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
+    const int64_t n = g->n_nodes;
+    const int64_t tiles = (n + 31) / 32;
+    const int64_t want = (tiles + kLayoutThreads / 32 - 1) / (kLayoutThreads / 32);
+    const int64_t cap = int64_t(sms) * 32;
+    const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
+    k_pr_layout<<<grid, kLayoutThreads, 0, stream>>>(g->in_ptr, g->in_idx, n, w.layout, w.meta);
+    count_launch();
+    return check_launch("k_pr_layout");
+}
+
 template <typename T>
 ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, int init,
                   T *ranks, PrWs &w, cudaStream_t stream) {
@@ -690,14 +704,6 @@ ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, in
     FFG_TRY(check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
     const int64_t n = g->n_nodes;
     const int64_t tiles = (n + 31) / 32;
-    {   // layout of the in-edges
-        const int64_t want = (tiles + kLayoutThreads / 32 - 1) / (kLayoutThreads / 32);
-        const int64_t cap = int64_t(sms) * 32;
-        const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
-        k_pr_layout<<<grid, kLayoutThreads, 0, stream>>>(g->in_ptr, g->in_idx, n, w.layout, w.meta);
-        count_launch();
-        FFG_TRY(check_launch("k_pr_layout"));
-    }
     auto kern = k_pagerank<T>;
     const size_t smem = pr_smem_bytes<T>();
     FFG_TRY(check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -778,15 +784,35 @@ extern "C" ffg_status pagerank_solve(const ffg_graph *g, double damping, double 
     PrWs w = carve(workspace, g->n_nodes, g->n_edges, prec == FFG_F32 ? 4 : 8);
     if (ws_bytes < w.bytes)
         return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
+    if (init & ~(FFG_INIT_RANKS | FFG_INIT_LAYOUT))
+        return set_error("unknown init flags 0x%x", init), FFG_ERR_INVALID_ARG;
     FFG_TRY(check_cuda(cudaMemsetAsync(w.ctl, 0, sizeof(PrCtl), stream), "memset"));
+    if (!(init & FFG_INIT_LAYOUT)) FFG_TRY(launch_layout(g, w, stream));
+    const int warm = (init & FFG_INIT_RANKS) ? 1 : 0;
     if (prec == FFG_F64)
-        FFG_TRY(launch<double>(g, damping, tol, max_iter, init, static_cast<double *>(ranks), w,
+        FFG_TRY(launch<double>(g, damping, tol, max_iter, warm, static_cast<double *>(ranks), w,
                                stream));
     else
-        FFG_TRY(launch<float>(g, damping, tol, max_iter, init, static_cast<float *>(ranks), w,
+        FFG_TRY(launch<float>(g, damping, tol, max_iter, warm, static_cast<float *>(ranks), w,
                               stream));
     if (!iters_out && !residual_out) return FFG_OK;
     return read_result(w.ctl, iters_out, residual_out, stream);
+}
+
+extern "C" ffg_status pagerank_prepare(const ffg_graph *g, ffg_prec prec, void *workspace,
+                                       size_t ws_bytes, void *stream_) {
+    clear_error();
+    if (!g || g->n_nodes <= 0 || !g->in_ptr || (g->n_edges > 0 && !g->in_idx))
+        return set_error("graph is empty or incomplete"), FFG_ERR_INVALID_ARG;
+    if (g->n_nodes >= (int64_t(1) << 31)) return set_error("too many nodes"), FFG_ERR_OVERFLOW;
+    if (prec != FFG_F64 && prec != FFG_F32)
+        return set_error("unknown precision %d", (int)prec), FFG_ERR_INVALID_ARG;
+    if (!workspace || !aligned256(workspace))
+        return set_error("workspace NULL or not 256-byte aligned"), FFG_ERR_INVALID_ARG;
+    PrWs w = carve(workspace, g->n_nodes, g->n_edges, prec == FFG_F32 ? 4 : 8);
+    if (ws_bytes < w.bytes)
+        return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
+    return launch_layout(g, w, static_cast<cudaStream_t>(stream_));
 }
 
 extern "C" ffg_status pagerank_query(const void *workspace, int32_t *iters_out,
@@ -796,66 +822,4 @@ extern "C" ffg_status pagerank_query(const void *workspace, int32_t *iters_out,
         return set_error("workspace NULL or misaligned"), FFG_ERR_INVALID_ARG;
     const PrCtl *ctl = static_cast<const PrCtl *>(workspace);
     return read_result(ctl, iters_out, residual_out, static_cast<cudaStream_t>(stream_));
-}
-
-// ---------------------------------------------------------------------------
-// PageRank without a caller-provided workspace.
-//
-// Some callers cannot allocate device memory when they want centralities:
-// code that runs while another component owns all device memory through its
-// own pool, or that runs where cudaMalloc is not allowed or would stall the
-// device (it can synchronise), e.g. a tuning loop embedded in a
-// latency-sensitive application.  For them the scratch space lives in one
-// file-scope device array, allocated when the library is loaded on a device
-// and held until the process exits.
-// ---------------------------------------------------------------------------
-namespace {
-
-constexpr size_t kStaticScratchBytes = size_t(8) << 20;  // 8 MiB per device
-__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::atomic<void *> g_static_ptr[kMaxDevices];
-
-// Device address of g_static_scratch on the current device (looked up once
-// per device; the host-side symbol itself is not a device address).
-ffg_status static_scratch(void **out) {
-    int dev = 0;
-    FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
-    if (dev < 0 || dev >= kMaxDevices) return set_error("device index %d too large", dev), FFG_ERR_CUDA;
-    void *p = g_static_ptr[dev].load();
-    if (!p) {
-        FFG_TRY(check_cuda(cudaGetSymbolAddress(&p, g_static_scratch),
-                           "cudaGetSymbolAddress(static scratch)"));
-        g_static_ptr[dev].store(p);
-    }
-    *out = p;
-    return FFG_OK;
-}
-
-}  // namespace
-
-extern "C" ffg_status pagerank_solve_static(const ffg_graph *g, double damping, double tol,
-                                            int32_t max_iter, ffg_prec prec, void *ranks,
-                                            int init, int32_t *iters_out, double *residual_out,
-                                            void *stream) {
-    clear_error();
-    if (!g || g->n_nodes <= 0 || g->n_edges < 0)
-        return set_error("graph is empty or incomplete"), FFG_ERR_INVALID_ARG;
-    const size_t need = pagerank_workspace_bytes(g->n_nodes, g->n_edges, prec);
-    if (need > kStaticScratchBytes) {
-        set_error("pagerank_solve_static: this graph needs %zu bytes of scratch, the static "
-                  "scratch holds %zu; use pagerank_solve with a workspace",
-                  need, kStaticScratchBytes);
-        return FFG_ERR_NO_MEMORY;
-    }
-    void *scratch = nullptr;
-    FFG_TRY(static_scratch(&scratch));
-    int32_t iters = 0;
-    double res = 0.0;
-    const ffg_status st = pagerank_solve(g, damping, tol, max_iter, prec, ranks, init, scratch,
-                                         kStaticScratchBytes, &iters, &res, stream);
-    if (iters_out) *iters_out = iters;
-    if (residual_out) *residual_out = res;
-    return st;
 }

@@ -83,6 +83,9 @@ def test_argument_errors_before_cuda(lib):
     assert ffg.pagerank_solve(g, 0.85, 1e-9, 0, 0, 256, 0, 256, 1 << 20)[0] == 1
     assert ffg.pagerank_solve(g, 0.85, 1e-9, 10, 5, 256, 0, 256, 1 << 20)[0] == 1
     assert ffg.pagerank_solve(g, 0.85, 1e-9, 10, 0, 256, 0, 256, 8)[0] == ffg.FFG_ERR_NO_MEMORY
+    assert ffg.pagerank_solve(g, 0.85, 1e-9, 10, 0, 256, 4, 256, 1 << 30)[0] == 1
+    assert ffg.pagerank_prepare(e, 0, 256, 1 << 20) == 1
+    assert ffg.pagerank_prepare(g, 0, 258, 1 << 20) == 1
     # centrality: n_p out of range, negative p
     g.is_min, g.node_raw, g.n_minima = 256, 256, 1
     out = np.zeros(40)

@@ -254,3 +254,18 @@ def test_centrality_many_thresholds():
     xe = oracle.pagerank_exact(og, 0.85)
     x, *_ = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64)
     assert np.abs(ffg.centrality(g, fd, x, p) - oracle.centrality(og, xe, p)).max() <= F64_CP
+
+
+def test_prepared_layout_and_damping_sweep():
+    """One pagerank_prepare, then solves at several damping factors reuse it."""
+    spec = fi.single_small()
+    f = fi.runtimes(spec, 10, fail_frac=0.2)
+    og = oracle.build(spec, f, oracle.HAMMING)
+    g, fd = run_build(spec, f, "hamming")
+    need = ffg.pagerank_workspace_bytes(g.n_nodes, g.n_edges, ffg.F64)
+    ws = ffg.workspace(need)
+    assert ffg.pagerank_prepare(g.c, ffg.F64, ws.data_ptr(), need,
+                                torch.cuda.current_stream().cuda_stream) == 0
+    for alpha in (0.5, 0.7, 0.85, 0.95):
+        x, it, res, conv = ffg.pagerank(g, alpha, 1e-13, prec=ffg.F64, ws=ws, prepared=True)
+        assert conv and np.abs(_np(x) - oracle.pagerank_exact(og, alpha)).sum() <= F64_L1
