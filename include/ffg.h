@@ -154,9 +154,10 @@ ffg_status ffg_build_fill(const ffg_space *space, const double *fitness_raw, ffg
  *           + (damping * sum_{outdeg(u)=0} x[u] + 1 - damping) / n_nodes.
  * Starts from x = 1/n_nodes (or from `ranks` when init has FFG_INIT_RANKS;
  * it must then hold a positive vector summing to 1) and stops when
- * sum_v |x'[v] - x[v]| < tol, returning x'.  FFG_F32 keeps ranks and the
- * per-row sums in FP32 and every reduction (dangling mass, residual,
- * normalisation) in FP64, and also stops once the residual stops decreasing
+ * sum_v |x'[v] - x[v]| < tol, returning x'.  The dangling mass, the
+ * residual and the normalising sum are exact 64-bit fixed-point sums
+ * (quantum 2^-60) read as FP64, in both precisions.  FFG_F32 keeps ranks and
+ * per-row sums in FP32 and also stops once the residual stops decreasing
  * (the FP32 rounding floor).  `ranks` (DEVICE, n_nodes floats or doubles per
  * `prec`) receives x' normalised to sum 1.
  * iters_out / residual_out (HOST) receive the iteration count and the last

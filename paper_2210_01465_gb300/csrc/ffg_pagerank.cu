@@ -28,18 +28,19 @@
 // in one chunk, or 2^24 nodes and more) keep the plain CSR path.
 //
 // k_pagerank is one cooperative persistent launch for every iteration.
-// Each warp owns a contiguous range of tiles of about equal cost; lane t
-// owns row 32*tile + t, so per-row loads and stores are coalesced.  One
+// Each block owns a contiguous range of tiles of about equal cost and its
+// warps take tiles from it in turn; lane t owns row 32*tile + t, so per-row
+// loads and stores are coalesced.  One
 // lane streams the tile's chunks into a double-buffered shared-memory stage
 // with TMA bulk copies (cp.async.bulk, completion on an mbarrier), one
 // segment ahead, while the warp gathers w for the current segment and adds
 // into its accumulators.  Only w is kept between iterations (ping-pong):
 // x[v] = w[v] * outdeg[v] (or w[v] for a node without out-edges).  Residual
-// sum |x'-x|, next D and sum x' are accumulated per thread
-// (Kahan-compensated FP32 in the FP32 path, FP64 otherwise), reduced in FP64
-// per block into a double-buffered partials array, and after a grid barrier
-// every block sums the partials in the same fixed order, so all blocks take
-// the same stopping decision and results are deterministic for a given grid.
+// sum |x'-x|, next D and sum x' are accumulated as exact 64-bit fixed-point
+// integers (quantum 2^-60), reduced per block into a double-buffered
+// partials array, and after a grid barrier every block sums the partials;
+// integer sums do not depend on order, so all blocks take the same stopping
+// decision and results are deterministic however tiles were scheduled.
 // Every wait (grid barrier, mbarrier) is bounded; on expiry the kernel
 // records FFG_ERR_TIMEOUT, lets its own copies land, and returns.
 #include "ffg_internal.cuh"
@@ -57,11 +58,20 @@ constexpr int kMaxSlots = 7;            // entries of one row within one chunk
 constexpr uint32_t kDummyOff = (7u << 5) | 7u;  // accumulator of padding entries
 constexpr uint32_t kPadEntry = kDummyOff;       // source 0, dummy accumulator
 constexpr int kAccElems = 8 * 32;       // accumulators per warp (7 slots + dummy)
-constexpr int kSeg = 16;                // chunks per TMA segment
-constexpr int kGroup = 8;               // gathers in flight per lane
+#ifndef FFG_PR_SEG
+#define FFG_PR_SEG 16
+#endif
+#ifndef FFG_PR_GROUP
+#define FFG_PR_GROUP 8
+#endif
+#ifndef FFG_PR_MINBLOCKS
+#define FFG_PR_MINBLOCKS 3
+#endif
+constexpr int kSeg = FFG_PR_SEG;        // chunks per TMA segment
+constexpr int kGroup = FFG_PR_GROUP;    // gathers in flight per lane
 constexpr int64_t kMaxPackedNodes = int64_t(1) << 24;
 constexpr int kLayoutThreads = 64;
-constexpr int64_t kRowCost = 8;         // per-row cost in in-edge units (warp split)
+constexpr int64_t kRowCost = 20;        // per-row cost in in-edge units (block split)
 
 struct PrCtl {
     unsigned int barrier;
@@ -75,7 +85,7 @@ struct PrCtl {
 
 struct PrWs {
     PrCtl *ctl;
-    double *partials;  // [2][kMaxBlocks][4]
+    long long *partials;  // [2][kMaxBlocks][4] fixed-point block sums
     void *w0, *w1;
     uint32_t *layout;  // packed chunks
     uint8_t *meta;     // per tile: accumulator slots used (1..kMaxSlots), 0 = CSR path
@@ -88,7 +98,7 @@ PrWs carve(void *base, int64_t n, int64_t e, size_t elem) {
     Carver c(base);
     PrWs w;
     w.ctl = c.take<PrCtl>(1);
-    w.partials = c.take<double>(size_t(2) * kMaxBlocks * 4);
+    w.partials = c.take<long long>(size_t(2) * kMaxBlocks * 4);
     w.w0 = c.take<char>(size_t(n) * elem);
     w.w1 = c.take<char>(size_t(n) * elem);
     w.layout = c.take<uint32_t>(size_t(layout_chunks(n, e)) * 32);
@@ -197,51 +207,72 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// block sums of three doubles; valid in thread 0
-__device__ __forceinline__ void block_sum3(double &a, double &b, double &c) {
-    __shared__ double red[3][kWarps];
-    a = warp_sum(a);
-    b = warp_sum(b);
-    c = warp_sum(c);
+// The residual, the dangling mass and the sum of x are accumulated as 64-bit
+// fixed-point integers with quantum 2^-60 (all three are sums of
+// non-negative values below 8).  Integer sums are exact and independent of
+// order, so they are deterministic however tiles are scheduled, and they use
+// no FP64 instruction (a narrow pipe on this part) on the per-row path.
+constexpr double kFix = 1152921504606846976.0;  // 2^60
+__device__ __forceinline__ long long to_fix(float x) {
+    return __float2ll_rn(x * 1152921504606846976.0f);
+}
+__device__ __forceinline__ long long to_fix(double x) { return __double2ll_rn(x * kFix); }
+
+struct Fix3 {
+    long long r = 0, d = 0, s = 0;
+};
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block sums of the three accumulators; valid in thread 0
+__device__ __forceinline__ Fix3 block_sum_fix(Fix3 v) {
+    __shared__ long long red[3][kWarps];
+    v.r = warp_sum_ll(v.r);
+    v.d = warp_sum_ll(v.d);
+    v.s = warp_sum_ll(v.s);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) {
-        red[0][warp] = a;
-        red[1][warp] = b;
-        red[2][warp] = c;
+        red[0][warp] = v.r;
+        red[1][warp] = v.d;
+        red[2][warp] = v.s;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        a = b = c = 0.0;
+    Fix3 t;
+    if (threadIdx.x == 0)
         for (int k = 0; k < kWarps; ++k) {
-            a += red[0][k];
-            b += red[1][k];
-            c += red[2][k];
+            t.r += red[0][k];
+            t.d += red[1][k];
+            t.s += red[2][k];
         }
-    }
+    return t;
 }
 
 struct Tot {
     double r, d, s;
 };
 
-// every block sums the partials of all blocks in the same order (warp 0)
-__device__ __forceinline__ Tot sum_partials(const double *part, int nb) {
+// every block sums the partials of all blocks (warp 0)
+__device__ __forceinline__ Tot sum_partials(const long long *part, int nb) {
     __shared__ double s_out[3];
     if (threadIdx.x < 32) {
-        double a = 0, b = 0, c = 0;
+        long long a = 0, b = 0, c = 0;
         for (int k = threadIdx.x; k < nb; k += 32) {
             a += __ldcg(part + 4 * k + 0);
             b += __ldcg(part + 4 * k + 1);
             c += __ldcg(part + 4 * k + 2);
         }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        c = warp_sum(c);
+        a = warp_sum_ll(a);
+        b = warp_sum_ll(b);
+        c = warp_sum_ll(c);
         if (threadIdx.x == 0) {
-            s_out[0] = a;
-            s_out[1] = b;
-            s_out[2] = c;
+            s_out[0] = static_cast<double>(a) / kFix;
+            s_out[1] = static_cast<double>(b) / kFix;
+            s_out[2] = static_cast<double>(c) / kFix;
         }
     }
     __syncthreads();
@@ -249,31 +280,6 @@ __device__ __forceinline__ Tot sum_partials(const double *part, int nb) {
     __syncthreads();
     return t;
 }
-
-// per-thread accumulation of the residual / dangling mass / sum: FP32 values
-// are added with Kahan compensation (no FP64 instruction per row); FP64
-// values are added in FP64.  The block reduction is FP64 in both cases.
-template <typename T>
-struct Acc;
-template <>
-struct Acc<float> {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const {
-        return static_cast<double>(s) - static_cast<double>(c);
-    }
-};
-template <>
-struct Acc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double x) { s += x; }
-    __device__ __forceinline__ double value() const { return s; }
-};
 
 // ---------------------------------------------------------------------------
 // gather-friendly layout of the in-edges (built once per solve)
@@ -390,7 +396,6 @@ struct Stream {
     __device__ __forceinline__ void issue(const uint32_t *layout, int64_t chunk, int cnt, int b,
                                           int lane) {
         if (lane == 0) {
-            fence_proxy_async();
             tma_load(stage + b * (kSeg * 32), layout + chunk * 32, static_cast<uint32_t>(cnt) * 128u,
                      bar + b);
         }
@@ -502,7 +507,7 @@ __device__ __forceinline__ T tile_sum_csr(const int32_t *__restrict__ in_idx, co
     return s;
 }
 
-// First tile of warp w when the tiles are split into nw contiguous ranges of
+// First tile of part w when the tiles are split into nw contiguous ranges of
 // about equal cost (in-edges plus kRowCost per row).
 __device__ __forceinline__ int64_t tile_split(const int64_t *__restrict__ in_ptr, int64_t n,
                                               int64_t ntiles, int64_t w, int64_t nw) {
@@ -526,11 +531,11 @@ constexpr size_t pr_smem_bytes() {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kPrThreads, 3) k_pagerank(
+__global__ void __launch_bounds__(kPrThreads, FFG_PR_MINBLOCKS) k_pagerank(
     const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx,
     const int32_t *__restrict__ outdeg, const uint32_t *__restrict__ layout,
     const uint8_t *__restrict__ meta, int64_t n, double alpha, double tol, int max_iter,
-    int init, T *ranks, T *w0, T *w1, double *partials, PrCtl *ctl) {
+    int init, T *ranks, T *w0, T *w1, long long *partials, PrCtl *ctl) {
     extern __shared__ __align__(128) unsigned char s_dyn[];
     const int nb = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -553,36 +558,38 @@ __global__ void __launch_bounds__(kPrThreads, 3) k_pagerank(
     }
     __syncwarp();
 
-    const int64_t gwarp = int64_t(blockIdx.x) * kWarps + warp;
-    const int64_t nwarps = int64_t(nb) * kWarps;
     const int64_t ntiles = (n + 31) >> 5;
-    int64_t ta = 0, tb = 0;
-    if (lane == 0) {
-        ta = tile_split(in_ptr, n, ntiles, gwarp, nwarps);
-        tb = tile_split(in_ptr, n, ntiles, gwarp + 1, nwarps);
+    // the block's contiguous tile range (about equal cost per block); its
+    // warps take tiles from it in turn through a shared counter
+    __shared__ int64_t s_range[2];
+    __shared__ unsigned long long s_next;
+    if (threadIdx.x == 0) {
+        s_range[0] = tile_split(in_ptr, n, ntiles, blockIdx.x, nb);
+        s_range[1] = tile_split(in_ptr, n, ntiles, blockIdx.x + 1, nb);
+        s_next = static_cast<unsigned long long>(s_range[0] + kWarps);
     }
-    ta = __shfl_sync(0xffffffffu, ta, 0);
-    tb = __shfl_sync(0xffffffffu, tb, 0);
+    __syncthreads();
+    const int64_t bt0 = s_range[0], bt1 = s_range[1];
     const double inv_n = 1.0 / static_cast<double>(n);
 
     // prologue: w from the start vector, D_0 and sum x_0 (grid-stride)
     {
-        Acc<double> dsum, xsum;
+        Fix3 acc0;
         const int64_t stride = int64_t(nb) * kPrThreads;
         for (int64_t v = int64_t(blockIdx.x) * kPrThreads + threadIdx.x; v < n; v += stride) {
             const double x0 = init ? static_cast<double>(ranks[v]) : inv_n;
             const int32_t od = __ldg(outdeg + v);
             w0[v] = static_cast<T>(od ? x0 / od : x0);
-            if (od == 0) dsum.add(x0);
-            xsum.add(x0);
+            const long long q = to_fix(x0);
+            if (od == 0) acc0.d += q;
+            acc0.s += q;
         }
-        double unused = 0.0, d = dsum.value(), x = xsum.value();
-        block_sum3(unused, d, x);
+        const Fix3 b = block_sum_fix(acc0);
         if (threadIdx.x == 0) {
-            double *p = partials + 4 * blockIdx.x;
-            p[0] = 0.0;
-            p[1] = d;
-            p[2] = x;
+            long long *p = partials + 4 * blockIdx.x;
+            p[0] = 0;
+            p[1] = b.d;
+            p[2] = b.s;
         }
     }
     unsigned phase = 1;
@@ -597,13 +604,17 @@ __global__ void __launch_bounds__(kPrThreads, 3) k_pagerank(
     int failed = 0;
     while (true) {
         const T c = static_cast<T>((alpha * dang + 1.0 - alpha) * inv_n);
-        Acc<T> r_acc, d_acc, s_acc;
-        if (ta < tb && !failed) {
-            TileInfo<T> cur = load_info<T>(ta, n, in_ptr, meta, outdeg, wc, lane);
-            for (int64_t t = ta; t < tb; ++t) {
-                const bool has_next = t + 1 < tb;
+        Fix3 facc;
+        int64_t t = bt0 + warp;
+        if (t < bt1 && !failed) {
+            TileInfo<T> cur = load_info<T>(t, n, in_ptr, meta, outdeg, wc, lane);
+            while (true) {
+                unsigned long long g = 0;
+                if (lane == 0) g = atomicAdd(&s_next, 1ULL);
+                const int64_t tn = static_cast<int64_t>(__shfl_sync(0xffffffffu, g, 0));
+                const bool has_next = tn < bt1;
                 TileInfo<T> nxt = cur;
-                if (has_next) nxt = load_info<T>(t + 1, n, in_ptr, meta, outdeg, wc, lane);
+                if (has_next) nxt = load_info<T>(tn, n, in_ptr, meta, outdeg, wc, lane);
                 const int64_t v = (t << 5) + lane;
                 const bool row_ok = v < n;
                 T s = T(0);
@@ -627,12 +638,15 @@ __global__ void __launch_bounds__(kPrThreads, 3) k_pagerank(
                 if (row_ok) {
                     const T xo = cur.od ? cur.wv * static_cast<T>(cur.od) : cur.wv;
                     const T xn = a * s + c;
-                    r_acc.add(xn > xo ? xn - xo : xo - xn);
-                    if (cur.od == 0) d_acc.add(xn);
-                    s_acc.add(xn);
+                    facc.r += to_fix(xn > xo ? xn - xo : xo - xn);
+                    const long long q = to_fix(xn);
+                    if (cur.od == 0) facc.d += q;
+                    facc.s += q;
                     wn[v] = cur.od ? xn / static_cast<T>(cur.od) : xn;
                 }
+                if (!has_next) break;
                 cur = nxt;
+                t = tn;
             }
         }
         if (failed == 1) {
@@ -641,15 +655,15 @@ __global__ void __launch_bounds__(kPrThreads, 3) k_pagerank(
             if (lane == 0) atomicCAS(&ctl->status, 0, (int)FFG_ERR_TIMEOUT);
             failed = 2;
         }
-        double r_b = r_acc.value(), d_b = d_acc.value(), s_b = s_acc.value();
-        block_sum3(r_b, d_b, s_b);
+        const Fix3 b = block_sum_fix(facc);
         par ^= 1;
-        double *pp = partials + size_t(par) * kMaxBlocks * 4;
+        long long *pp = partials + size_t(par) * kMaxBlocks * 4;
         if (threadIdx.x == 0) {
-            double *p = pp + 4 * blockIdx.x;
-            p[0] = r_b;
-            p[1] = d_b;
-            p[2] = s_b;
+            long long *p = pp + 4 * blockIdx.x;
+            p[0] = b.r;
+            p[1] = b.d;
+            p[2] = b.s;
+            s_next = static_cast<unsigned long long>(bt0 + kWarps);  // next iteration's counter
         }
         ++phase;
         if (!grid_barrier(ctl, phase * nb)) return;
@@ -724,7 +738,7 @@ ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, in
     const uint8_t *meta = w.meta;
     int64_t nn = n;
     T *w0 = static_cast<T *>(w.w0), *w1 = static_cast<T *>(w.w1);
-    double *partials = w.partials;
+    long long *partials = w.partials;
     PrCtl *ctl = w.ctl;
     void *args[] = {(void *)&in_ptr, (void *)&in_idx, (void *)&outdeg, (void *)&layout,
                     (void *)&meta, (void *)&nn, (void *)&alpha, (void *)&tol,
