@@ -204,6 +204,52 @@ ffg_status pagerank_solve_static(const ffg_graph *g, double damping, double tol,
                                  int32_t max_iter, ffg_prec prec, void *ranks, int init,
                                  int32_t *iters_out, double *residual_out, void *stream);
 
+/* ---- batched PageRank: many solves in one persistent launch ----
+ * A job is one PageRank solve (same definition and stopping rules as
+ * pagerank_solve): graph g (host struct with DEVICE arrays), damping, tol,
+ * max_iter, init (FFG_INIT_RANKS or 0), and `ranks` (DEVICE output, n_nodes
+ * elements of the batch precision).  Jobs may share a graph (e.g. a damping
+ * sweep): its edge layout is built once per run.  The batch form of the
+ * survey shape of Sec. VII-B (one metric per kernel x GPU space). */
+typedef struct {
+    const ffg_graph *g;
+    double damping, tol;
+    int32_t max_iter, init;
+    void *ranks;
+} ffg_pr_job;
+
+/* Filled by pagerank_batch_plan; plain data owned by the caller (device
+ * pointers point into the plan's workspace). */
+typedef struct {
+    int32_t prec, n_jobs, n_graphs, n_blocks;
+    int64_t total_tiles;
+    void *jobs, *graphs, *items, *first, *ctl;
+} ffg_pr_batch;
+
+size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec);
+
+/* Host-side planning: validates the jobs, assigns every job a group of
+ * blocks of one cooperative grid (large jobs get several dedicated blocks,
+ * small ones one block each, longest first onto the least loaded block),
+ * carves the workspace and uploads the tables.  Synchronises `stream`. */
+ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec,
+                               void *workspace, size_t ws_bytes, ffg_pr_batch *plan,
+                               void *stream);
+
+/* Enqueues the whole batch: one layout launch over every distinct graph and
+ * one persistent launch that runs every job to its own convergence.  Host
+ * work is argument checking only, so the call can be captured in a CUDA
+ * graph and replayed (the graphs' contents may change between replays, not
+ * their sizes or addresses). */
+ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream);
+
+/* Per-job iterations, residuals and statuses (HOST arrays of n_jobs, each
+ * may be NULL) of the last run; synchronises `stream`.  Returns FFG_OK if
+ * every job converged, else the first non-OK status (FFG_ERR_TIMEOUT
+ * first). */
+ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *iters_out,
+                                double *residual_out, int32_t *status_out, void *stream);
+
 /* Reads the outcome of the last pagerank_solve run in `workspace`
  * (synchronises `stream`).  Returns that run's status. */
 ffg_status pagerank_query(const void *workspace, int32_t *iters_out, double *residual_out,

@@ -63,11 +63,24 @@ class ffg_graph(C.Structure):
                 ("node_raw", C.c_void_p), ("is_min", C.c_void_p), ("f_opt", C.c_double)]
 
 
+class ffg_pr_job(C.Structure):
+    _fields_ = [("g", C.POINTER(ffg_graph)), ("damping", C.c_double), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("init", C.c_int32), ("ranks", C.c_void_p)]
+
+
+class ffg_pr_batch(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("n_jobs", C.c_int32), ("n_graphs", C.c_int32),
+                ("n_blocks", C.c_int32), ("total_tiles", C.c_int64), ("jobs", C.c_void_p),
+                ("graphs", C.c_void_p), ("items", C.c_void_p), ("first", C.c_void_p),
+                ("ctl", C.c_void_p)]
+
+
 # names of include/ffg.h's entry points (the ABI test checks the header)
 ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
                 "pagerank_workspace_bytes", "pagerank_prepare", "pagerank_solve",
                 "pagerank_solve_static",
-                "pagerank_query",
+                "pagerank_query", "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
+                "pagerank_batch_run", "pagerank_batch_query",
                 "centrality_workspace_bytes", "centrality_proportion", "ffg_status_str",
                 "ffg_last_error", "ffg_launch_count")
 
@@ -99,6 +112,11 @@ def load(path: str | None = None):
     lib.pagerank_solve_static.argtypes = [P(ffg_graph), f64, f64, i32, C.c_int, vp, C.c_int,
                                           P(i32), P(f64), vp]
     lib.pagerank_query.argtypes = [vp, P(i32), P(f64), vp]
+    lib.pagerank_batch_workspace_bytes.argtypes = [P(ffg_pr_job), i32, C.c_int]
+    lib.pagerank_batch_workspace_bytes.restype = sz
+    lib.pagerank_batch_plan.argtypes = [P(ffg_pr_job), i32, C.c_int, vp, sz, P(ffg_pr_batch), vp]
+    lib.pagerank_batch_run.argtypes = [P(ffg_pr_batch), vp]
+    lib.pagerank_batch_query.argtypes = [P(ffg_pr_batch), vp, vp, vp, vp]
     lib.centrality_workspace_bytes.argtypes = [i32]
     lib.centrality_workspace_bytes.restype = sz
     lib.centrality_proportion.argtypes = [P(ffg_graph), vp, vp, C.c_int, vp, i32, vp, vp, sz, vp]
@@ -176,6 +194,32 @@ def pagerank_solve_static(g: ffg_graph, damping: float, tol: float, max_iter: in
                                       int(prec), C.c_void_p(ranks), int(init), C.byref(it),
                                       C.byref(res), C.c_void_p(stream))
     return int(st), int(it.value), float(res.value)
+
+
+def pagerank_batch_workspace_bytes(jobs, prec: int) -> int:
+    return int(load().pagerank_batch_workspace_bytes(jobs, len(jobs), int(prec)))
+
+
+def pagerank_batch_plan(jobs, prec: int, ws: int, ws_bytes: int, plan: "ffg_pr_batch",
+                        stream: int = 0) -> int:
+    return int(load().pagerank_batch_plan(jobs, len(jobs), int(prec), C.c_void_p(ws),
+                                          int(ws_bytes), C.byref(plan), C.c_void_p(stream)))
+
+
+def pagerank_batch_run(plan: "ffg_pr_batch", stream: int = 0) -> int:
+    return int(load().pagerank_batch_run(C.byref(plan), C.c_void_p(stream)))
+
+
+def pagerank_batch_query(plan: "ffg_pr_batch", stream: int = 0):
+    """Returns (status, iters[n_jobs], residual[n_jobs], status[n_jobs])."""
+    n = plan.n_jobs
+    it = np.zeros(n, dtype=np.int32)
+    res = np.zeros(n, dtype=np.float64)
+    st = np.zeros(n, dtype=np.int32)
+    s = load().pagerank_batch_query(C.byref(plan), C.c_void_p(it.ctypes.data),
+                                    C.c_void_p(res.ctypes.data), C.c_void_p(st.ctypes.data),
+                                    C.c_void_p(stream))
+    return int(s), it, res, st
 
 
 def pagerank_query(ws: int, stream: int = 0):
@@ -324,6 +368,46 @@ def pagerank(g: Graph, damping: float = 0.85, tol: float = 1e-12, max_iter: int 
                                  ws.data_ptr(), need, True, _stream_handle(stream))
     _check(st, "pagerank_solve", ok=(FFG_OK, FFG_ERR_NOT_CONVERGED))
     return ranks, it, res, st == FFG_OK
+
+
+class PageRankBatch:
+    """Many PageRank solves in one persistent launch (``pagerank_batch_*``).
+
+    ``specs``: list of (Graph, damping).  Holds the job array, the workspace,
+    the plan and the output tensors; ``run()`` only enqueues kernels, so it can
+    be captured in a CUDA graph; ``query()`` synchronises and returns the
+    per-job iterations, residuals and statuses."""
+
+    def __init__(self, specs, prec: int = F32, tol: float = 1e-12, max_iter: int = 10000,
+                 stream=None):
+        torch = _torch()
+        dt = torch.float64 if prec == F64 else torch.float32
+        self.graphs = [g for g, _ in specs]
+        self.ranks = [torch.empty(g.n_nodes, dtype=dt, device=g.out_ptr.device) for g in self.graphs]
+        self.jobs = (ffg_pr_job * len(specs))()
+        for k, (g, alpha) in enumerate(specs):
+            self.jobs[k].g = C.pointer(g.c)
+            self.jobs[k].damping = float(alpha)
+            self.jobs[k].tol = float(tol)
+            self.jobs[k].max_iter = int(max_iter)
+            self.jobs[k].init = 0
+            self.jobs[k].ranks = self.ranks[k].data_ptr()
+        self.prec = prec
+        need = pagerank_batch_workspace_bytes(self.jobs, prec)
+        if need == 0:
+            raise FFGError(FFG_ERR_INVALID_ARG, "pagerank_batch_workspace_bytes")
+        self.ws = workspace(need, self.graphs[0].out_ptr.device)
+        self.plan = ffg_pr_batch()
+        _check(pagerank_batch_plan(self.jobs, prec, self.ws.data_ptr(), need, self.plan,
+                                   _stream_handle(stream)), "pagerank_batch_plan")
+
+    def run(self, stream=None):
+        _check(pagerank_batch_run(self.plan, _stream_handle(stream)), "pagerank_batch_run")
+
+    def query(self, stream=None):
+        st, it, res, sts = pagerank_batch_query(self.plan, _stream_handle(stream))
+        _check(st, "pagerank_batch_query", ok=(FFG_OK, FFG_ERR_NOT_CONVERGED))
+        return it, res, sts
 
 
 def centrality(g: Graph, fitness, ranks, p, ws=None, stream=None) -> np.ndarray:

@@ -132,9 +132,6 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar) {
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 // one lane: expect `bytes` on `bar` and start the bulk copy global -> shared
 __device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes,
                                          uint64_t *bar) {
@@ -168,12 +165,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     }
 }
 
-// Grid-wide barrier over a cooperative launch.  Bounded: gives up after
+// Barrier over the `group` blocks of one job (all co-resident: cooperative
+// launch).  Bounded: gives up after
 // kTimeoutNs (or 2^24 polls), records FFG_ERR_TIMEOUT.  Returns false
 // (uniformly for the whole block) if the run must stop.
-__device__ bool grid_barrier(PrCtl *ctl, unsigned target) {
+__device__ bool group_barrier(PrCtl *ctl, unsigned target, int group) {
     __shared__ int s_ok;
     __syncthreads();
+    if (group == 1) return true;  // a one-block group only needs the block barrier
     if (threadIdx.x == 0) {
         __threadfence();
         red_release_add(&ctl->barrier, 1u);
@@ -201,11 +200,6 @@ __device__ bool grid_barrier(PrCtl *ctl, unsigned target) {
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // The residual, the dangling mass and the sum of x are accumulated as 64-bit
 // fixed-point integers with quantum 2^-60 (all three are sums of
@@ -284,23 +278,19 @@ __device__ __forceinline__ Tot sum_partials(const long long *part, int nb) {
 // ---------------------------------------------------------------------------
 // gather-friendly layout of the in-edges (built once per solve)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kLayoutThreads) k_pr_layout(
-    const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx, int64_t n,
-    uint32_t *__restrict__ layout, uint8_t *__restrict__ meta) {
-    __shared__ int32_t s_src[kLayoutThreads / 32][kSortCap];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t *src = s_src[warp];
-    const int64_t ntiles = (n + 31) >> 5;
-    const int64_t step = int64_t(gridDim.x) * (kLayoutThreads / 32);
+// One tile of the layout (one warp): see the comment at the top of the file.
+__device__ void layout_tiles(const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx,
+                             int64_t n, uint32_t *__restrict__ layout, uint8_t *__restrict__ meta,
+                             int64_t t, int32_t *src, int lane) {
     const unsigned lt_mask = (1u << lane) - 1u;
-    for (int64_t t = int64_t(blockIdx.x) * (kLayoutThreads / 32) + warp; t < ntiles; t += step) {
+    do {
         const int64_t r0 = t << 5;
         const int64_t rend = r0 + 32 < n ? r0 + 32 : n;
         const int64_t ip0 = in_ptr[r0], ip1 = in_ptr[rend];
         const int64_t et = ip1 - ip0;
         if (et > kSortCap || n >= kMaxPackedNodes) {
             if (lane == 0) meta[t] = 0;
-            continue;
+            break;
         }
         for (int64_t k = lane; k < et; k += 32) src[k] = in_idx[ip0 + k];
         const int64_t v = r0 + lane;
@@ -348,8 +338,19 @@ __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout(
             maxslot = y > maxslot ? y : maxslot;
         }
         if (lane == 0) meta[t] = maxslot < kMaxSlots ? static_cast<uint8_t>(maxslot + 1) : 0;
-        __syncwarp();
-    }
+    } while (false);
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kLayoutThreads) k_pr_layout(
+    const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx, int64_t n,
+    uint32_t *__restrict__ layout, uint8_t *__restrict__ meta) {
+    __shared__ int32_t s_src[kLayoutThreads / 32][kSortCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t ntiles = (n + 31) >> 5;
+    const int64_t step = int64_t(gridDim.x) * (kLayoutThreads / 32);
+    for (int64_t t = int64_t(blockIdx.x) * (kLayoutThreads / 32) + warp; t < ntiles; t += step)
+        layout_tiles(in_ptr, in_idx, n, layout, meta, t, s_src[warp], lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -530,42 +531,49 @@ constexpr size_t pr_smem_bytes() {
     return size_t(kWarps) * (2 * kSeg * 32 * sizeof(uint32_t) + kAccElems * sizeof(T) + 16);
 }
 
+// One PageRank job: a graph, its layout, its buffers and its parameters.
+// `group` blocks work on it together (ranks 0..group-1), synchronised by the
+// job's own bounded barrier in `ctl`.
+struct JobDev {
+    const int64_t *in_ptr;
+    const int32_t *in_idx;
+    const int32_t *outdeg;
+    const uint32_t *layout;
+    const uint8_t *meta;
+    void *ranks, *w0, *w1;
+    long long *partials;  // [2][group][4]
+    PrCtl *ctl;
+    int64_t n;
+    double alpha, tol;
+    int max_iter, init, group, pad;
+};
+
+// A group of blocks runs all iterations of one job.  Returns false if the
+// block must stop (a bounded wait expired).
 template <typename T>
-__global__ void __launch_bounds__(kPrThreads, FFG_PR_MINBLOCKS) k_pagerank(
-    const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx,
-    const int32_t *__restrict__ outdeg, const uint32_t *__restrict__ layout,
-    const uint8_t *__restrict__ meta, int64_t n, double alpha, double tol, int max_iter,
-    int init, T *ranks, T *w0, T *w1, long long *partials, PrCtl *ctl) {
-    extern __shared__ __align__(128) unsigned char s_dyn[];
-    const int nb = gridDim.x;
+__device__ bool run_job(const JobDev &J, int rank, Stream &st, T *acc) {
+    const int64_t *__restrict__ in_ptr = J.in_ptr;
+    const int32_t *__restrict__ in_idx = J.in_idx;
+    const int32_t *__restrict__ outdeg = J.outdeg;
+    const uint32_t *__restrict__ layout = J.layout;
+    const uint8_t *__restrict__ meta = J.meta;
+    const int64_t n = J.n;
+    const int nb = J.group;
+    T *ranks = static_cast<T *>(J.ranks);
+    T *w0 = static_cast<T *>(J.w0), *w1 = static_cast<T *>(J.w1);
+    long long *partials = J.partials;
+    PrCtl *ctl = J.ctl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // shared memory: per-warp stages, then accumulators, then mbarriers
-    Stream st;
-    st.stage = reinterpret_cast<uint32_t *>(s_dyn) + size_t(warp) * 2 * kSeg * 32;
-    T *acc = reinterpret_cast<T *>(s_dyn + size_t(kWarps) * 2 * kSeg * 32 * sizeof(uint32_t)) +
-             size_t(warp) * kAccElems;
-    st.bar = reinterpret_cast<uint64_t *>(s_dyn + size_t(kWarps) * 2 * kSeg * 32 * sizeof(uint32_t) +
-                                          size_t(kWarps) * kAccElems * sizeof(T)) +
-             2 * warp;
-    st.phase = 0;
-    st.pending = 0;
-    st.buf = 0;
-    st.issued = false;
-    if (lane == 0) {
-        mbar_init(st.bar);
-        mbar_init(st.bar + 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
 
     const int64_t ntiles = (n + 31) >> 5;
     // the block's contiguous tile range (about equal cost per block); its
     // warps take tiles from it in turn through a shared counter
     __shared__ int64_t s_range[2];
     __shared__ unsigned long long s_next;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        s_range[0] = tile_split(in_ptr, n, ntiles, blockIdx.x, nb);
-        s_range[1] = tile_split(in_ptr, n, ntiles, blockIdx.x + 1, nb);
+        s_range[0] = tile_split(in_ptr, n, ntiles, rank, nb);
+        s_range[1] = tile_split(in_ptr, n, ntiles, rank + 1, nb);
         s_next = static_cast<unsigned long long>(s_range[0] + kWarps);
     }
     __syncthreads();
@@ -576,8 +584,8 @@ __global__ void __launch_bounds__(kPrThreads, FFG_PR_MINBLOCKS) k_pagerank(
     {
         Fix3 acc0;
         const int64_t stride = int64_t(nb) * kPrThreads;
-        for (int64_t v = int64_t(blockIdx.x) * kPrThreads + threadIdx.x; v < n; v += stride) {
-            const double x0 = init ? static_cast<double>(ranks[v]) : inv_n;
+        for (int64_t v = int64_t(rank) * kPrThreads + threadIdx.x; v < n; v += stride) {
+            const double x0 = J.init ? static_cast<double>(ranks[v]) : inv_n;
             const int32_t od = __ldg(outdeg + v);
             w0[v] = static_cast<T>(od ? x0 / od : x0);
             const long long q = to_fix(x0);
@@ -586,20 +594,21 @@ __global__ void __launch_bounds__(kPrThreads, FFG_PR_MINBLOCKS) k_pagerank(
         }
         const Fix3 b = block_sum_fix(acc0);
         if (threadIdx.x == 0) {
-            long long *p = partials + 4 * blockIdx.x;
+            long long *p = partials + 4 * rank;
             p[0] = 0;
             p[1] = b.d;
             p[2] = b.s;
         }
     }
     unsigned phase = 1;
-    if (!grid_barrier(ctl, phase * nb)) return;
+    if (!group_barrier(ctl, phase * nb, nb)) return false;
     Tot tot = sum_partials(partials, nb);
     double dang = tot.d, xs = tot.s;
     double res = __longlong_as_double(0x7ff0000000000000LL), prev_res = res;
     int it = 0, converged = 0;
     T *wc = w0, *wn = w1;
     int par = 0;
+    const double alpha = J.alpha;
     const T a = static_cast<T>(alpha);
     int failed = 0;
     while (true) {
@@ -657,16 +666,16 @@ __global__ void __launch_bounds__(kPrThreads, FFG_PR_MINBLOCKS) k_pagerank(
         }
         const Fix3 b = block_sum_fix(facc);
         par ^= 1;
-        long long *pp = partials + size_t(par) * kMaxBlocks * 4;
+        long long *pp = partials + size_t(par) * nb * 4;
         if (threadIdx.x == 0) {
-            long long *p = pp + 4 * blockIdx.x;
+            long long *p = pp + 4 * rank;
             p[0] = b.r;
             p[1] = b.d;
             p[2] = b.s;
             s_next = static_cast<unsigned long long>(bt0 + kWarps);  // next iteration's counter
         }
         ++phase;
-        if (!grid_barrier(ctl, phase * nb)) return;
+        if (!group_barrier(ctl, phase * nb, nb)) return false;
         tot = sum_partials(pp, nb);
         prev_res = res;
         res = tot.r;
@@ -676,23 +685,94 @@ __global__ void __launch_bounds__(kPrThreads, FFG_PR_MINBLOCKS) k_pagerank(
         T *tmp = wc;
         wc = wn;
         wn = tmp;
-        if (res < tol) { converged = 1; break; }
+        if (res < J.tol) { converged = 1; break; }
         if (sizeof(T) == 4 && res >= prev_res) { converged = 1; break; }  // FP32 rounding floor
-        if (it >= max_iter) break;
+        if (it >= J.max_iter) break;
     }
     // epilogue: x' normalised to sum 1
     const double inv_s = 1.0 / xs;
     const int64_t stride = int64_t(nb) * kPrThreads;
-    for (int64_t v = int64_t(blockIdx.x) * kPrThreads + threadIdx.x; v < n; v += stride) {
+    for (int64_t v = int64_t(rank) * kPrThreads + threadIdx.x; v < n; v += stride) {
         const int32_t od = __ldg(outdeg + v);
         const double x = od ? static_cast<double>(wc[v]) * od : static_cast<double>(wc[v]);
         ranks[v] = static_cast<T>(x * inv_s);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
         ctl->iters = it;
         ctl->residual = res;
         ctl->converged = converged;
         ctl->nblocks = nb;
+    }
+    return failed == 0;
+}
+
+// The persistent kernel.  With jobs == nullptr it runs `single` on the whole
+// grid; otherwise block b runs the plan items [first[b], first[b+1]) in
+// order -- (job, rank) pairs, each block's multi-block job first, so that
+// no two groups ever wait on each other.
+template <typename T>
+__global__ void __launch_bounds__(kPrThreads, FFG_PR_MINBLOCKS)
+    k_pagerank(const JobDev *__restrict__ jobs, const int2 *__restrict__ items,
+               const int *__restrict__ first, int plan_blocks, JobDev single) {
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // shared memory: per-warp stages, then accumulators, then mbarriers
+    Stream st;
+    st.stage = reinterpret_cast<uint32_t *>(s_dyn) + size_t(warp) * 2 * kSeg * 32;
+    T *acc = reinterpret_cast<T *>(s_dyn + size_t(kWarps) * 2 * kSeg * 32 * sizeof(uint32_t)) +
+             size_t(warp) * kAccElems;
+    st.bar = reinterpret_cast<uint64_t *>(s_dyn + size_t(kWarps) * 2 * kSeg * 32 * sizeof(uint32_t) +
+                                          size_t(kWarps) * kAccElems * sizeof(T)) +
+             2 * warp;
+    st.phase = 0;
+    st.pending = 0;
+    st.buf = 0;
+    st.issued = false;
+    if (lane == 0) {
+        mbar_init(st.bar);
+        mbar_init(st.bar + 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (jobs == nullptr) {
+        run_job<T>(single, blockIdx.x, st, acc);
+        return;
+    }
+    if (static_cast<int>(gridDim.x) != plan_blocks) return;  // the host checks this too
+    for (int i = first[blockIdx.x]; i < first[blockIdx.x + 1]; ++i) {
+        const int2 item = items[i];
+        const JobDev J = jobs[item.x];
+        if (!run_job<T>(J, item.y, st, acc)) return;
+    }
+}
+
+// Layout kernel over every distinct graph of a batch: global tile index ->
+// graph by binary search over the graphs' first tiles.
+struct GraphDev {
+    const int64_t *in_ptr;
+    const int32_t *in_idx;
+    uint32_t *layout;
+    uint8_t *meta;
+    int64_t n;
+    int64_t tile0;  // first global tile of this graph
+};
+
+__global__ void __launch_bounds__(kLayoutThreads) k_pr_layout_batch(const GraphDev *__restrict__ gr,
+                                                                     int n_graphs,
+                                                                     int64_t total_tiles) {
+    __shared__ int32_t s_src[kLayoutThreads / 32][kSortCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t step = int64_t(gridDim.x) * (kLayoutThreads / 32);
+    for (int64_t gt = int64_t(blockIdx.x) * (kLayoutThreads / 32) + warp; gt < total_tiles;
+         gt += step) {
+        int lo = 0, hi = n_graphs - 1;  // last graph with tile0 <= gt
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (gr[mid].tile0 <= gt) lo = mid;
+            else hi = mid - 1;
+        }
+        const GraphDev g = gr[lo];
+        layout_tiles(g.in_ptr, g.in_idx, g.n, g.layout, g.meta, gt - g.tile0, s_src[warp], lane);
     }
 }
 
@@ -711,44 +791,65 @@ ffg_status launch_layout(const ffg_graph *g, PrWs &w, cudaStream_t stream) {
 }
 
 template <typename T>
-ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, int init,
-                  T *ranks, PrWs &w, cudaStream_t stream) {
-    int dev = 0, sms = 0, per_sm = 0;
+ffg_status kernel_config(int *blocks_per_sm, int *sms) {
+    int dev = 0;
     FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
-    FFG_TRY(check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
-    const int64_t n = g->n_nodes;
-    const int64_t tiles = (n + 31) / 32;
+    FFG_TRY(check_cuda(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
     auto kern = k_pagerank<T>;
     const size_t smem = pr_smem_bytes<T>();
     FFG_TRY(check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             static_cast<int>(smem)),
                        "smem attribute"));
     FFG_TRY(check_cuda(
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPrThreads, smem),
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, kPrThreads, smem),
         "occupancy"));
-    int64_t max_res = int64_t(sms) * per_sm;
-    if (max_res > kMaxBlocks) max_res = kMaxBlocks;
-    const int64_t want = (tiles + 4 * kWarps - 1) / (4 * kWarps);  // >= ~4 tiles per warp
-    int nb = static_cast<int>(want < 1 ? 1 : (want > max_res ? max_res : want));
-    if (nb < 1) return set_error("kernel does not fit on the device"), FFG_ERR_CUDA;
-    const int64_t *in_ptr = g->in_ptr;
-    const int32_t *in_idx = g->in_idx;
-    const int32_t *outdeg = g->outdeg;
-    const uint32_t *layout = w.layout;
-    const uint8_t *meta = w.meta;
-    int64_t nn = n;
-    T *w0 = static_cast<T *>(w.w0), *w1 = static_cast<T *>(w.w1);
-    long long *partials = w.partials;
-    PrCtl *ctl = w.ctl;
-    void *args[] = {(void *)&in_ptr, (void *)&in_idx, (void *)&outdeg, (void *)&layout,
-                    (void *)&meta, (void *)&nn, (void *)&alpha, (void *)&tol,
-                    (void *)&max_iter, (void *)&init, (void *)&ranks, (void *)&w0, (void *)&w1,
-                    (void *)&partials, (void *)&ctl};
+    if (*blocks_per_sm < 1) return set_error("kernel does not fit on the device"), FFG_ERR_CUDA;
+    return FFG_OK;
+}
+
+template <typename T>
+ffg_status launch_pr(const JobDev *jobs, const int2 *items, const int *first, int nb,
+                     const JobDev &single, cudaStream_t stream) {
+    auto kern = k_pagerank<T>;
+    const size_t smem = pr_smem_bytes<T>();
+    JobDev s = single;
+    void *args[] = {(void *)&jobs, (void *)&items, (void *)&first, (void *)&nb, (void *)&s};
     FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)kern, dim3(nb), dim3(kPrThreads),
                                                    args, smem, stream),
                        "k_pagerank"));
     count_launch();
     return FFG_OK;
+}
+
+template <typename T>
+ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, int init,
+                  T *ranks, PrWs &w, cudaStream_t stream) {
+    int per_sm = 0, sms = 0;
+    FFG_TRY(kernel_config<T>(&per_sm, &sms));
+    const int64_t tiles = (g->n_nodes + 31) / 32;
+    int64_t max_res = int64_t(sms) * per_sm;
+    if (max_res > kMaxBlocks) max_res = kMaxBlocks;
+    const int64_t want = (tiles + 4 * kWarps - 1) / (4 * kWarps);  // >= ~4 tiles per warp
+    const int nb = static_cast<int>(want < 1 ? 1 : (want > max_res ? max_res : want));
+    JobDev J;
+    J.in_ptr = g->in_ptr;
+    J.in_idx = g->in_idx;
+    J.outdeg = g->outdeg;
+    J.layout = w.layout;
+    J.meta = w.meta;
+    J.ranks = ranks;
+    J.w0 = w.w0;
+    J.w1 = w.w1;
+    J.partials = w.partials;
+    J.ctl = w.ctl;
+    J.n = g->n_nodes;
+    J.alpha = alpha;
+    J.tol = tol;
+    J.max_iter = max_iter;
+    J.init = init;
+    J.group = nb;
+    J.pad = 0;
+    return launch_pr<T>(nullptr, nullptr, nullptr, nb, J, stream);
 }
 
 ffg_status read_result(const PrCtl *dctl, int32_t *iters_out, double *residual_out,
@@ -836,4 +937,302 @@ extern "C" ffg_status pagerank_query(const void *workspace, int32_t *iters_out,
         return set_error("workspace NULL or misaligned"), FFG_ERR_INVALID_ARG;
     const PrCtl *ctl = static_cast<const PrCtl *>(workspace);
     return read_result(ctl, iters_out, residual_out, static_cast<cudaStream_t>(stream_));
+}
+
+// ---------------------------------------------------------------------------
+// batched PageRank: many jobs (graph, damping, tolerance) in one persistent
+// launch.  The plan assigns each job a group of blocks: jobs costing more
+// than two blocks' share of the total get dedicated blocks (their first
+// item on every one of them), the others run on one block each, placed by
+// longest-processing-time-first on the least loaded block.
+// ---------------------------------------------------------------------------
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <queue>
+#include <unordered_map>
+#include <vector>
+
+namespace ffg {
+namespace {
+
+struct PlanHost {
+    int nb = 0;
+    std::vector<int> group;           // per job
+    std::vector<int> first;           // nb + 1
+    std::vector<int2> items;          // (job, rank)
+    std::vector<int> graph_of_job;    // job -> distinct graph index
+    std::vector<const ffg_graph *> graphs;
+};
+
+double est_iters(double alpha) { return std::log(1.0 / (1 << 21)) / std::log(alpha); }
+
+ffg_status check_job(const ffg_pr_job &j, int idx) {
+    const ffg_graph *g = j.g;
+    if (!g || g->n_nodes <= 0 || !g->in_ptr || !g->outdeg || (g->n_edges > 0 && !g->in_idx) ||
+        !j.ranks)
+        return set_error("job %d: graph empty or incomplete, or ranks NULL", idx),
+               FFG_ERR_INVALID_ARG;
+    if (g->n_nodes >= (int64_t(1) << 31))
+        return set_error("job %d: too many nodes", idx), FFG_ERR_OVERFLOW;
+    if (!(j.damping > 0.0 && j.damping < 1.0) || !(j.tol >= 0.0) || j.max_iter < 1 ||
+        (j.init & ~FFG_INIT_RANKS))
+        return set_error("job %d: bad damping, tol, max_iter or init", idx), FFG_ERR_INVALID_ARG;
+    return FFG_OK;
+}
+
+ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, PlanHost &P) {
+    // distinct graphs (jobs may share one)
+    std::unordered_map<const int64_t *, int> gidx;
+    P.graph_of_job.resize(n_jobs);
+    std::vector<double> cost(n_jobs);
+    int64_t useful = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        FFG_TRY(check_job(jobs[j], j));
+        const ffg_graph *g = jobs[j].g;
+        auto it = gidx.find(g->in_ptr);
+        if (it == gidx.end()) {
+            it = gidx.emplace(g->in_ptr, static_cast<int>(P.graphs.size())).first;
+            P.graphs.push_back(g);
+        } else if (P.graphs[it->second]->n_nodes != g->n_nodes ||
+                   P.graphs[it->second]->n_edges != g->n_edges) {
+            return set_error("jobs %d: two graphs share in_ptr with different sizes", j),
+                   FFG_ERR_INVALID_ARG;
+        }
+        P.graph_of_job[j] = it->second;
+        cost[j] = double(g->n_edges + kRowCost * g->n_nodes) * est_iters(jobs[j].damping);
+        const int64_t tiles = (g->n_nodes + 31) / 32;
+        useful += std::max<int64_t>(1, (tiles + 4 * kWarps - 1) / (4 * kWarps));
+    }
+    const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(nb_max, useful)));
+    P.nb = nb;
+    const double total = std::accumulate(cost.begin(), cost.end(), 0.0);
+    const double share = total / nb;
+    std::vector<int> order(n_jobs);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    P.group.assign(n_jobs, 1);
+    std::vector<std::vector<int2>> per_block(nb);
+    std::vector<double> load(nb, 0.0);
+    int next_block = 0;
+    std::vector<int> small;
+    for (int j : order) {
+        const int64_t tiles = (jobs[j].g->n_nodes + 31) / 32;
+        int k = static_cast<int>(std::floor(cost[j] / share));
+        k = static_cast<int>(std::min<int64_t>(k, std::max<int64_t>(1, tiles / kWarps)));
+        if (k >= 2 && next_block + k <= nb) {
+            P.group[j] = k;
+            for (int r = 0; r < k; ++r) {
+                per_block[next_block + r].push_back(make_int2(j, r));
+                load[next_block + r] += cost[j] / k;
+            }
+            next_block += k;
+        } else {
+            small.push_back(j);
+        }
+    }
+    // one-block jobs, longest first, onto the least loaded block
+    using Slot = std::pair<double, int>;
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+    for (int b = 0; b < nb; ++b) heap.push({load[b], b});
+    for (int j : small) {
+        Slot s = heap.top();
+        heap.pop();
+        per_block[s.second].push_back(make_int2(j, 0));
+        s.first += cost[j];
+        heap.push(s);
+    }
+    P.first.assign(nb + 1, 0);
+    P.items.clear();
+    for (int b = 0; b < nb; ++b) {
+        P.first[b] = static_cast<int>(P.items.size());
+        for (const int2 &it : per_block[b]) P.items.push_back(it);
+    }
+    P.first[nb] = static_cast<int>(P.items.size());
+    return FFG_OK;
+}
+
+struct BatchWs {
+    JobDev *jobs;
+    GraphDev *graphs;
+    int *first;
+    int2 *items;
+    PrCtl *ctl;
+    size_t bytes;
+};
+
+// Workspace of a plan: tables, then per job ctl / partials / w buffers, then
+// per distinct graph the layout and tile metadata.  host_jobs / host_graphs
+// (if non-NULL) receive the device pointers of every job and graph.
+BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
+                    const PlanHost &P, std::vector<JobDev> *host_jobs,
+                    std::vector<GraphDev> *host_graphs) {
+    Carver c(base);
+    BatchWs w;
+    w.jobs = c.take<JobDev>(n_jobs);
+    w.graphs = c.take<GraphDev>(P.graphs.size());
+    w.first = c.take<int>(P.nb + 1);
+    w.items = c.take<int2>(std::max<size_t>(1, P.items.size()));
+    w.ctl = c.take<PrCtl>(n_jobs);
+    std::vector<GraphDev> gd(P.graphs.size());
+    int64_t tile0 = 0;
+    for (size_t k = 0; k < P.graphs.size(); ++k) {
+        const ffg_graph *g = P.graphs[k];
+        gd[k].in_ptr = g->in_ptr;
+        gd[k].in_idx = g->in_idx;
+        gd[k].layout = c.take<uint32_t>(size_t(layout_chunks(g->n_nodes, g->n_edges)) * 32);
+        gd[k].meta = c.take<uint8_t>(size_t((g->n_nodes + 31) / 32));
+        gd[k].n = g->n_nodes;
+        gd[k].tile0 = tile0;
+        tile0 += (g->n_nodes + 31) / 32;
+    }
+    std::vector<JobDev> jd(n_jobs);
+    for (int j = 0; j < n_jobs; ++j) {
+        const ffg_graph *g = jobs[j].g;
+        const GraphDev &G = gd[P.graph_of_job[j]];
+        JobDev &J = jd[j];
+        J.in_ptr = g->in_ptr;
+        J.in_idx = g->in_idx;
+        J.outdeg = g->outdeg;
+        J.layout = G.layout;
+        J.meta = G.meta;
+        J.ranks = jobs[j].ranks;
+        J.w0 = c.take<char>(size_t(g->n_nodes) * elem);
+        J.w1 = c.take<char>(size_t(g->n_nodes) * elem);
+        J.partials = c.take<long long>(size_t(2) * P.group[j] * 4);
+        J.ctl = w.ctl + j;
+        J.n = g->n_nodes;
+        J.alpha = jobs[j].damping;
+        J.tol = jobs[j].tol;
+        J.max_iter = jobs[j].max_iter;
+        J.init = (jobs[j].init & FFG_INIT_RANKS) ? 1 : 0;
+        J.group = P.group[j];
+        J.pad = 0;
+    }
+    w.bytes = c.off;
+    if (host_jobs) *host_jobs = std::move(jd);
+    if (host_graphs) *host_graphs = std::move(gd);
+    return w;
+}
+
+ffg_status batch_blocks(ffg_prec prec, int *nb_max) {
+    int per_sm = 0, sms = 0;
+    if (prec == FFG_F64) FFG_TRY(kernel_config<double>(&per_sm, &sms));
+    else FFG_TRY(kernel_config<float>(&per_sm, &sms));
+    *nb_max = std::min(kMaxBlocks, sms * per_sm);
+    return FFG_OK;
+}
+
+}  // namespace
+}  // namespace ffg
+
+extern "C" size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs,
+                                                 ffg_prec prec) {
+    clear_error();
+    if (!jobs || n_jobs < 1 || (prec != FFG_F64 && prec != FFG_F32)) return 0;
+    int nb_max = 0;
+    if (batch_blocks(prec, &nb_max) != FFG_OK) return 0;
+    PlanHost P;
+    if (make_plan(jobs, n_jobs, nb_max, P) != FFG_OK) return 0;
+    return carve_batch(nullptr, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, nullptr, nullptr).bytes;
+}
+
+extern "C" ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec,
+                                          void *workspace, size_t ws_bytes, ffg_pr_batch *plan,
+                                          void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!jobs || n_jobs < 1 || !plan || !workspace)
+        return set_error("jobs, plan and workspace must be non-NULL, n_jobs >= 1"),
+               FFG_ERR_INVALID_ARG;
+    if (prec != FFG_F64 && prec != FFG_F32)
+        return set_error("unknown precision %d", (int)prec), FFG_ERR_INVALID_ARG;
+    if (!aligned256(workspace))
+        return set_error("workspace not 256-byte aligned"), FFG_ERR_INVALID_ARG;
+    int nb_max = 0;
+    FFG_TRY(batch_blocks(prec, &nb_max));
+    PlanHost P;
+    FFG_TRY(make_plan(jobs, n_jobs, nb_max, P));
+    std::vector<JobDev> jd;
+    std::vector<GraphDev> gd;
+    BatchWs w = carve_batch(workspace, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, &jd, &gd);
+    if (ws_bytes < w.bytes)
+        return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
+    FFG_TRY(check_cuda(cudaMemcpyAsync(w.jobs, jd.data(), sizeof(JobDev) * jd.size(),
+                                       cudaMemcpyHostToDevice, stream), "upload jobs"));
+    FFG_TRY(check_cuda(cudaMemcpyAsync(w.graphs, gd.data(), sizeof(GraphDev) * gd.size(),
+                                       cudaMemcpyHostToDevice, stream), "upload graphs"));
+    FFG_TRY(check_cuda(cudaMemcpyAsync(w.first, P.first.data(), sizeof(int) * P.first.size(),
+                                       cudaMemcpyHostToDevice, stream), "upload plan"));
+    if (!P.items.empty())
+        FFG_TRY(check_cuda(cudaMemcpyAsync(w.items, P.items.data(), sizeof(int2) * P.items.size(),
+                                           cudaMemcpyHostToDevice, stream), "upload plan"));
+    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync plan upload"));
+    int64_t tiles = 0;
+    for (const ffg_graph *g : P.graphs) tiles += (g->n_nodes + 31) / 32;
+    plan->prec = prec;
+    plan->n_jobs = n_jobs;
+    plan->n_graphs = static_cast<int32_t>(P.graphs.size());
+    plan->n_blocks = P.nb;
+    plan->total_tiles = tiles;
+    plan->jobs = w.jobs;
+    plan->graphs = w.graphs;
+    plan->items = w.items;
+    plan->first = w.first;
+    plan->ctl = w.ctl;
+    return FFG_OK;
+}
+
+extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!plan || plan->n_jobs < 1 || !plan->jobs || !plan->ctl || plan->n_blocks < 1)
+        return set_error("plan is empty"), FFG_ERR_INVALID_ARG;
+    const ffg_prec prec = static_cast<ffg_prec>(plan->prec);
+    int nb_max = 0;
+    FFG_TRY(batch_blocks(prec, &nb_max));
+    if (plan->n_blocks > nb_max)
+        return set_error("plan made for %d blocks, %d fit", plan->n_blocks, nb_max),
+               FFG_ERR_INVALID_ARG;
+    FFG_TRY(check_cuda(cudaMemsetAsync(plan->ctl, 0, sizeof(PrCtl) * plan->n_jobs, stream),
+                       "memset"));
+    int dev = 0, sms = 0;
+    FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
+    FFG_TRY(check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
+    const int64_t want = (plan->total_tiles + kLayoutThreads / 32 - 1) / (kLayoutThreads / 32);
+    const int64_t cap = int64_t(sms) * 32;
+    k_pr_layout_batch<<<static_cast<unsigned>(std::max<int64_t>(1, std::min(want, cap))),
+                        kLayoutThreads, 0, stream>>>(static_cast<const GraphDev *>(plan->graphs),
+                                                     plan->n_graphs, plan->total_tiles);
+    count_launch();
+    FFG_TRY(check_launch("k_pr_layout_batch"));
+    JobDev none{};
+    const JobDev *jobs = static_cast<const JobDev *>(plan->jobs);
+    const int2 *items = static_cast<const int2 *>(plan->items);
+    const int *first = static_cast<const int *>(plan->first);
+    if (prec == FFG_F64) return launch_pr<double>(jobs, items, first, plan->n_blocks, none, stream);
+    return launch_pr<float>(jobs, items, first, plan->n_blocks, none, stream);
+}
+
+extern "C" ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *iters_out,
+                                           double *residual_out, int32_t *status_out,
+                                           void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!plan || plan->n_jobs < 1 || !plan->ctl) return set_error("plan is empty"), FFG_ERR_INVALID_ARG;
+    std::vector<PrCtl> h(plan->n_jobs);
+    FFG_TRY(check_cuda(cudaMemcpyAsync(h.data(), plan->ctl, sizeof(PrCtl) * h.size(),
+                                       cudaMemcpyDeviceToHost, stream), "read batch results"));
+    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync batch results"));
+    ffg_status worst = FFG_OK;
+    for (int j = 0; j < plan->n_jobs; ++j) {
+        const ffg_status st = h[j].status ? static_cast<ffg_status>(h[j].status)
+                                          : (h[j].converged ? FFG_OK : FFG_ERR_NOT_CONVERGED);
+        if (iters_out) iters_out[j] = h[j].iters;
+        if (residual_out) residual_out[j] = h[j].residual;
+        if (status_out) status_out[j] = st;
+        if (st == FFG_ERR_TIMEOUT || (st != FFG_OK && worst == FFG_OK)) worst = st;
+    }
+    if (worst == FFG_ERR_TIMEOUT) set_error("pagerank batch: a bounded device wait timed out");
+    return worst;
 }

@@ -269,3 +269,50 @@ def test_prepared_layout_and_damping_sweep():
     for alpha in (0.5, 0.7, 0.85, 0.95):
         x, it, res, conv = ffg.pagerank(g, alpha, 1e-13, prec=ffg.F64, ws=ws, prepared=True)
         assert conv and np.abs(_np(x) - oracle.pagerank_exact(og, alpha)).sum() <= F64_L1
+
+
+def test_batched_pagerank_matches_oracle():
+    """Many jobs of uneven size, shared graphs, several dampings, one launch."""
+    specs, refs = [], []
+    cases = [(fi.single_small(), 1), (fi.pnpoly_space(), 2), (fi.conv_mi50_space(), 3),
+             (fi.gemm_space(), 4)] + [(sp, 10 + k) for k, sp in
+                                      enumerate(fi.tiny_spaces(6, seed0=13000, max_raw=3000))]
+    graphs = []
+    for spec, seed in cases:
+        f = fi.runtimes(spec, seed, fail_frac=0.7 if spec.name == "gemm" else 0.05)
+        for nbh in ("hamming", "adjacent"):
+            og = oracle.build(spec, f, NBH[nbh][1])
+            g, fd = run_build(spec, f, nbh)
+            graphs.append((g, og))
+    for k, (g, og) in enumerate(graphs):
+        for alpha in ((0.5, 0.85) if k % 2 else (0.95,)):
+            specs.append((g, alpha))
+            refs.append(oracle.pagerank_exact(og, alpha))
+    for prec, bar in ((ffg.F64, F64_L1), (ffg.F32, 1e-5)):
+        batch = ffg.PageRankBatch(specs, prec=prec, tol=1e-12)
+        for _ in range(2):          # a plan can be run again
+            batch.run()
+            it, res, st = batch.query()
+            assert (st == ffg.FFG_OK).all(), st
+            for x, xe in zip(batch.ranks, refs):
+                assert np.abs(_np(x).astype(np.float64) - xe).sum() <= bar
+
+
+def test_batched_pagerank_large_jobs_share_blocks():
+    """A large job (several dedicated blocks) next to small ones."""
+    spec = fi.single_large()
+    f = fi.runtimes(spec, 1)
+    og = oracle.build(spec, f, oracle.ADJACENT)
+    g, fd = run_build(spec, f, "adjacent")
+    small = fi.single_small()
+    fs = fi.runtimes(small, 2)
+    ogs = oracle.build(small, fs, oracle.HAMMING)
+    gs, _ = run_build(small, fs, "hamming")
+    batch = ffg.PageRankBatch([(g, 0.85), (gs, 0.85), (gs, 0.6)], prec=ffg.F64, tol=1e-12)
+    assert batch.plan.n_blocks > 3
+    batch.run()
+    it, res, st = batch.query()
+    assert (st == 0).all()
+    assert np.abs(_np(batch.ranks[0]) - oracle.pagerank_exact(og, 0.85)).sum() <= F64_L1
+    assert np.abs(_np(batch.ranks[1]) - oracle.pagerank_exact(ogs, 0.85)).sum() <= F64_L1
+    assert np.abs(_np(batch.ranks[2]) - oracle.pagerank_exact(ogs, 0.6)).sum() <= F64_L1
