@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--impl", default="ffg", choices=["ffg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -348,6 +349,11 @@ def run_gpu(args):
         cpu = {"value": u / s, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": ORACLE_SAMPLE + f" ({s:.1f} s)"}
 
+    batched = sweep = None
+    if not args.no_batched:
+        batched = run_batched(dev, stream, steps=max(3, args.steps // 10), warmup=1)
+        sweep = run_sweep(dev, stream, steps=max(3, args.steps // 10), warmup=1)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": units32_all / (ms32_all / 1e3), "unit": UNIT,
@@ -372,6 +378,8 @@ def run_gpu(args):
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes": bytes_launch,
                          "launch_ms": statistics.mean(durs)},
+            "batched": batched,
+            "sweep": sweep,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -381,6 +389,143 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+BATCH_P = [0.01, 0.02, 0.05, 0.10, 0.20]
+
+
+def _build_all(ffg, spaces, fits, nbh, graphs=None, wss=None, stream=None):
+    """FFGs of many spaces (count + fill each); allocates on the first call."""
+    sh = stream.cuda_stream
+    if graphs is None:
+        graphs = [ffg.build_graph(sp, f, nbh) for sp, f in zip(spaces, fits)]
+        wss = [ffg.workspace(ffg.ffg_workspace_bytes(sp, nbh)) for sp in spaces]
+        return graphs, wss
+    for sp, f, g, ws in zip(spaces, fits, graphs, wss):
+        need = ffg.ffg_workspace_bytes(sp, nbh)
+        g0 = ffg.ffg_graph()
+        st = ffg.ffg_build_count(sp, f.data_ptr(), nbh, 1e10, g0, ws.data_ptr(), need, sh)
+        assert st == 0 and g0.n_edges == g.n_edges, st
+        g.c.f_opt, g.c.n_minima = g0.f_opt, g0.n_minima
+        st = ffg.ffg_build_fill(sp, f.data_ptr(), nbh, 1e10, g.c, ws.data_ptr(), need, sh)
+        assert st == 0, st
+    return graphs, wss
+
+
+def run_batched(dev, stream, steps, warmup):
+    """234 spaces (26 kernel templates x 9 fitness seeds, sizes log-uniform,
+    3/30/70 % failures): per step build every Hamming FFG, one batched FP32
+    PageRank launch, batched C_p at 1/2/5/10/20 %.  Compared with the plain
+    FP64 per-space solve of the same graphs."""
+    import torch
+    import ffg_inputs as fi
+    import paper_2210_01465_gb300 as ffg
+    work = fi.batch_workload()
+    spaces = [ffg.Space.from_spec(sp) for sp, _, _ in work]
+    fits = [fi.runtimes_torch(sp, seed, fail, device=dev) for sp, seed, fail in work]
+    graphs, wss = _build_all(ffg, spaces, fits, ffg.HAMMING, stream=stream)
+    batch = ffg.PageRankBatch([(g, DAMPING) for g in graphs], prec=ffg.F32, tol=TOL)
+    E = np.array([g.n_edges for g in graphs], dtype=np.float64)
+    N = np.array([g.n_nodes for g in graphs], dtype=np.float64)
+
+    def step(record):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        _build_all(ffg, spaces, fits, ffg.HAMMING, graphs, wss, stream)
+        e1.record(stream)
+        batch.run()
+        e2.record(stream)
+        it, res, st = batch.query()
+        assert (st == 0).all(), st
+        ffg.centrality_many([(g, f, x) for g, f, x in zip(graphs, fits, batch.ranks)], BATCH_P)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e3.record(stream)
+        e3.synchronize()
+        if record is not None:
+            record.append((e0.elapsed_time(e3), e0.elapsed_time(e1), e1.elapsed_time(e2), it.copy()))
+
+    for _ in range(warmup):
+        step(None)
+    recs = []
+    for _ in range(steps):
+        torch.cuda.synchronize(dev)
+        step(recs)
+    ms = float(np.mean([r[0] for r in recs]))
+    pr_ms = float(np.mean([r[2] for r in recs]))
+    iters = recs[-1][3].astype(np.float64)
+    units = float((E * iters).sum())
+    # plain FP64, one solve per space
+    t64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    units64 = 0.0
+    t64[0].record(stream)
+    for g in graphs:
+        x, it, res, conv = ffg.pagerank(g, DAMPING, TOL, prec=ffg.F64)
+        units64 += g.n_edges * it
+    t64[1].record(stream)
+    t64[1].synchronize()
+    ms64 = t64[0].elapsed_time(t64[1])
+    return {"workload": "234 spaces (26 templates incl. the paper's convolution, GEMM and "
+                        "PnPoly spaces x 9 seeds), Hamming FFGs, batched FP32 PageRank in one "
+                        "persistent launch, batched C_p at 1/2/5/10/20 %",
+            "spaces": len(graphs), "nodes": int(N.sum()), "edges": int(E.sum()),
+            "value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "spaces_per_s": len(graphs) / (ms / 1e3), "pagerank_ms": pr_ms,
+            "pagerank_edges_iters_per_s": units / (pr_ms / 1e3),
+            "plain_f64_pagerank_ms": ms64,
+            "plain_f64_edges_iters_per_s": units64 / (ms64 / 1e3),
+            "batched_f32_vs_plain_f64_speedup": (units / (pr_ms / 1e3)) / (units64 / (ms64 / 1e3)),
+            "blocks": int(batch.plan.n_blocks)}
+
+
+def run_sweep(dev, stream, steps, warmup):
+    """64 spaces x {Hamming, adjacent} x damping {0.5, 0.7, 0.85, 0.95} = 512
+    FP32 PageRank solves per step, replayed from one captured CUDA graph."""
+    import torch
+    import ffg_inputs as fi
+    import paper_2210_01465_gb300 as ffg
+    specs = fi.sweep_spaces()
+    spaces = [ffg.Space.from_spec(sp) for sp in specs]
+    fits = [fi.runtimes_torch(sp, 500 + k, 0.03, device=dev) for k, sp in enumerate(specs)]
+    graphs = []
+    for nbh in (ffg.HAMMING, ffg.ADJACENT):
+        graphs += _build_all(ffg, spaces, fits, nbh, stream=stream)[0]
+    dampings = (0.5, 0.7, 0.85, 0.95)
+    batch = ffg.PageRankBatch([(g, a) for g in graphs for a in dampings], prec=ffg.F32, tol=TOL)
+    E = np.array([g.n_edges for g in graphs for _ in dampings], dtype=np.float64)
+    captured = True
+    try:
+        cg = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            batch.run()                      # warm the plan outside capture
+            with torch.cuda.graph(cg, stream=side):
+                batch.run()
+        stream.wait_stream(side)
+        replay = cg.replay
+    except Exception:
+        captured = False
+        replay = batch.run
+    for _ in range(warmup):
+        replay()
+        batch.query()
+    ms = []
+    for _ in range(steps):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        replay()
+        e1.record(stream)
+        it, res, st = batch.query()
+        assert (st == 0).all(), st
+        ms.append(e0.elapsed_time(e1))
+    m = float(np.mean(ms))
+    units = float((E * it).sum())
+    return {"workload": "64 spaces x 2 neighbourhoods x damping {0.5,0.7,0.85,0.95} = 512 "
+                        "FP32 PageRank solves in one batch",
+            "solves": len(E), "cuda_graph": captured, "ms_per_step": m,
+            "solves_per_s": len(E) / (m / 1e3), "value": units / (m / 1e3), "unit": UNIT,
+            "blocks": int(batch.plan.n_blocks)}
 
 
 def main():

@@ -335,6 +335,8 @@ def sized_random_space(seed: int, target_raw: int, max_radix: int = 12) -> Space
     total = 1
     while total < target_raw and len(vals) < 16:
         rem = target_raw / total
+        if rem < 1.5 and len(vals) >= 3:
+            break
         uu = float(uniform01(seed, 40 + stream, np.arange(2))[0])
         k = int(min(max_radix, max(2, round(2 + uu * (max_radix - 2)))))
         if rem < k * 1.5 or len(vals) == 15:
@@ -349,10 +351,29 @@ def sized_random_space(seed: int, target_raw: int, max_radix: int = 12) -> Space
         total *= k
         stream += 1
     n = len(vals)
-    base = random_space(seed, max(n, 2), n_clauses=2)
-    clauses = tuple(c for c in base.clauses if all(i < n for i in c.a + c.b)) if n >= 2 else ()
+    # Clauses that the configuration of all list minima satisfies (so the
+    # space is never empty): a product upper bound no smaller than the
+    # product of the minima, and divisibility by a parameter whose list
+    # starts at 1.
+    cu = uniform01(seed, 90, np.arange(16))
+    clauses = []
+    if n >= 2:
+        i = int(cu[0] * n)
+        j = (i + 1 + int(cu[1] * (n - 1))) % n
+        lo = min(vals[i]) * min(vals[j])
+        hi = max(vals[i]) * max(vals[j])
+        if hi > lo:
+            frac = 0.4 + 0.4 * cu[2]
+            bound = int(round(max(lo, 1) * (hi / max(lo, 1)) ** frac))
+            clauses.append(Clause("prod_le", tuple(sorted((i, j))), (), max(bound, lo)))
+        divs = [k for k in range(n) if vals[k][0] == 1 and len(vals[k]) > 1]
+        if divs and cu[3] < 0.6:
+            d = divs[int(cu[4] * len(divs))]
+            a = (d + 1 + int(cu[5] * (n - 1))) % n
+            if a != d:
+                clauses.append(Clause("divides", (a,), (d,)))
     return SpaceSpec(f"sized_{seed}_{target_raw}", tuple(f"p{i}" for i in range(n)),
-                     tuple(vals), clauses)
+                     tuple(vals), tuple(clauses))
 
 
 def tiny_spaces(count: int, seed0: int = 1000, max_raw: int = 5000):
@@ -366,3 +387,129 @@ def tiny_spaces(count: int, seed0: int = 1000, max_raw: int = 5000):
             out.append(sp)
         s += 1
     return out
+
+
+# --------------------------------------------------------------------------
+# batched workloads (many spaces of uneven size) and a device-side runtime
+# model for them
+# --------------------------------------------------------------------------
+
+def _loguniform(seed: int, stream: int, count: int, lo: float, hi: float) -> np.ndarray:
+    u = uniform01(seed, stream, np.arange(count))
+    return np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))
+
+
+def batch_templates(count: int = 26, seed: int = 7, lo: float = 1.5e3, hi: float = 6e6):
+    """The paper's convolution, GEMM and PnPoly spaces plus seeded random
+    templates whose raw size is drawn log-uniformly in [lo, hi] (the valid
+    count is whatever the template's clauses leave)."""
+    out = [conv_space(), gemm_space(), pnpoly_space()]
+    targets = _loguniform(seed, 1, count, lo, hi)
+    k = 0
+    while len(out) < count:
+        sp = sized_random_space(seed * 1000 + k, int(targets[len(out)]))
+        k += 1
+        if 3 <= sp.n_params <= 10:
+            out.append(SpaceSpec(f"template_{len(out)}", sp.names, sp.values, sp.clauses))
+    return out
+
+
+FAIL_LEVELS = (0.03, 0.30, 0.70)
+
+
+def batch_workload(n_templates: int = 26, n_seeds: int = 9):
+    """(space, seed, fail_frac) for every template x fitness seed; the failure
+    fraction cycles over 3 %, 30 % and 70 % by template."""
+    jobs = []
+    for t, sp in enumerate(batch_templates(n_templates)):
+        for s in range(n_seeds):
+            jobs.append((sp, 100 * t + s + 1, FAIL_LEVELS[t % 3]))
+    return jobs
+
+
+def sweep_spaces(count: int = 64, seed: int = 11, lo: float = 1.5e4, hi: float = 3e6):
+    """Random spaces with raw sizes log-uniform in [lo, hi]."""
+    targets = _loguniform(seed, 2, count, lo, hi)
+    out = []
+    k = 0
+    while len(out) < count:
+        sp = sized_random_space(seed * 1000 + k, int(targets[len(out)]))
+        k += 1
+        if 3 <= sp.n_params <= 10:
+            out.append(SpaceSpec(f"sweep_{len(out)}", sp.names, sp.values, sp.clauses))
+    return out
+
+
+def _mix64_t(z):
+    """SplitMix64 finaliser on int64 tensors (two's-complement wrap-around,
+    logical shifts emulated with masks)."""
+    import torch
+    m30 = (1 << 34) - 1
+    m27 = (1 << 37) - 1
+    m31 = (1 << 33) - 1
+    c1 = torch.tensor(0xBF58476D1CE4E5B9 - (1 << 64), dtype=torch.int64, device=z.device)
+    c2 = torch.tensor(0x94D049BB133111EB - (1 << 64), dtype=torch.int64, device=z.device)
+    z = z ^ ((z >> 30) & m30)
+    z = z * c1
+    z = z ^ ((z >> 27) & m27)
+    z = z * c2
+    return z ^ ((z >> 31) & m31)
+
+
+def _s64(v: int) -> int:
+    v &= _M64
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def uniform01_torch(seed: int, stream: int, n: int, device):
+    """The counter-based U[0,1) stream of ``uniform01`` evaluated on a device."""
+    import torch
+    idx = torch.arange(1, n + 1, dtype=torch.int64, device=device)
+    gamma = torch.tensor(_s64(_GAMMA), dtype=torch.int64, device=device)
+    z = torch.tensor(_s64(_base(seed, stream)), dtype=torch.int64, device=device) + idx * gamma
+    h = _mix64_t(z)
+    return ((h >> 11) & ((1 << 53) - 1)).to(torch.float64) * (1.0 / 9007199254740992.0)
+
+
+def runtimes_torch(spec: SpaceSpec, seed: int, fail_frac: float = 0.03, noise_sd: float = 0.05,
+                   device="cuda", n_bumps: int = 3):
+    """``runtimes`` evaluated with torch on ``device`` (float64).  Same model
+    and same counter streams; transcendental functions may differ from
+    numpy's in the last bits, so use one or the other consistently."""
+    import torch
+    n = spec.n_params
+    shape = spec.radix
+    z = [torch.as_tensor(_coordinate(v), device=device) for v in spec.values]
+    a = _uniform_n(seed, 1, n, 0.2, 1.0)
+    m = _uniform_n(seed, 2, n, -0.6, 0.6)
+    bij = _uniform_n(seed, 3, n * n, -0.15, 0.15).reshape(n, n)
+    h = _uniform_n(seed, 4, n_bumps, 0.3, 0.8)
+    sig = _uniform_n(seed, 5, n_bumps, 0.15, 0.35)
+    mu = _uniform_n(seed, 6, n_bumps * n, -1.0, 1.0).reshape(n_bumps, n)
+
+    def axis(i, vec):
+        s = [1] * n
+        s[i] = vec.shape[0]
+        return vec.reshape(s)
+
+    g = torch.zeros(shape, dtype=torch.float64, device=device)
+    for i in range(n):
+        g += axis(i, float(a[i]) * (z[i] - float(m[i])) ** 2)
+    for i in range(n):
+        for j in range(i + 1, n):
+            g += float(bij[i, j]) * axis(i, z[i] - float(m[i])) * axis(j, z[j] - float(m[j]))
+    for k in range(n_bumps):
+        bump = torch.ones(shape, dtype=torch.float64, device=device)
+        for i in range(n):
+            bump = bump * axis(i, torch.exp(-((z[i] - float(mu[k, i])) ** 2) /
+                                            (2.0 * float(sig[k]) ** 2)))
+        g -= float(h[k]) * bump
+    g = g.reshape(-1)
+    R = spec.n_raw
+    u1 = uniform01_torch(seed, 101, R, device)
+    u2 = uniform01_torch(seed, 102, R, device)
+    eps = noise_sd * torch.sqrt(-2.0 * torch.log1p(-u1)) * torch.cos(2.0 * math.pi * u2)
+    rt = torch.exp(1.0 + g + eps)
+    if fail_frac > 0:
+        rt[uniform01_torch(seed, 103, R, device) < fail_frac] = FAIL_RUNTIME
+    return rt

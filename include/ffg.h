@@ -270,6 +270,24 @@ ffg_status centrality_proportion(const ffg_graph *g, const double *fitness_raw,
                                  int32_t n_p, double *cp_out, void *workspace, size_t ws_bytes,
                                  void *stream);
 
+/* Batched C_p: the same quantity for n_jobs graphs at once (one launch for
+ * the sums of every job, one read-back).  Job j: g (host struct with DEVICE
+ * arrays, host fields from ffg_build_count), fitness_raw and ranks (DEVICE,
+ * precision `prec`).  cp_out (HOST) is n_jobs x n_p, row-major.  A job
+ * whose graph has no local minimum gets NaN and the call returns
+ * FFG_ERR_EMPTY (the other rows are valid).  Synchronises `stream` once. */
+typedef struct {
+    const ffg_graph *g;
+    const double *fitness_raw;
+    const void *ranks;
+} ffg_cp_job;
+
+size_t centrality_batch_workspace_bytes(int32_t n_jobs, int32_t n_p);
+
+ffg_status centrality_batch(const ffg_cp_job *jobs, int32_t n_jobs, ffg_prec prec,
+                            const double *p, int32_t n_p, double *cp_out, void *workspace,
+                            size_t ws_bytes, void *stream);
+
 /* ---- diagnostics ---- */
 const char *ffg_status_str(ffg_status s);
 /* Detail of the last error raised on the calling thread ("" if none). */

@@ -75,13 +75,18 @@ class ffg_pr_batch(C.Structure):
                 ("ctl", C.c_void_p)]
 
 
+class ffg_cp_job(C.Structure):
+    _fields_ = [("g", C.POINTER(ffg_graph)), ("fitness_raw", C.c_void_p), ("ranks", C.c_void_p)]
+
+
 # names of include/ffg.h's entry points (the ABI test checks the header)
 ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
                 "pagerank_workspace_bytes", "pagerank_prepare", "pagerank_solve",
                 "pagerank_solve_static",
                 "pagerank_query", "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
                 "pagerank_batch_run", "pagerank_batch_query",
-                "centrality_workspace_bytes", "centrality_proportion", "ffg_status_str",
+                "centrality_workspace_bytes", "centrality_proportion",
+                "centrality_batch_workspace_bytes", "centrality_batch", "ffg_status_str",
                 "ffg_last_error", "ffg_launch_count")
 
 _lib = None
@@ -120,6 +125,9 @@ def load(path: str | None = None):
     lib.centrality_workspace_bytes.argtypes = [i32]
     lib.centrality_workspace_bytes.restype = sz
     lib.centrality_proportion.argtypes = [P(ffg_graph), vp, vp, C.c_int, vp, i32, vp, vp, sz, vp]
+    lib.centrality_batch_workspace_bytes.argtypes = [i32, i32]
+    lib.centrality_batch_workspace_bytes.restype = sz
+    lib.centrality_batch.argtypes = [P(ffg_cp_job), i32, C.c_int, vp, i32, vp, vp, sz, vp]
     lib.ffg_status_str.argtypes = [C.c_int]
     lib.ffg_status_str.restype = C.c_char_p
     lib.ffg_last_error.argtypes = []
@@ -368,6 +376,35 @@ def pagerank(g: Graph, damping: float = 0.85, tol: float = 1e-12, max_iter: int 
                                  ws.data_ptr(), need, True, _stream_handle(stream))
     _check(st, "pagerank_solve", ok=(FFG_OK, FFG_ERR_NOT_CONVERGED))
     return ranks, it, res, st == FFG_OK
+
+
+def centrality_batch_workspace_bytes(n_jobs: int, n_p: int) -> int:
+    return int(load().centrality_batch_workspace_bytes(int(n_jobs), int(n_p)))
+
+
+def centrality_batch(jobs, prec: int, p, cp_out, ws: int, ws_bytes: int, stream: int = 0) -> int:
+    pv = np.ascontiguousarray(p, dtype=np.float64)
+    assert cp_out.dtype == np.float64 and cp_out.size >= len(jobs) * len(pv)
+    return int(load().centrality_batch(jobs, len(jobs), int(prec), C.c_void_p(pv.ctypes.data),
+                                       len(pv), C.c_void_p(cp_out.ctypes.data), C.c_void_p(ws),
+                                       int(ws_bytes), C.c_void_p(stream)))
+
+
+def centrality_many(specs, p, stream=None) -> np.ndarray:
+    """C_p of many graphs at once; ``specs``: list of (Graph, fitness, ranks)."""
+    torch = _torch()
+    jobs = (ffg_cp_job * len(specs))()
+    for k, (g, fit, x) in enumerate(specs):
+        jobs[k].g = C.pointer(g.c)
+        jobs[k].fitness_raw = fit.data_ptr()
+        jobs[k].ranks = x.data_ptr()
+    prec = F64 if specs[0][2].dtype == torch.float64 else F32
+    need = centrality_batch_workspace_bytes(len(specs), len(p))
+    ws = workspace(need, specs[0][2].device)
+    out = np.zeros((len(specs), len(p)), dtype=np.float64)
+    _check(centrality_batch(jobs, prec, p, out, ws.data_ptr(), need, _stream_handle(stream)),
+           "centrality_batch")
+    return out
 
 
 class PageRankBatch:

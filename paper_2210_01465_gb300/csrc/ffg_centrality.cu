@@ -199,3 +199,182 @@ extern "C" ffg_status centrality_proportion(const ffg_graph *g, const double *fi
     for (int k = 0; k < n_p; ++k) cp_out[order[k]] = host_neumaier(h, k + 1) / sl;
     return FFG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// batched C_p: one launch for the bucket sums of every job (blockIdx.y = job,
+// kCpBatchBlocks blocks per job), one launch for the per-job final sums, one
+// read-back.
+// ---------------------------------------------------------------------------
+namespace ffg {
+namespace {
+
+constexpr int kCpBatchBlocks = 32;
+
+struct CpJobDev {
+    const uint8_t *is_min;
+    const int64_t *node_raw;
+    const double *fit;
+    const void *ranks;
+    int64_t n;
+    Thresholds th;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kCpThreads) k_cp_partial_batch(const CpJobDev *__restrict__ jobs,
+                                                                  double *__restrict__ partials) {
+    const CpJobDev &J = jobs[blockIdx.y];
+    const T *x = static_cast<const T *>(J.ranks);
+    double acc[kBuckets];
+    for (int b = 0; b <= J.th.n; ++b) acc[b] = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < J.n; v += stride) {
+        if (!J.is_min[v]) continue;
+        const double f = J.fit[J.node_raw[v]];
+        int b = 0;
+        while (b < J.th.n && !(f <= J.th.thr[b])) ++b;
+        acc[b] += static_cast<double>(x[v]);
+    }
+    __shared__ double red[kCpThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *out = partials + (size_t(blockIdx.y) * kCpBatchBlocks + blockIdx.x) * kBuckets * 2;
+    for (int b = 0; b <= J.th.n; ++b) {
+        double v = acc[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0, c = 0.0;
+            for (int k = 0; k < kCpThreads / 32; ++k) neumaier(s, c, red[k]);
+            out[b * 2 + 0] = s;
+            out[b * 2 + 1] = c;
+        }
+    }
+}
+
+// block j: lane-strided compensated sums of job j's block partials per bucket
+__global__ void k_cp_final_batch(const double *__restrict__ partials, int nb,
+                                 double *__restrict__ buckets) {
+    const int job = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    __shared__ double red[32][32][2];
+    const double *base = partials + size_t(job) * kCpBatchBlocks * kBuckets * 2;
+    for (int b = warp; b <= nb; b += nwarps) {
+        double s = 0.0, c = 0.0;
+        for (int k = lane; k < kCpBatchBlocks; k += 32) {
+            neumaier(s, c, base[(size_t(k) * kBuckets + b) * 2 + 0]);
+            neumaier(s, c, base[(size_t(k) * kBuckets + b) * 2 + 1]);
+        }
+        red[warp][lane][0] = s;
+        red[warp][lane][1] = c;
+        __syncwarp();
+        if (lane == 0) {
+            double ts = 0.0, tc = 0.0;
+            for (int k = 0; k < 32; ++k) {
+                neumaier(ts, tc, red[warp][k][0]);
+                neumaier(ts, tc, red[warp][k][1]);
+            }
+            buckets[size_t(job) * kBuckets + b] = ts + tc;
+        }
+        __syncwarp();
+    }
+}
+
+struct CpBatchWs {
+    CpJobDev *jobs;
+    double *partials;
+    double *buckets;
+    size_t bytes;
+};
+
+CpBatchWs carve_cp_batch(void *base, int n_jobs) {
+    Carver c(base);
+    CpBatchWs w;
+    w.jobs = c.take<CpJobDev>(n_jobs);
+    w.partials = c.take<double>(size_t(n_jobs) * kCpBatchBlocks * kBuckets * 2);
+    w.buckets = c.take<double>(size_t(n_jobs) * kBuckets);
+    w.bytes = c.off;
+    return w;
+}
+
+}  // namespace
+}  // namespace ffg
+
+extern "C" size_t centrality_batch_workspace_bytes(int32_t n_jobs, int32_t n_p) {
+    (void)n_p;
+    if (n_jobs < 1 || n_jobs > 65535) return 0;
+    return carve_cp_batch(nullptr, n_jobs).bytes;
+}
+
+extern "C" ffg_status centrality_batch(const ffg_cp_job *jobs, int32_t n_jobs, ffg_prec prec,
+                                       const double *p, int32_t n_p, double *cp_out,
+                                       void *workspace, size_t ws_bytes, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!jobs || n_jobs < 1 || n_jobs > 65535 || !p || !cp_out || !workspace)
+        return set_error("jobs, p, cp_out, workspace non-NULL and 1 <= n_jobs <= 65535"),
+               FFG_ERR_INVALID_ARG;
+    if (n_p < 1 || n_p > FFG_MAX_P)
+        return set_error("n_p must lie in [1,%d]", FFG_MAX_P), FFG_ERR_INVALID_ARG;
+    if (prec != FFG_F64 && prec != FFG_F32)
+        return set_error("unknown precision"), FFG_ERR_INVALID_ARG;
+    for (int k = 0; k < n_p; ++k)
+        if (!(p[k] >= 0.0) || p[k] == __builtin_inf())
+            return set_error("p[%d] must be finite and >= 0", k), FFG_ERR_INVALID_ARG;
+    if (!aligned256(workspace))
+        return set_error("workspace not 256-byte aligned"), FFG_ERR_INVALID_ARG;
+    CpBatchWs w = carve_cp_batch(workspace, n_jobs);
+    if (ws_bytes < w.bytes)
+        return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
+    std::vector<CpJobDev> jd(n_jobs);
+    std::vector<std::vector<int>> orders(n_jobs, std::vector<int>(n_p));
+    bool empty = false;
+    for (int j = 0; j < n_jobs; ++j) {
+        const ffg_graph *g = jobs[j].g;
+        if (!g || g->n_nodes <= 0 || !g->is_min || !g->node_raw || !jobs[j].fitness_raw ||
+            !jobs[j].ranks)
+            return set_error("job %d: graph, fitness or ranks missing", j), FFG_ERR_INVALID_ARG;
+        empty = empty || g->n_minima <= 0;
+        std::vector<double> thr(n_p);
+        for (int k = 0; k < n_p; ++k) {
+            volatile double onep = 1.0 + p[k];
+            thr[k] = g->f_opt * onep;
+        }
+        std::vector<int> &order = orders[j];
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return thr[a] < thr[b]; });
+        jd[j].is_min = g->is_min;
+        jd[j].node_raw = g->node_raw;
+        jd[j].fit = jobs[j].fitness_raw;
+        jd[j].ranks = jobs[j].ranks;
+        jd[j].n = g->n_nodes;
+        jd[j].th.n = n_p;
+        for (int k = 0; k < n_p; ++k) jd[j].th.thr[k] = thr[order[k]];
+    }
+    FFG_TRY(check_cuda(cudaMemcpyAsync(w.jobs, jd.data(), sizeof(CpJobDev) * n_jobs,
+                                       cudaMemcpyHostToDevice, stream), "upload jobs"));
+    const dim3 grid(kCpBatchBlocks, n_jobs);
+    if (prec == FFG_F64)
+        k_cp_partial_batch<double><<<grid, kCpThreads, 0, stream>>>(w.jobs, w.partials);
+    else
+        k_cp_partial_batch<float><<<grid, kCpThreads, 0, stream>>>(w.jobs, w.partials);
+    FFG_TRY(check_launch("k_cp_partial_batch"));
+    k_cp_final_batch<<<n_jobs, 32 * std::min(n_p + 1, 32), 0, stream>>>(w.partials, n_p, w.buckets);
+    count_launch(2);
+    FFG_TRY(check_launch("k_cp_final_batch"));
+    std::vector<double> h(size_t(n_jobs) * kBuckets);
+    FFG_TRY(check_cuda(cudaMemcpyAsync(h.data(), w.buckets, sizeof(double) * h.size(),
+                                       cudaMemcpyDeviceToHost, stream), "read buckets"));
+    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync centrality"));
+    for (int j = 0; j < n_jobs; ++j) {
+        const double *b = h.data() + size_t(j) * kBuckets;
+        const double sl = host_neumaier(b, n_p + 1);
+        for (int k = 0; k < n_p; ++k)
+            cp_out[size_t(j) * n_p + orders[j][k]] =
+                sl > 0.0 ? host_neumaier(b, k + 1) / sl : __builtin_nan("");
+    }
+    if (empty) return set_error("a job's graph has no local minimum (its C_p is NaN)"), FFG_ERR_EMPTY;
+    return FFG_OK;
+}

@@ -316,3 +316,18 @@ def test_batched_pagerank_large_jobs_share_blocks():
     assert np.abs(_np(batch.ranks[0]) - oracle.pagerank_exact(og, 0.85)).sum() <= F64_L1
     assert np.abs(_np(batch.ranks[1]) - oracle.pagerank_exact(ogs, 0.85)).sum() <= F64_L1
     assert np.abs(_np(batch.ranks[2]) - oracle.pagerank_exact(ogs, 0.6)).sum() <= F64_L1
+
+
+def test_batched_centrality_matches_single():
+    p = [0.0, 0.01, 0.05, 0.2, 0.1]
+    specs, refs = [], []
+    for k, spec in enumerate([fi.single_small(), fi.pnpoly_space(), fi.conv_mi50_space()]):
+        f = fi.runtimes(spec, k + 3)
+        og = oracle.build(spec, f, oracle.HAMMING)
+        g, fd = run_build(spec, f, "hamming")
+        x, *_ = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64)
+        specs.append((g, fd, x))
+        refs.append(oracle.centrality(og, oracle.pagerank_exact(og, 0.85), p))
+    out = ffg.centrality_many(specs, p)
+    for row, ref in zip(out, refs):
+        assert np.abs(row - ref).max() <= F64_CP
