@@ -300,14 +300,10 @@ def run_gpu(args):
         launches = ffg.ffg_launch_count() - l0
         return total_ms, units, recs, launches
 
+    from paper_2210_01465_gb300.multi import reduce_time_work
+
     def reduce_max_sum(ms, units):
-        if world == 1:
-            return ms, units
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
-        return float(t.item()), float(u.item())
+        return reduce_time_work(ms, units, device=dev)
 
     clocks = ClockSampler(dev.index if world == 1 else local)
     ms32, units32, recs32, launches = timed(ffg.F32, args.steps, args.warmup)
@@ -351,7 +347,8 @@ def run_gpu(args):
 
     batched = sweep = None
     if not args.no_batched:
-        batched = run_batched(dev, stream, steps=max(3, args.steps // 10), warmup=1)
+        batched = run_batched(dev, stream, steps=max(3, args.steps // 10), warmup=1,
+                              rank=rank, world=world)
         sweep = run_sweep(dev, stream, steps=max(3, args.steps // 10), warmup=1)
 
     if rank == 0:
@@ -412,7 +409,7 @@ def _build_all(ffg, spaces, fits, nbh, graphs=None, wss=None, stream=None):
     return graphs, wss
 
 
-def run_batched(dev, stream, steps, warmup):
+def run_batched(dev, stream, steps, warmup, rank=0, world=1):
     """234 spaces (26 kernel templates x 9 fitness seeds, sizes log-uniform,
     3/30/70 % failures): per step build every Hamming FFG, one batched FP32
     PageRank launch, batched C_p at 1/2/5/10/20 %.  Compared with the plain
@@ -421,6 +418,10 @@ def run_batched(dev, stream, steps, warmup):
     import ffg_inputs as fi
     import paper_2210_01465_gb300 as ffg
     work = fi.batch_workload()
+    if world > 1:   # independent spaces: LPT shards by raw size, no data-path collective
+        from paper_2210_01465_gb300.multi import shard_lpt
+        mine = shard_lpt([float(sp.n_raw) for sp, _, _ in work], world)[rank]
+        work = [work[j] for j in mine]
     spaces = [ffg.Space.from_spec(sp) for sp, _, _ in work]
     fits = [fi.runtimes_torch(sp, seed, fail, device=dev) for sp, seed, fail in work]
     graphs, wss = _build_all(ffg, spaces, fits, ffg.HAMMING, stream=stream)
@@ -454,6 +455,11 @@ def run_batched(dev, stream, steps, warmup):
     pr_ms = float(np.mean([r[2] for r in recs]))
     iters = recs[-1][3].astype(np.float64)
     units = float((E * iters).sum())
+    from paper_2210_01465_gb300.multi import reduce_time_work
+    n_spaces = len(graphs)
+    ms, units_all = reduce_time_work(ms, units, device=dev)
+    pr_ms, _ = reduce_time_work(pr_ms, 0.0, device=dev)
+    _, n_spaces = reduce_time_work(0.0, n_spaces, device=dev)
     # plain FP64, one solve per space
     t64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     units64 = 0.0
@@ -464,12 +470,14 @@ def run_batched(dev, stream, steps, warmup):
     t64[1].record(stream)
     t64[1].synchronize()
     ms64 = t64[0].elapsed_time(t64[1])
+    ms64, units64 = reduce_time_work(ms64, units64, device=dev)
+    units = units_all
     return {"workload": "234 spaces (26 templates incl. the paper's convolution, GEMM and "
                         "PnPoly spaces x 9 seeds), Hamming FFGs, batched FP32 PageRank in one "
                         "persistent launch, batched C_p at 1/2/5/10/20 %",
-            "spaces": len(graphs), "nodes": int(N.sum()), "edges": int(E.sum()),
+            "spaces": int(n_spaces), "nodes_rank0": int(N.sum()), "edges_rank0": int(E.sum()),
             "value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-            "spaces_per_s": len(graphs) / (ms / 1e3), "pagerank_ms": pr_ms,
+            "spaces_per_s": n_spaces / (ms / 1e3), "pagerank_ms": pr_ms,
             "pagerank_edges_iters_per_s": units / (pr_ms / 1e3),
             "plain_f64_pagerank_ms": ms64,
             "plain_f64_edges_iters_per_s": units64 / (ms64 / 1e3),

@@ -331,3 +331,60 @@ def test_batched_centrality_matches_single():
     out = ffg.centrality_many(specs, p)
     for row, ref in zip(out, refs):
         assert np.abs(row - ref).max() <= F64_CP
+
+
+def test_bounded_wait_reports_timeout():
+    """Fault injected on the host: the plan is edited so that one block of a
+    multi-block job never starts.  The job's other blocks give up at the
+    bounded barrier and the host reads FFG_ERR_TIMEOUT; the context stays
+    usable."""
+    spec = fi.single_large()
+    g, _ = run_build(spec, fi.runtimes(spec, 1), "adjacent")
+    small = fi.single_small()
+    gs, _ = run_build(small, fi.runtimes(small, 2), "hamming")
+    batch = ffg.PageRankBatch([(g, 0.85), (gs, 0.85)], prec=ffg.F32)
+    nb = batch.plan.n_blocks
+    ws_base = batch.ws.data_ptr()
+    first = batch.ws[batch.plan.first - ws_base:batch.plan.first - ws_base + 4 * (nb + 1)]
+    first = first.view(torch.int32)
+    items = batch.ws[batch.plan.items - ws_base:].view(torch.int32)
+    f = first.cpu().numpy()
+    # blocks 0 and 1 start with ranks 0 and 1 of the large job
+    assert items[2 * f[0]].item() == 0 and items[2 * f[0] + 1].item() == 0
+    assert items[2 * f[1]].item() == 0 and items[2 * f[1] + 1].item() == 1
+    first[1] = int(f[2])          # block 1 runs nothing; block 0 would run ranks 0 and 1
+    torch.cuda.synchronize()
+    batch.run()
+    st, it, res, sts = ffg.pagerank_batch_query(batch.plan,
+                                                torch.cuda.current_stream().cuda_stream)
+    assert st == ffg.FFG_ERR_TIMEOUT and sts[0] == ffg.FFG_ERR_TIMEOUT
+    # the device is still usable: a fresh plan runs to convergence
+    fresh = ffg.PageRankBatch([(g, 0.85), (gs, 0.85)], prec=ffg.F32)
+    fresh.run()
+    it, res, sts = fresh.query()
+    assert (sts == ffg.FFG_OK).all()
+
+
+def test_precision_form_at_scale():
+    """11 parameters, 19.5M raw / 12.8M valid points, Hamming: the FFG is
+    bit-exact; FP32 ranks (FP64/exact reductions) and C_p are compared with the
+    oracle's exact FP64 solve, and so are the FP64 ranks."""
+    spec = fi.precision_large()
+    f = fi.runtimes(spec, 1)
+    p = [0.01, 0.05, 0.10]
+    og = oracle.build(spec, f, oracle.HAMMING)
+    g, fd = run_build(spec, f, "hamming")
+    assert g.n_nodes == 12774528
+    assert_same_graph(g, og)
+    xe = oracle.pagerank_exact(og, 0.85)
+    cpe = oracle.centrality(og, xe, p)
+    x32, it32, res32, conv32 = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F32)
+    l1_32 = float(np.abs(_np(x32).astype(np.float64) - xe).sum())
+    cp32 = ffg.centrality(g, fd, x32, p)
+    x64, it64, res64, conv64 = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64)
+    l1_64 = float(np.abs(_np(x64) - xe).sum())
+    print(f"\nprecision form: N={g.n_nodes} E={g.n_edges}; FP32 iters {it32} rank L1 {l1_32:.3e} "
+          f"C_p err {np.abs(cp32 - cpe).max():.3e}; FP64 iters {it64} rank L1 {l1_64:.3e}")
+    assert conv32 and conv64
+    assert np.abs(cp32 - cpe).max() <= F32_CP
+    assert l1_64 <= F64_L1
