@@ -426,6 +426,8 @@ def run_batched(dev, stream, steps, warmup, rank=0, world=1):
     fits = [fi.runtimes_torch(sp, seed, fail, device=dev) for sp, seed, fail in work]
     graphs, wss = _build_all(ffg, spaces, fits, ffg.HAMMING, stream=stream)
     batch = ffg.PageRankBatch([(g, DAMPING) for g in graphs], prec=ffg.F32, tol=TOL)
+    from paper_2210_01465_gb300.autotune import tune
+    best, tried = tune(batch)
     E = np.array([g.n_edges for g in graphs], dtype=np.float64)
     N = np.array([g.n_nodes for g in graphs], dtype=np.float64)
 
@@ -482,7 +484,9 @@ def run_batched(dev, stream, steps, warmup, rank=0, world=1):
             "plain_f64_pagerank_ms": ms64,
             "plain_f64_edges_iters_per_s": units64 / (ms64 / 1e3),
             "batched_f32_vs_plain_f64_speedup": (units / (pr_ms / 1e3)) / (units64 / (ms64 / 1e3)),
-            "blocks": int(batch.plan.n_blocks)}
+            "blocks": int(batch.plan.n_blocks),
+            "autotune": {"chosen (split/grain/max_blocks)": "/".join(map(str, best)),
+                         "ms_per_candidate": tried}}
 
 
 def run_sweep(dev, stream, steps, warmup):
@@ -500,6 +504,8 @@ def run_sweep(dev, stream, steps, warmup):
     dampings = (0.5, 0.7, 0.85, 0.95)
     batch = ffg.PageRankBatch([(g, a) for g in graphs for a in dampings], prec=ffg.F32, tol=TOL)
     E = np.array([g.n_edges for g in graphs for _ in dampings], dtype=np.float64)
+    from paper_2210_01465_gb300.autotune import tune
+    best, tried = tune(batch)
     captured = True
     try:
         cg = torch.cuda.CUDAGraph()
@@ -533,7 +539,9 @@ def run_sweep(dev, stream, steps, warmup):
                         "FP32 PageRank solves in one batch",
             "solves": len(E), "cuda_graph": captured, "ms_per_step": m,
             "solves_per_s": len(E) / (m / 1e3), "value": units / (m / 1e3), "unit": UNIT,
-            "blocks": int(batch.plan.n_blocks)}
+            "blocks": int(batch.plan.n_blocks),
+            "autotune": {"chosen (split/grain/max_blocks)": "/".join(map(str, best)),
+                         "ms_per_candidate": tried}}
 
 
 def main():

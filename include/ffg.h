@@ -236,6 +236,20 @@ ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec 
                                void *workspace, size_t ws_bytes, ffg_pr_batch *plan,
                                void *stream);
 
+/* Planning options.  A job whose cost exceeds `split` times the per-block
+ * share of the batch gets its own blocks, about one per `grain` shares (the
+ * others run on one block each); `max_blocks` caps the grid (0 = every
+ * co-resident block).  Defaults: 1.0, 1.0, 0.  They change only the
+ * schedule, never results or the workspace size. */
+typedef struct {
+    double split, grain;
+    int32_t max_blocks, reserved;
+} ffg_pr_tuning;
+
+ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec,
+                                     const ffg_pr_tuning *tuning, void *workspace,
+                                     size_t ws_bytes, ffg_pr_batch *plan, void *stream);
+
 /* Enqueues the whole batch: one layout launch over every distinct graph and
  * one persistent launch that runs every job to its own convergence.  Host
  * work is argument checking only, so the call can be captured in a CUDA

@@ -75,6 +75,11 @@ class ffg_pr_batch(C.Structure):
                 ("ctl", C.c_void_p)]
 
 
+class ffg_pr_tuning(C.Structure):
+    _fields_ = [("split", C.c_double), ("grain", C.c_double), ("max_blocks", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class ffg_cp_job(C.Structure):
     _fields_ = [("g", C.POINTER(ffg_graph)), ("fitness_raw", C.c_void_p), ("ranks", C.c_void_p)]
 
@@ -84,6 +89,7 @@ ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
                 "pagerank_workspace_bytes", "pagerank_prepare", "pagerank_solve",
                 "pagerank_solve_static",
                 "pagerank_query", "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
+                "pagerank_batch_plan_tuned",
                 "pagerank_batch_run", "pagerank_batch_query",
                 "centrality_workspace_bytes", "centrality_proportion",
                 "centrality_batch_workspace_bytes", "centrality_batch", "ffg_status_str",
@@ -120,6 +126,8 @@ def load(path: str | None = None):
     lib.pagerank_batch_workspace_bytes.argtypes = [P(ffg_pr_job), i32, C.c_int]
     lib.pagerank_batch_workspace_bytes.restype = sz
     lib.pagerank_batch_plan.argtypes = [P(ffg_pr_job), i32, C.c_int, vp, sz, P(ffg_pr_batch), vp]
+    lib.pagerank_batch_plan_tuned.argtypes = [P(ffg_pr_job), i32, C.c_int, P(ffg_pr_tuning), vp,
+                                              sz, P(ffg_pr_batch), vp]
     lib.pagerank_batch_run.argtypes = [P(ffg_pr_batch), vp]
     lib.pagerank_batch_query.argtypes = [P(ffg_pr_batch), vp, vp, vp, vp]
     lib.centrality_workspace_bytes.argtypes = [i32]
@@ -212,6 +220,15 @@ def pagerank_batch_plan(jobs, prec: int, ws: int, ws_bytes: int, plan: "ffg_pr_b
                         stream: int = 0) -> int:
     return int(load().pagerank_batch_plan(jobs, len(jobs), int(prec), C.c_void_p(ws),
                                           int(ws_bytes), C.byref(plan), C.c_void_p(stream)))
+
+
+def pagerank_batch_plan_tuned(jobs, prec: int, tuning, ws: int, ws_bytes: int,
+                              plan: "ffg_pr_batch", stream: int = 0) -> int:
+    """``tuning``: (split, grain, max_blocks)."""
+    t = ffg_pr_tuning(float(tuning[0]), float(tuning[1]), int(tuning[2]), 0)
+    return int(load().pagerank_batch_plan_tuned(jobs, len(jobs), int(prec), C.byref(t),
+                                                C.c_void_p(ws), int(ws_bytes), C.byref(plan),
+                                                C.c_void_p(stream)))
 
 
 def pagerank_batch_run(plan: "ffg_pr_batch", stream: int = 0) -> int:
@@ -434,9 +451,18 @@ class PageRankBatch:
         if need == 0:
             raise FFGError(FFG_ERR_INVALID_ARG, "pagerank_batch_workspace_bytes")
         self.ws = workspace(need, self.graphs[0].out_ptr.device)
+        self.need = need
         self.plan = ffg_pr_batch()
+        self.tuning = (1.0, 1.0, 0)
         _check(pagerank_batch_plan(self.jobs, prec, self.ws.data_ptr(), need, self.plan,
                                    _stream_handle(stream)), "pagerank_batch_plan")
+
+    def replan(self, tuning, stream=None):
+        """Re-plan into the same workspace with (split, grain, max_blocks)."""
+        _check(pagerank_batch_plan_tuned(self.jobs, self.prec, tuning, self.ws.data_ptr(),
+                                         self.need, self.plan, _stream_handle(stream)),
+               "pagerank_batch_plan_tuned")
+        self.tuning = tuple(tuning)
 
     def run(self, stream=None):
         _check(pagerank_batch_run(self.plan, _stream_handle(stream)), "pagerank_batch_run")

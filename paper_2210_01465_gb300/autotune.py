@@ -1,0 +1,56 @@
+"""Autotuner for the batched PageRank schedule.
+
+The kernels' shapes are fixed at build time (the build-time sweep found the
+defaults best on the single large space); what varies with the workload is
+the schedule of a batch: which jobs get dedicated blocks (`split`), how many
+(`grain`) and how large the grid is (`max_blocks`).  ``tune`` runs the
+batch once per candidate (same workspace, re-planned), times it with CUDA
+events and leaves the fastest plan in place.  Results never depend on the
+tuning, only the time does.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+CANDIDATES = (
+    (1.0, 1.0, 0),
+    (2.0, 1.0, 0),
+    (0.5, 0.5, 0),
+    (1.0, 0.5, 0),
+    (0.25, 0.25, 0),
+)
+
+
+def tune(batch, candidates=CANDIDATES, reps: int = 1, table_path: str | None = None):
+    """Pick the fastest schedule for ``batch`` (a PageRankBatch); returns
+    (best (split, grain, max_blocks), {candidate: ms})."""
+    import torch
+    times = {}
+    for cand in candidates:
+        batch.replan(cand)
+        batch.run()
+        batch.query()                      # warm-up run of this plan
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            batch.run()
+            e1.record()
+            batch.query()
+            ms.append(e0.elapsed_time(e1))
+        times[cand] = min(ms)
+    best = min(times, key=times.get)
+    batch.replan(best)
+    if table_path:
+        key = f"jobs={batch.plan.n_jobs},graphs={batch.plan.n_graphs}," \
+              f"edges={sum(g.n_edges for g in batch.graphs)},prec={batch.prec}"
+        table = {}
+        if os.path.exists(table_path):
+            with open(table_path) as fh:
+                table = json.load(fh)
+        table[key] = {"split": best[0], "grain": best[1], "max_blocks": best[2],
+                      "ms": times[best]}
+        with open(table_path, "w") as fh:
+            json.dump(table, fh, indent=1)
+    return best, {f"{c[0]}/{c[1]}/{c[2]}": round(t, 3) for c, t in times.items()}

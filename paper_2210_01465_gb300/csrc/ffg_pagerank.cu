@@ -981,7 +981,8 @@ ffg_status check_job(const ffg_pr_job &j, int idx) {
     return FFG_OK;
 }
 
-ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, PlanHost &P) {
+ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, const ffg_pr_tuning &tu,
+                     PlanHost &P) {
     // distinct graphs (jobs may share one)
     std::unordered_map<const int64_t *, int> gidx;
     P.graph_of_job.resize(n_jobs);
@@ -1004,7 +1005,9 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, PlanHost &P
         const int64_t tiles = (g->n_nodes + 31) / 32;
         useful += std::max<int64_t>(1, (tiles + 4 * kWarps - 1) / (4 * kWarps));
     }
-    const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(nb_max, useful)));
+    int cap = nb_max;
+    if (tu.max_blocks > 0 && tu.max_blocks < cap) cap = tu.max_blocks;
+    const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(cap, useful)));
     P.nb = nb;
     const double total = std::accumulate(cost.begin(), cost.end(), 0.0);
     const double share = total / nb;
@@ -1018,9 +1021,13 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, PlanHost &P
     std::vector<int> small;
     for (int j : order) {
         const int64_t tiles = (jobs[j].g->n_nodes + 31) / 32;
-        int k = static_cast<int>(std::floor(cost[j] / share));
+        // a job above `split` shares gets about one block per `grain` shares
+        int k = cost[j] > tu.split * share
+                    ? static_cast<int>(std::llround(cost[j] / (tu.grain * share)))
+                    : 1;
         k = static_cast<int>(std::min<int64_t>(k, std::max<int64_t>(1, tiles / kWarps)));
-        if (k >= 2 && next_block + k <= nb) {
+        k = std::min(k, nb - next_block);
+        if (k >= 2) {
             P.group[j] = k;
             for (int r = 0; r < k; ++r) {
                 per_block[next_block + r].push_back(make_int2(j, r));
@@ -1065,14 +1072,16 @@ struct BatchWs {
 // per distinct graph the layout and tile metadata.  host_jobs / host_graphs
 // (if non-NULL) receive the device pointers of every job and graph.
 BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
-                    const PlanHost &P, std::vector<JobDev> *host_jobs,
+                    const PlanHost &P, int nb_max, std::vector<JobDev> *host_jobs,
                     std::vector<GraphDev> *host_graphs) {
     Carver c(base);
     BatchWs w;
     w.jobs = c.take<JobDev>(n_jobs);
     w.graphs = c.take<GraphDev>(P.graphs.size());
-    w.first = c.take<int>(P.nb + 1);
-    w.items = c.take<int2>(std::max<size_t>(1, P.items.size()));
+    // plan tables sized for any tuning: at most nb_max blocks, and a job in a
+    // group of k blocks adds k - 1 items, with sum(k) <= nb_max
+    w.first = c.take<int>(size_t(nb_max) + 1);
+    w.items = c.take<int2>(size_t(n_jobs) + nb_max);
     w.ctl = c.take<PrCtl>(n_jobs);
     std::vector<GraphDev> gd(P.graphs.size());
     int64_t tile0 = 0;
@@ -1099,7 +1108,9 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
         J.ranks = jobs[j].ranks;
         J.w0 = c.take<char>(size_t(g->n_nodes) * elem);
         J.w1 = c.take<char>(size_t(g->n_nodes) * elem);
-        J.partials = c.take<long long>(size_t(2) * P.group[j] * 4);
+        // sized for any group (<= nb_max): the workspace size does not depend
+        // on the tuning
+        J.partials = c.take<long long>(size_t(2) * nb_max * 4);
         J.ctl = w.ctl + j;
         J.n = g->n_nodes;
         J.alpha = jobs[j].damping;
@@ -1126,6 +1137,8 @@ ffg_status batch_blocks(ffg_prec prec, int *nb_max) {
 }  // namespace
 }  // namespace ffg
 
+const ffg_pr_tuning kDefaultTuning = {1.0, 1.0, 0, 0};
+
 extern "C" size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs,
                                                  ffg_prec prec) {
     clear_error();
@@ -1133,13 +1146,23 @@ extern "C" size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t
     int nb_max = 0;
     if (batch_blocks(prec, &nb_max) != FFG_OK) return 0;
     PlanHost P;
-    if (make_plan(jobs, n_jobs, nb_max, P) != FFG_OK) return 0;
-    return carve_batch(nullptr, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, nullptr, nullptr).bytes;
+    if (make_plan(jobs, n_jobs, nb_max, kDefaultTuning, P) != FFG_OK) return 0;
+    return carve_batch(nullptr, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, nb_max, nullptr,
+                       nullptr)
+        .bytes;
 }
 
 extern "C" ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec,
                                           void *workspace, size_t ws_bytes, ffg_pr_batch *plan,
                                           void *stream_) {
+    return pagerank_batch_plan_tuned(jobs, n_jobs, prec, &kDefaultTuning, workspace, ws_bytes,
+                                     plan, stream_);
+}
+
+extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t n_jobs,
+                                                ffg_prec prec, const ffg_pr_tuning *tuning,
+                                                void *workspace, size_t ws_bytes,
+                                                ffg_pr_batch *plan, void *stream_) {
     clear_error();
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (!jobs || n_jobs < 1 || !plan || !workspace)
@@ -1149,15 +1172,21 @@ extern "C" ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs
         return set_error("unknown precision %d", (int)prec), FFG_ERR_INVALID_ARG;
     if (!aligned256(workspace))
         return set_error("workspace not 256-byte aligned"), FFG_ERR_INVALID_ARG;
+    const ffg_pr_tuning tu = tuning ? *tuning : kDefaultTuning;
+    if (!(tu.split > 0.0) || !(tu.grain > 0.0) || tu.max_blocks < 0)
+        return set_error("tuning: split and grain must be > 0, max_blocks >= 0"),
+               FFG_ERR_INVALID_ARG;
     int nb_max = 0;
     FFG_TRY(batch_blocks(prec, &nb_max));
     PlanHost P;
-    FFG_TRY(make_plan(jobs, n_jobs, nb_max, P));
+    FFG_TRY(make_plan(jobs, n_jobs, nb_max, tu, P));
     std::vector<JobDev> jd;
     std::vector<GraphDev> gd;
-    BatchWs w = carve_batch(workspace, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, &jd, &gd);
+    BatchWs w = carve_batch(workspace, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, nb_max, &jd, &gd);
     if (ws_bytes < w.bytes)
         return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
+    if (P.nb > nb_max || P.items.size() > size_t(n_jobs) + nb_max)
+        return set_error("internal: plan exceeds its tables"), FFG_ERR_INVALID_ARG;
     FFG_TRY(check_cuda(cudaMemcpyAsync(w.jobs, jd.data(), sizeof(JobDev) * jd.size(),
                                        cudaMemcpyHostToDevice, stream), "upload jobs"));
     FFG_TRY(check_cuda(cudaMemcpyAsync(w.graphs, gd.data(), sizeof(GraphDev) * gd.size(),

@@ -115,3 +115,12 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(root, f)).read()
                 assert "import oracle" not in src and "ffg_oracle" not in src, f
+
+
+def test_batch_tuning_validated_on_host(lib):
+    jobs = (ffg.ffg_pr_job * 1)()
+    plan = ffg.ffg_pr_batch()
+    for tuning in ((0.0, 1.0, 0), (1.0, -1.0, 0), (float("nan"), 1.0, 0), (1.0, 1.0, -2)):
+        assert ffg.pagerank_batch_plan_tuned(jobs, ffg.F32, tuning, 256, 1 << 20, plan) == \
+            ffg.FFG_ERR_INVALID_ARG
+        assert "tuning" in ffg.ffg_last_error()

@@ -388,3 +388,31 @@ def test_precision_form_at_scale():
     assert conv32 and conv64
     assert np.abs(cp32 - cpe).max() <= F32_CP
     assert l1_64 <= F64_L1
+
+
+def test_batch_tuning_changes_schedule_not_results():
+    specs, refs = [], []
+    for k, spec in enumerate([fi.single_small(), fi.pnpoly_space(), fi.conv_mi50_space()]):
+        f = fi.runtimes(spec, 20 + k)
+        og = oracle.build(spec, f, oracle.HAMMING)
+        g, _ = run_build(spec, f, "hamming")
+        for alpha in (0.7, 0.9):
+            specs.append((g, alpha))
+            refs.append(oracle.pagerank_exact(og, alpha))
+    batch = ffg.PageRankBatch(specs, prec=ffg.F64, tol=1e-12)
+    first = None
+    for tuning in ((1.0, 1.0, 0), (0.1, 0.1, 0), (5.0, 1.0, 3)):
+        batch.replan(tuning)
+        batch.run()
+        it, res, st = batch.query()
+        assert (st == 0).all()
+        xs = [_np(x) for x in batch.ranks]
+        for x, xe in zip(xs, refs):
+            assert np.abs(x - xe).sum() <= F64_L1
+        # fixed-point reductions: the block count does not change a single bit
+        if first is None:
+            first = (it.copy(), xs)
+        else:
+            np.testing.assert_array_equal(it, first[0])
+            for x, x0 in zip(xs, first[1]):
+                np.testing.assert_array_equal(x, x0)
