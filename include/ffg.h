@@ -172,10 +172,12 @@ ffg_status ffg_build_fill(const ffg_space *space, const double *fitness_raw, ffg
 
 size_t pagerank_workspace_bytes(int64_t n_nodes, int64_t n_edges, ffg_prec prec);
 
-/* Builds, in `workspace`, the edge layout that pagerank_solve streams: the
- * in-edges regrouped per tile of 32 rows by neighbourhood offset.  It
- * depends on the graph only, so several solves of one graph (other damping
- * factors, warm starts) pass FFG_INIT_LAYOUT and skip it.  Asynchronous. */
+/* Builds, in `workspace`, the edge layout that pagerank_solve streams: per
+ * tile of 32 rows, one (offset, row mask) descriptor per distinct in-edge
+ * offset src - dst, plus the tiles' cost prefix used to split them between
+ * blocks.  It depends on the graph only, so several solves of one graph
+ * (other damping factors, warm starts) pass FFG_INIT_LAYOUT and skip it.
+ * Asynchronous. */
 ffg_status pagerank_prepare(const ffg_graph *g, ffg_prec prec, void *workspace,
                             size_t ws_bytes, void *stream);
 
@@ -192,7 +194,7 @@ ffg_status pagerank_solve(const ffg_graph *g, double damping, double tol, int32_
  * scratch space is a file-scope device array of 8 MiB that every device
  * holds from the moment the library is loaded until the process exits.
  * Graphs whose pagerank_workspace_bytes exceeds 8 MiB are rejected with
- * FFG_ERR_NO_MEMORY (about 85,000 nodes at 20 in-edges per node in FP32).
+ * FFG_ERR_NO_MEMORY (about 48,000 nodes at 20 in-edges per node in FP32).
  * The first call on a device looks up the array's device address; make
  * that first call before any stream capture.  Every call shares the one
  * array (the parts that must start at zero are cleared by each call), so
@@ -224,6 +226,7 @@ typedef struct {
     int32_t prec, n_jobs, n_graphs, n_blocks;
     int64_t total_tiles;
     void *jobs, *graphs, *items, *first, *ctl;
+    void *tile_cnt, *tile_pre, *scan_tmp;  /* per-tile cost tables of all graphs */
 } ffg_pr_batch;
 
 size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec);

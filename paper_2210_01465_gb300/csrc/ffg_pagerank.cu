@@ -9,38 +9,37 @@
 //
 // Two launches per solve.
 //
-// k_pr_layout builds, in the workspace, a gather-friendly copy of the
-// in-edges.  Rows are grouped in tiles of 32 consecutive nodes; a tile's
-// in-edges are ordered by (src - dst, dst), i.e. grouped by neighbourhood
-// offset.  For an FFG a tile has few distinct offsets (about one per stencil
-// slot of the Hamming or adjacent neighbourhood) and each group holds
-// consecutive sources, so 32 consecutive entries (a chunk, one per lane)
-// gather few 32-byte sectors.  No sort is needed: each row's list is already
-// ascending, so a warp merge over the distinct offsets emits the groups in
-// order.  Each entry carries the shared-memory offset of its accumulator:
-// slot = number of earlier entries of the same chunk with the same row, and
-// the accumulator of (slot, row) lives at (slot << 5) | (row ^ slot) (the
-// XOR spreads one row's slots over distinct banks).  Within a chunk no two
-// lanes share an accumulator and the summation order is fixed.  Entry =
-// (src << 8) | offset; padding entries gather node 0 into a dummy slot.
-// Tile t's chunks start at chunk floor(in_ptr[32t] / 32) + t.  Tiles that do
-// not fit (more than kSortCap edges, a row with more than kMaxSlots entries
-// in one chunk, or 2^24 nodes and more) keep the plain CSR path.
+// k_pr_layout builds, in the workspace, a compact copy of the in-edges.
+// Rows are grouped in tiles of 32 consecutive nodes, one row per lane.  In an
+// FFG the in-neighbours of a tile lie at few distinct node offsets
+// off = src - dst (about one per stencil slot of the Hamming or adjacent
+// neighbourhood, a few more where invalid configurations shift the
+// numbering), so a tile is stored as a list of descriptors (off, mask): lane
+// r has the in-edge (32t + r + off) -> (32t + r) iff bit r of mask is set.
+// Eight bytes per descriptor replace four bytes per edge, and the 32 lanes
+// of one descriptor gather consecutive sources.  No sort is needed: each
+// row's in-list is ascending, so a warp merge over the 32 lists emits the
+// offsets in ascending order, and every row sums its in-edges in ascending
+// source order.  A tile's list is padded with empty descriptors to a
+// multiple of kU and starts at desc_begin(in_ptr[32t], t), which leaves room
+// for one descriptor per in-edge; the padded count is kept per tile.
 //
 // k_pagerank is one cooperative persistent launch for every iteration.
 // Each block owns a contiguous range of tiles of about equal cost and its
-// warps take tiles from it in turn; lane t owns row 32*tile + t, so per-row
-// loads and stores are coalesced.  One
-// lane streams the tile's chunks into a double-buffered shared-memory stage
+// warps take tiles from it in turn.  Lane r owns row 32t + r and accumulates
+// it in a register; per-row loads and stores are coalesced.  One lane
+// streams the tile's descriptors into a double-buffered shared-memory stage
 // with TMA bulk copies (cp.async.bulk, completion on an mbarrier), one
-// segment ahead, while the warp gathers w for the current segment and adds
-// into its accumulators.  Only w is kept between iterations (ping-pong):
-// x[v] = w[v] * outdeg[v] (or w[v] for a node without out-edges).  Residual
+// segment (or the next tile's first segment) ahead, while the warp reads
+// the current segment by broadcast and gathers w.  Only w is kept between
+// iterations (ping-pong): x[v] = w[v] * outdeg[v] (or w[v] for a node
+// without out-edges).  Residual
 // sum |x'-x|, next D and sum x' are accumulated as exact 64-bit fixed-point
-// integers (quantum 2^-60), reduced per block into a double-buffered
-// partials array, and after a grid barrier every block sums the partials;
-// integer sums do not depend on order, so all blocks take the same stopping
-// decision and results are deterministic however tiles were scheduled.
+// integers (quantum 2^-60, converted with integer instructions), added per
+// block into a triple-buffered accumulator of the job, which every block
+// reads after the grid barrier; integer sums do not depend on order, so all
+// blocks take the same stopping decision and results are deterministic
+// however tiles were scheduled.
 // Every wait (grid barrier, mbarrier) is bounded; on expiry the kernel
 // records FFG_ERR_TIMEOUT, lets its own copies land, and returns.
 #include "ffg_internal.cuh"
@@ -49,30 +48,39 @@ namespace ffg {
 
 namespace {
 
-constexpr int kPrThreads = 256;
-constexpr int kWarps = kPrThreads / 32;
+// Warps per block: a single solve runs one block of kWarpsSingle warps per
+// SM, so that all warps of an SM share one tile counter (warps of one SM are
+// not served equally: with several blocks per SM the youngest block finishes
+// last); a batch runs blocks of kWarpsBatch warps, several per SM, one job
+// (or one rank of a job) per block at a time.
+#ifndef FFG_PR_WARPS
+#define FFG_PR_WARPS 24
+#endif
+constexpr int kWarpsSingle = FFG_PR_WARPS;
+constexpr int kWarpsBatch = 8;
 constexpr int kMaxBlocks = 4096;
 constexpr uint64_t kTimeoutNs = 2000000000ULL;
-constexpr int kSortCap = 2048;          // in-edges per tile staged by the layout kernel
-constexpr int kMaxSlots = 7;            // entries of one row within one chunk
-constexpr uint32_t kDummyOff = (7u << 5) | 7u;  // accumulator of padding entries
-constexpr uint32_t kPadEntry = kDummyOff;       // source 0, dummy accumulator
-constexpr int kAccElems = 8 * 32;       // accumulators per warp (7 slots + dummy)
 #ifndef FFG_PR_SEG
-#define FFG_PR_SEG 16
+#define FFG_PR_SEG 128
 #endif
-#ifndef FFG_PR_GROUP
-#define FFG_PR_GROUP 8
+#ifndef FFG_PR_UNROLL
+#define FFG_PR_UNROLL 8
 #endif
 #ifndef FFG_PR_MINBLOCKS
 #define FFG_PR_MINBLOCKS 3
 #endif
-constexpr int kSeg = FFG_PR_SEG;        // chunks per TMA segment
-constexpr int kGroup = FFG_PR_GROUP;    // gathers in flight per lane
-constexpr int64_t kMaxPackedNodes = int64_t(1) << 24;
+constexpr int kSegD = FFG_PR_SEG;       // descriptors per TMA segment
+constexpr int kU = FFG_PR_UNROLL;       // descriptors per step (gathers in flight per lane)
+static_assert(kU % 2 == 0 && kSegD % kU == 0 && kU <= 32, "descriptor padding");
 constexpr int kLayoutThreads = 64;
-constexpr int64_t kRowCost = 20;        // per-row cost in in-edge units (block split)
+constexpr int64_t kRowCost = 20;        // per-row cost in in-edge units (batch plan)
+constexpr int64_t kTileCost = 19;       // per-tile cost in descriptor units (block split)
 
+// Control block of one job (zeroed by the host before each run).  acc[b]
+// holds the fixed-point sums (residual, dangling mass, sum of x) of the
+// phases p with (p - 1) % 3 == b: blocks add theirs before the phase's
+// barrier, everyone reads them after it, and rank 0 clears the next buffer
+// during the phase (its last readers passed the previous barrier).
 struct PrCtl {
     unsigned int barrier;
     int status;
@@ -81,28 +89,36 @@ struct PrCtl {
     double residual;
     int nblocks;
     int pad;
+    unsigned long long acc[3][4];
 };
 
 struct PrWs {
     PrCtl *ctl;
-    long long *partials;  // [2][kMaxBlocks][4] fixed-point block sums
     void *w0, *w1;
-    uint32_t *layout;  // packed chunks
-    uint8_t *meta;     // per tile: accumulator slots used (1..kMaxSlots), 0 = CSR path
+    uint2 *desc;          // tile descriptors (off, mask)
+    int32_t *cnt;         // per tile: descriptors, padded to a multiple of kU
+    int64_t *tpre;        // exclusive prefix sums of cnt (ntiles + 1)
+    int64_t *scan;        // scan scratch
     size_t bytes;
 };
 
-inline int64_t layout_chunks(int64_t n, int64_t e) { return e / 32 + (n + 31) / 32 + 1; }
+// first descriptor of tile t, whose first in-edge is e0: every tile has room
+// for one descriptor per in-edge plus its padding, and starts 64-byte aligned
+__host__ __device__ __forceinline__ int64_t desc_begin(int64_t e0, int64_t t) {
+    return (e0 + kU - 1) / kU * kU + 2 * kU * t;
+}
+inline int64_t desc_capacity(int64_t n, int64_t e) { return e + 2 * kU * ((n + 31) / 32 + 1); }
 
 PrWs carve(void *base, int64_t n, int64_t e, size_t elem) {
     Carver c(base);
     PrWs w;
     w.ctl = c.take<PrCtl>(1);
-    w.partials = c.take<long long>(size_t(2) * kMaxBlocks * 4);
     w.w0 = c.take<char>(size_t(n) * elem);
     w.w1 = c.take<char>(size_t(n) * elem);
-    w.layout = c.take<uint32_t>(size_t(layout_chunks(n, e)) * 32);
-    w.meta = c.take<uint8_t>(size_t((n + 31) / 32));
+    w.desc = c.take<uint2>(size_t(desc_capacity(n, e)));
+    w.cnt = c.take<int32_t>(size_t((n + 31) / 32));
+    w.tpre = c.take<int64_t>(size_t((n + 31) / 32) + 1);
+    w.scan = c.take<int64_t>(size_t(scan_scratch_elems((n + 31) / 32)));
     w.bytes = c.off;
     return w;
 }
@@ -174,22 +190,24 @@ __device__ bool group_barrier(PrCtl *ctl, unsigned target, int group) {
     __syncthreads();
     if (group == 1) return true;  // a one-block group only needs the block barrier
     if (threadIdx.x == 0) {
-        __threadfence();
+        // release: this block's writes (ordered before by the block barrier)
+        // become visible to every block that acquires the count
         red_release_add(&ctl->barrier, 1u);
         const uint64_t t0 = global_ns();
-        unsigned ns = 32;
+        unsigned ns = 0;
         int ok = 1;
         for (uint32_t polls = 0; ld_acquire(&ctl->barrier) < target; ++polls) {
-            if (*(volatile int *)&ctl->status != 0) { ok = 0; break; }
+            if ((polls & 15) == 15 && *(volatile int *)&ctl->status != 0) { ok = 0; break; }
             if (polls > (1u << 24) || global_ns() - t0 > kTimeoutNs) {
                 atomicCAS(&ctl->status, 0, (int)FFG_ERR_TIMEOUT);
                 ok = 0;
                 break;
             }
-            __nanosleep(ns);
-            if (ns < 256) ns <<= 1;
+            if (polls > 64) {  // spin briefly, then back off
+                __nanosleep(ns);
+                ns = ns < 32 ? 32 : (ns < 256 ? ns << 1 : ns);
+            }
         }
-        __threadfence();
         if (*(volatile int *)&ctl->status != 0) ok = 0;
         s_ok = ok;
     }
@@ -204,13 +222,28 @@ __device__ bool group_barrier(PrCtl *ctl, unsigned target, int group) {
 // The residual, the dangling mass and the sum of x are accumulated as 64-bit
 // fixed-point integers with quantum 2^-60 (all three are sums of
 // non-negative values below 8).  Integer sums are exact and independent of
-// order, so they are deterministic however tiles are scheduled, and they use
-// no FP64 instruction (a narrow pipe on this part) on the per-row path.
+// order, so they are deterministic however tiles are scheduled.  The
+// conversion truncates the significand shifted into place, with integer
+// instructions only: conversions to 64-bit integers, like FP64 arithmetic,
+// run on a narrow pipe on this part.
 constexpr double kFix = 1152921504606846976.0;  // 2^60
-__device__ __forceinline__ long long to_fix(float x) {
-    return __float2ll_rn(x * 1152921504606846976.0f);
+constexpr long long kFixSat = 1LL << 62;        // stands for values >= 4 (never reached)
+__device__ __forceinline__ long long to_fix(float x) {  // x >= 0
+    const uint32_t b = __float_as_uint(x);
+    if (b < 0x00800000u) return 0;                    // zero or below 2^-126
+    const int e = static_cast<int>(b >> 23) - 90;     // x * 2^60 = m * 2^e
+    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
+    if (e >= 39) return kFixSat;
+    return e >= 0 ? static_cast<long long>(m << e) : (e > -24 ? static_cast<long long>(m >> -e) : 0);
 }
-__device__ __forceinline__ long long to_fix(double x) { return __double2ll_rn(x * kFix); }
+__device__ __forceinline__ long long to_fix(double x) {  // x >= 0
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    if (b < 0x0010000000000000ULL) return 0;            // zero or subnormal
+    const int e = static_cast<int>(b >> 52) - 1015;     // x * 2^60 = m * 2^e
+    const unsigned long long m = (b & 0xfffffffffffffULL) | 0x10000000000000ULL;
+    if (e >= 10) return kFixSat;
+    return e >= 0 ? static_cast<long long>(m << e) : (e > -53 ? static_cast<long long>(m >> -e) : 0);
+}
 
 struct Fix3 {
     long long r = 0, d = 0, s = 0;
@@ -223,8 +256,9 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 }
 
 // block sums of the three accumulators; valid in thread 0
+template <int W>
 __device__ __forceinline__ Fix3 block_sum_fix(Fix3 v) {
-    __shared__ long long red[3][kWarps];
+    __shared__ long long red[3][W];
     v.r = warp_sum_ll(v.r);
     v.d = warp_sum_ll(v.d);
     v.s = warp_sum_ll(v.s);
@@ -238,7 +272,7 @@ __device__ __forceinline__ Fix3 block_sum_fix(Fix3 v) {
     __syncthreads();
     Fix3 t;
     if (threadIdx.x == 0)
-        for (int k = 0; k < kWarps; ++k) {
+        for (int k = 0; k < W; ++k) {
             t.r += red[0][k];
             t.d += red[1][k];
             t.s += red[2][k];
@@ -250,107 +284,68 @@ struct Tot {
     double r, d, s;
 };
 
-// every block sums the partials of all blocks (warp 0)
-__device__ __forceinline__ Tot sum_partials(const long long *part, int nb) {
-    __shared__ double s_out[3];
-    if (threadIdx.x < 32) {
-        long long a = 0, b = 0, c = 0;
-        for (int k = threadIdx.x; k < nb; k += 32) {
-            a += __ldcg(part + 4 * k + 0);
-            b += __ldcg(part + 4 * k + 1);
-            c += __ldcg(part + 4 * k + 2);
-        }
-        a = warp_sum_ll(a);
-        b = warp_sum_ll(b);
-        c = warp_sum_ll(c);
-        if (threadIdx.x == 0) {
-            s_out[0] = static_cast<double>(a) / kFix;
-            s_out[1] = static_cast<double>(b) / kFix;
-            s_out[2] = static_cast<double>(c) / kFix;
-        }
+// thread 0: add the block's sums into buffer `buf`; rank 0 also clears the
+// buffer of the next phase
+__device__ __forceinline__ void publish(PrCtl *ctl, int buf, const Fix3 &b, int rank) {
+    if (b.r) atomicAdd(&ctl->acc[buf][0], static_cast<unsigned long long>(b.r));
+    if (b.d) atomicAdd(&ctl->acc[buf][1], static_cast<unsigned long long>(b.d));
+    if (b.s) atomicAdd(&ctl->acc[buf][2], static_cast<unsigned long long>(b.s));
+    if (rank == 0) {
+        unsigned long long *nx = ctl->acc[buf == 2 ? 0 : buf + 1];
+        nx[0] = 0;
+        nx[1] = 0;
+        nx[2] = 0;
     }
-    __syncthreads();
-    Tot t{s_out[0], s_out[1], s_out[2]};
-    __syncthreads();
-    return t;
 }
 
 // ---------------------------------------------------------------------------
-// gather-friendly layout of the in-edges (built once per solve)
+// descriptor layout of the in-edges (built once per graph)
 // ---------------------------------------------------------------------------
-// One tile of the layout (one warp): see the comment at the top of the file.
-__device__ void layout_tiles(const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx,
-                             int64_t n, uint32_t *__restrict__ layout, uint8_t *__restrict__ meta,
-                             int64_t t, int32_t *src, int lane) {
-    const unsigned lt_mask = (1u << lane) - 1u;
-    do {
-        const int64_t r0 = t << 5;
-        const int64_t rend = r0 + 32 < n ? r0 + 32 : n;
-        const int64_t ip0 = in_ptr[r0], ip1 = in_ptr[rend];
-        const int64_t et = ip1 - ip0;
-        if (et > kSortCap || n >= kMaxPackedNodes) {
-            if (lane == 0) meta[t] = 0;
-            break;
+// One tile (one warp): merge the 32 ascending in-lists by offset src - dst;
+// each distinct offset becomes one descriptor whose mask holds the lanes
+// that have it.  Offsets fit int32 (n < 2^31); INT32_MAX marks an exhausted
+// list.
+__device__ void layout_tile(const int64_t *__restrict__ in_ptr,
+                            const int32_t *__restrict__ in_idx, int64_t n,
+                            uint2 *__restrict__ desc, int32_t *__restrict__ cnt, int64_t t,
+                            int lane) {
+    const int64_t r0 = t << 5;
+    const int64_t v = r0 + lane;
+    int64_t cur = 0, end = 0;
+    if (v < n) {
+        cur = in_ptr[v];
+        end = in_ptr[v + 1];
+    }
+    const int64_t e0 = __shfl_sync(0xffffffffu, cur, 0);  // in_ptr[r0]: row r0 exists
+    uint2 *out = desc + desc_begin(e0, t);
+    const int32_t vi = static_cast<int32_t>(v);
+    int32_t head = cur < end ? __ldg(in_idx + cur) - vi : INT32_MAX;
+    int k = 0;
+    while (true) {
+        const int32_t m = __reduce_min_sync(0xffffffffu, head);
+        if (m == INT32_MAX) break;
+        const bool hit = head == m;
+        const unsigned mask = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) out[k] = make_uint2(static_cast<uint32_t>(m), mask);
+        ++k;
+        if (hit) {
+            ++cur;
+            head = cur < end ? __ldg(in_idx + cur) - vi : INT32_MAX;
         }
-        for (int64_t k = lane; k < et; k += 32) src[k] = in_idx[ip0 + k];
-        const int64_t v = r0 + lane;
-        int cur = 0, end = 0;
-        if (v < rend) {
-            cur = static_cast<int>(in_ptr[v] - ip0);
-            end = static_cast<int>(in_ptr[v + 1] - ip0);
-        }
-        __syncwarp();
-        const int64_t base = ((ip0 >> 5) + t) * 32;  // first entry of the tile
-        int pos = 0, last_chunk = -1, count = 0, maxslot = 0;
-        // merge the 32 ascending lists by offset src - dst; one group per offset
-        while (true) {
-            const int32_t head = cur < end ? src[cur] - static_cast<int32_t>(v) : INT32_MAX;
-            int32_t m = head;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const int32_t y = __shfl_xor_sync(0xffffffffu, m, o);
-                m = y < m ? y : m;
-            }
-            if (m == INT32_MAX) break;
-            const bool hit = head == m;
-            const unsigned mask = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const int p = pos + __popc(mask & lt_mask);
-                const int chunk = p >> 5;
-                if (chunk != last_chunk) {
-                    last_chunk = chunk;
-                    count = 0;
-                }
-                const int slot = count++;
-                if (slot > maxslot) maxslot = slot;
-                const uint32_t sl = static_cast<uint32_t>(slot < kMaxSlots ? slot : 0);
-                layout[base + p] = (static_cast<uint32_t>(src[cur]) << 8) | (sl << 5) |
-                                   (static_cast<uint32_t>(lane) ^ sl);
-                ++cur;
-            }
-            pos += __popc(mask);
-        }
-        const int padded = (pos + 31) & ~31;
-        if (pos + lane < padded) layout[base + pos + lane] = kPadEntry;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const int y = __shfl_xor_sync(0xffffffffu, maxslot, o);
-            maxslot = y > maxslot ? y : maxslot;
-        }
-        if (lane == 0) meta[t] = maxslot < kMaxSlots ? static_cast<uint8_t>(maxslot + 1) : 0;
-    } while (false);
-    __syncwarp();
+    }
+    const int padded = (k + kU - 1) / kU * kU;
+    if (k + lane < padded) out[k + lane] = make_uint2(0u, 0u);
+    if (lane == 0) cnt[t] = padded;
 }
 
 __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout(
     const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx, int64_t n,
-    uint32_t *__restrict__ layout, uint8_t *__restrict__ meta) {
-    __shared__ int32_t s_src[kLayoutThreads / 32][kSortCap];
+    uint2 *__restrict__ desc, int32_t *__restrict__ cnt) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t ntiles = (n + 31) >> 5;
     const int64_t step = int64_t(gridDim.x) * (kLayoutThreads / 32);
     for (int64_t t = int64_t(blockIdx.x) * (kLayoutThreads / 32) + warp; t < ntiles; t += step)
-        layout_tiles(in_ptr, in_idx, n, layout, meta, t, s_src[warp], lane);
+        layout_tile(in_ptr, in_idx, n, desc, cnt, t, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -358,48 +353,40 @@ __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout(
 // ---------------------------------------------------------------------------
 template <typename T>
 struct TileInfo {
-    int64_t t, e0, e1;  // tile index, in-edge range
-    int nslots;         // accumulator slots (0 = CSR path)
-    int32_t od;         // out-degree of this lane's row
-    T wv;               // w of this lane's row
-    __device__ __forceinline__ int nch() const { return static_cast<int>((e1 - e0 + 31) >> 5); }
-    __device__ __forceinline__ int64_t chunk0() const { return (e0 >> 5) + t; }
+    int64_t dbeg;  // first descriptor
+    int cnt;       // descriptors (multiple of kU)
+    int32_t od;    // out-degree of this lane's row
+    T wv;          // w of this lane's row
 };
 
 template <typename T>
-__device__ __forceinline__ TileInfo<T> load_info(int64_t t, int64_t n,
-                                                 const int64_t *__restrict__ in_ptr,
-                                                 const uint8_t *__restrict__ meta,
+__device__ __forceinline__ TileInfo<T> load_info(int t, int n, const int64_t *__restrict__ in_ptr,
+                                                 const int32_t *__restrict__ cnt,
                                                  const int32_t *__restrict__ outdeg, const T *wc,
                                                  int lane) {
     TileInfo<T> ti;
-    const int64_t r0 = t << 5;
-    const int64_t rend = r0 + 32 < n ? r0 + 32 : n;
-    const int64_t v = r0 + lane;
-    ti.t = t;
-    ti.e0 = __ldg(in_ptr + r0);
-    ti.e1 = __ldg(in_ptr + rend);
-    ti.nslots = __ldg(meta + t);
-    ti.od = v < rend ? __ldg(outdeg + v) : 0;
-    ti.wv = v < rend ? wc[v] : T(0);
+    const int v = (t << 5) + lane;  // n < 2^31
+    ti.dbeg = desc_begin(__ldg(in_ptr + (t << 5)), t);
+    ti.cnt = __ldg(cnt + t);
+    ti.od = v < n ? __ldg(outdeg + v) : 0;
+    ti.wv = v < n ? wc[v] : T(0);
     return ti;
 }
 
-// Per-warp TMA stream of packed chunk segments into a two-buffer stage.
+// Per-warp TMA stream of descriptor segments into a two-buffer stage.
 // `pending` has bit b set while a copy into buffer b is outstanding.
 struct Stream {
-    uint32_t *stage;   // [2][kSeg * 32]
+    uint2 *stage;      // [2][kSegD]
     uint64_t *bar;     // [2]
     uint32_t phase;    // bit b = parity of the next completion on buffer b
     uint32_t pending;  // bit b = a copy into buffer b is outstanding
     int buf;           // buffer of the segment to process next
     bool issued;       // the segment for `buf` has been issued
-    __device__ __forceinline__ void issue(const uint32_t *layout, int64_t chunk, int cnt, int b,
-                                          int lane) {
-        if (lane == 0) {
-            tma_load(stage + b * (kSeg * 32), layout + chunk * 32, static_cast<uint32_t>(cnt) * 128u,
-                     bar + b);
-        }
+    // copy `count` descriptors (a multiple of kU: 64-byte multiples, 64-byte
+    // aligned source) into buffer b
+    __device__ __forceinline__ void issue(const uint2 *src, int count, int b, int lane) {
+        if (lane == 0)
+            tma_load(stage + b * kSegD, src, static_cast<uint32_t>(count) * 8u, bar + b);
         pending |= 1u << b;
     }
     // bounded wait on buffer b, uniform over the warp; false on timeout
@@ -418,117 +405,81 @@ struct Stream {
     }
 };
 
-// Sum over the rows of a packed tile (lane = row), streaming its chunks in
-// segments of kSeg; the segment after the current one (or the first segment
-// of the next tile) is copied while the current one is gathered.
+// Sum over the in-edges of this lane's row (wrow = w + row): the tile's
+// descriptors stream in segments of kSegD; the segment after the current one
+// (or the first segment of the next tile) is copied while the current one is
+// gathered.  kU descriptors per step: kU independent gathers per lane.
 template <typename T>
-__device__ __forceinline__ bool tile_sum_packed(const uint32_t *__restrict__ layout,
-                                                const TileInfo<T> &cur, const TileInfo<T> &nxt,
-                                                bool has_next, Stream &st, const T *wc, T *acc,
-                                                int lane, T &sum) {
-    const int nch = cur.nch();
-    for (int k = 0; k < cur.nslots; ++k) acc[(k << 5) | (lane ^ k)] = T(0);
-    __syncwarp();
-    const int nseg = (nch + kSeg - 1) / kSeg;
-    const bool next_packed = has_next && nxt.nslots > 0 && nxt.nch() > 0;
-    for (int s = 0; s < nseg; ++s) {
-        const int c0 = s * kSeg;
-        const int cnt = nch - c0 < kSeg ? nch - c0 : kSeg;
-        if (!st.issued) st.issue(layout, cur.chunk0() + c0, cnt, st.buf, lane);
-        // prefetch the following segment into the other buffer
-        if (s + 1 < nseg) {
-            const int c1 = c0 + kSeg;
-            st.issue(layout, cur.chunk0() + c1, nch - c1 < kSeg ? nch - c1 : kSeg, st.buf ^ 1,
-                     lane);
+__device__ __forceinline__ bool tile_sum(const uint2 *__restrict__ desc, const TileInfo<T> &cur,
+                                         const TileInfo<T> &nxt, bool has_next, Stream &st,
+                                         const T *wrow, uint32_t bit, int lane, T &sum) {
+    const int cnt = cur.cnt;
+    const int nseg = (cnt + kSegD - 1) / kSegD;
+    const bool next_any = has_next && nxt.cnt > 0;
+    T s = T(0);
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int c0 = sg * kSegD;
+        const int m = cnt - c0 < kSegD ? cnt - c0 : kSegD;
+        if (!st.issued) st.issue(desc + cur.dbeg + c0, m, st.buf, lane);
+        if (sg + 1 < nseg) {
+            const int c1 = c0 + kSegD;
+            st.issue(desc + cur.dbeg + c1, cnt - c1 < kSegD ? cnt - c1 : kSegD, st.buf ^ 1, lane);
             st.issued = true;
-        } else if (next_packed) {
-            const int n1 = nxt.nch();
-            st.issue(layout, nxt.chunk0(), n1 < kSeg ? n1 : kSeg, st.buf ^ 1, lane);
+        } else if (next_any) {
+            st.issue(desc + nxt.dbeg, nxt.cnt < kSegD ? nxt.cnt : kSegD, st.buf ^ 1, lane);
             st.issued = true;
         } else {
             st.issued = false;
         }
         if (!st.wait(st.buf)) return false;
-        const uint32_t *ent = st.stage + st.buf * (kSeg * 32) + lane;
-        for (int g0 = 0; g0 < cnt; g0 += kGroup) {
-            uint32_t e[kGroup];
-            T val[kGroup];
+        const uint4 *q = reinterpret_cast<const uint4 *>(st.stage + st.buf * kSegD);
+        for (int k = 0; k < m; k += kU) {
+            T v[kU];
 #pragma unroll
-            for (int g = 0; g < kGroup; ++g) e[g] = g0 + g < cnt ? ent[(g0 + g) * 32] : kPadEntry;
-#pragma unroll
-            for (int g = 0; g < kGroup; ++g) val[g] = wc[e[g] >> 8];
-#pragma unroll
-            for (int g = 0; g < kGroup; ++g) {
-                acc[e[g] & 0xffu] += val[g];
-                __syncwarp();
+            for (int j = 0; j < kU / 2; ++j) {
+                const uint4 d = q[(k >> 1) + j];  // two descriptors, same for every lane
+                v[2 * j] = (d.y & bit) ? wrow[static_cast<int32_t>(d.x)] : T(0);
+                v[2 * j + 1] = (d.w & bit) ? wrow[static_cast<int32_t>(d.z)] : T(0);
             }
+#pragma unroll
+            for (int h = kU / 2; h > 0; h >>= 1)  // pairwise: depth log2(kU)
+#pragma unroll
+                for (int j = 0; j < h; ++j) v[j] += v[j + h];
+            s += v[0];
         }
         st.buf ^= 1;
     }
-    if (nseg == 0 && !st.issued && next_packed) {
-        const int n1 = nxt.nch();
-        st.issue(layout, nxt.chunk0(), n1 < kSeg ? n1 : kSeg, st.buf, lane);
+    if (nseg == 0 && !st.issued && next_any) {
+        st.issue(desc + nxt.dbeg, nxt.cnt < kSegD ? nxt.cnt : kSegD, st.buf, lane);
         st.issued = true;
     }
-    T s = T(0);
-    for (int k = 0; k < cur.nslots; ++k) s += acc[(k << 5) | (lane ^ k)];
-    __syncwarp();
     sum = s;
     return true;
 }
 
-// CSR path of one tile: the tile's in-edges [e0, e1) are streamed in windows
-// with coalesced in_idx loads, gathered into shared memory, and each lane
-// adds the part of its own row [p, p_next) that lies in the window.
-template <typename T>
-__device__ __forceinline__ T tile_sum_csr(const int32_t *__restrict__ in_idx, const T *wc,
-                                          T *buf, int64_t p, int64_t p_next, int64_t e0,
-                                          int64_t e1, int lane) {
-    T s = T(0);
-    for (int64_t ws = e0; ws < e1; ws += kAccElems) {
-        const int n = static_cast<int>(e1 - ws < kAccElems ? e1 - ws : kAccElems);
-        const int32_t *src = in_idx + ws;
-        int i = lane;
-        for (; i + 96 < n; i += 128) {
-            const int32_t j0 = __ldg(src + i), j1 = __ldg(src + i + 32);
-            const int32_t j2 = __ldg(src + i + 64), j3 = __ldg(src + i + 96);
-            const T a0 = wc[j0], a1 = wc[j1], a2 = wc[j2], a3 = wc[j3];
-            buf[i] = a0;
-            buf[i + 32] = a1;
-            buf[i + 64] = a2;
-            buf[i + 96] = a3;
-        }
-        for (; i < n; i += 32) buf[i] = wc[__ldg(src + i)];
-        __syncwarp();
-        const int64_t a = p > ws ? p : ws;
-        const int64_t b = p_next < ws + n ? p_next : ws + n;
-        for (int64_t e = a; e < b; ++e) s += buf[e - ws];
-        __syncwarp();
-    }
-    return s;
-}
-
 // First tile of part w when the tiles are split into nw contiguous ranges of
-// about equal cost (in-edges plus kRowCost per row).
-__device__ __forceinline__ int64_t tile_split(const int64_t *__restrict__ in_ptr, int64_t n,
-                                              int64_t ntiles, int64_t w, int64_t nw) {
+// about equal cost; a tile costs its descriptors plus kTileCost (the time
+// per tile is close to linear in these two).  tpre: prefix sums of the
+// descriptor counts (any base).
+__device__ __forceinline__ int64_t tile_split(const int64_t *__restrict__ tpre, int64_t ntiles,
+                                              int64_t w, int64_t nw) {
     if (w <= 0) return 0;
     if (w >= nw) return ntiles;
-    const int64_t total = __ldg(in_ptr + n) + kRowCost * n;
+    const int64_t base = __ldg(tpre);
+    const int64_t total = __ldg(tpre + ntiles) - base + kTileCost * ntiles;
     const int64_t target = total / nw * w + (total % nw) * w / nw;
     int64_t lo = 0, hi = ntiles;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        const int64_t r = mid << 5 < n ? mid << 5 : n;
-        if (__ldg(in_ptr + r) + kRowCost * r >= target) hi = mid;
+        if (__ldg(tpre + mid) - base + kTileCost * mid >= target) hi = mid;
         else lo = mid + 1;
     }
     return lo;
 }
 
-template <typename T>
+template <int W>
 constexpr size_t pr_smem_bytes() {
-    return size_t(kWarps) * (2 * kSeg * 32 * sizeof(uint32_t) + kAccElems * sizeof(T) + 16);
+    return size_t(W) * (2 * kSegD * sizeof(uint2) + 16);
 }
 
 // One PageRank job: a graph, its layout, its buffers and its parameters.
@@ -536,12 +487,11 @@ constexpr size_t pr_smem_bytes() {
 // job's own bounded barrier in `ctl`.
 struct JobDev {
     const int64_t *in_ptr;
-    const int32_t *in_idx;
     const int32_t *outdeg;
-    const uint32_t *layout;
-    const uint8_t *meta;
+    const uint2 *desc;
+    const int32_t *cnt;
+    const int64_t *tpre;
     void *ranks, *w0, *w1;
-    long long *partials;  // [2][group][4]
     PrCtl *ctl;
     int64_t n;
     double alpha, tol;
@@ -550,41 +500,73 @@ struct JobDev {
 
 // A group of blocks runs all iterations of one job.  Returns false if the
 // block must stop (a bounded wait expired).
+// Loop state of a job, kept by thread 0 in shared memory: the tile loop
+// holds none of it in registers.
+struct LoopState {
+    double res, prev_res, xs;
+    int it, stop, converged, pad;
+};
+
+// thread 0, after the barrier of a phase: read the job's sums, decide
+// whether to stop, and publish the next teleport term
 template <typename T>
-__device__ bool run_job(const JobDev &J, int rank, Stream &st, T *acc) {
+__device__ __forceinline__ void advance(const JobDev &J, LoopState &ls, const PrCtl *ctl, int buf,
+                                        T *s_c, bool count_iter) {
+    const double r = static_cast<double>(__ldcg(&ctl->acc[buf][0])) / kFix;
+    const double d = static_cast<double>(__ldcg(&ctl->acc[buf][1])) / kFix;
+    const double x = static_cast<double>(__ldcg(&ctl->acc[buf][2])) / kFix;
+    ls.xs = x;
+    *s_c = static_cast<T>((J.alpha * d + 1.0 - J.alpha) / static_cast<double>(J.n));
+    if (!count_iter) return;  // the prologue: no iteration yet
+    ls.prev_res = ls.res;
+    ls.res = r;
+    ++ls.it;
+    if (r < J.tol) ls.converged = ls.stop = 1;
+    else if (sizeof(T) == 4 && r >= ls.prev_res) ls.converged = ls.stop = 1;  // FP32 floor
+    else if (ls.it >= J.max_iter) ls.stop = 1;
+}
+
+// A group of blocks runs all iterations of one job.  Returns false if the
+// block must stop (a bounded wait expired).
+template <typename T, int W>
+__device__ bool run_job(const JobDev &J, int rank, Stream &st) {
+    constexpr int kThreads = 32 * W;
     const int64_t *__restrict__ in_ptr = J.in_ptr;
-    const int32_t *__restrict__ in_idx = J.in_idx;
     const int32_t *__restrict__ outdeg = J.outdeg;
-    const uint32_t *__restrict__ layout = J.layout;
-    const uint8_t *__restrict__ meta = J.meta;
+    const uint2 *__restrict__ desc = J.desc;
+    const int32_t *__restrict__ tcnt = J.cnt;
     const int64_t n = J.n;
     const int nb = J.group;
-    T *ranks = static_cast<T *>(J.ranks);
     T *w0 = static_cast<T *>(J.w0), *w1 = static_cast<T *>(J.w1);
-    long long *partials = J.partials;
     PrCtl *ctl = J.ctl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     const int64_t ntiles = (n + 31) >> 5;
     // the block's contiguous tile range (about equal cost per block); its
     // warps take tiles from it in turn through a shared counter
-    __shared__ int64_t s_range[2];
-    __shared__ unsigned long long s_next;
+    __shared__ int s_range[2];
+    __shared__ unsigned s_next;
+    __shared__ LoopState s_ls;
+    __shared__ T s_c;
     __syncthreads();
     if (threadIdx.x == 0) {
-        s_range[0] = tile_split(in_ptr, n, ntiles, rank, nb);
-        s_range[1] = tile_split(in_ptr, n, ntiles, rank + 1, nb);
-        s_next = static_cast<unsigned long long>(s_range[0] + kWarps);
+        s_range[0] = static_cast<int>(tile_split(J.tpre, ntiles, rank, nb));
+        s_range[1] = static_cast<int>(tile_split(J.tpre, ntiles, rank + 1, nb));
+        s_next = static_cast<unsigned>(s_range[0] + W);
+        s_ls.res = __longlong_as_double(0x7ff0000000000000LL);
+        s_ls.it = s_ls.stop = s_ls.converged = 0;
     }
     __syncthreads();
-    const int64_t bt0 = s_range[0], bt1 = s_range[1];
-    const double inv_n = 1.0 / static_cast<double>(n);
+    const int bt0 = s_range[0], bt1 = s_range[1];
+    const int ni = static_cast<int>(n);
 
     // prologue: w from the start vector, D_0 and sum x_0 (grid-stride)
     {
+        const double inv_n = 1.0 / static_cast<double>(n);
+        const T *ranks = static_cast<const T *>(J.ranks);
         Fix3 acc0;
-        const int64_t stride = int64_t(nb) * kPrThreads;
-        for (int64_t v = int64_t(rank) * kPrThreads + threadIdx.x; v < n; v += stride) {
+        const int64_t stride = int64_t(nb) * kThreads;
+        for (int64_t v = int64_t(rank) * kThreads + threadIdx.x; v < n; v += stride) {
             const double x0 = J.init ? static_cast<double>(ranks[v]) : inv_n;
             const int32_t od = __ldg(outdeg + v);
             w0[v] = static_cast<T>(od ? x0 / od : x0);
@@ -592,59 +574,40 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st, T *acc) {
             if (od == 0) acc0.d += q;
             acc0.s += q;
         }
-        const Fix3 b = block_sum_fix(acc0);
-        if (threadIdx.x == 0) {
-            long long *p = partials + 4 * rank;
-            p[0] = 0;
-            p[1] = b.d;
-            p[2] = b.s;
-        }
+        const Fix3 b = block_sum_fix<W>(acc0);
+        if (threadIdx.x == 0) publish(ctl, 0, b, rank);
     }
     unsigned phase = 1;
+    int buf = 0;
     if (!group_barrier(ctl, phase * nb, nb)) return false;
-    Tot tot = sum_partials(partials, nb);
-    double dang = tot.d, xs = tot.s;
-    double res = __longlong_as_double(0x7ff0000000000000LL), prev_res = res;
-    int it = 0, converged = 0;
+    if (threadIdx.x == 0) advance<T>(J, s_ls, ctl, buf, &s_c, false);
+    __syncthreads();
     T *wc = w0, *wn = w1;
-    int par = 0;
-    const double alpha = J.alpha;
-    const T a = static_cast<T>(alpha);
+    const T a = static_cast<T>(J.alpha);
     int failed = 0;
+    const int t0 = bt0 + warp;  // this warp's first tile in every iteration
+    TileInfo<T> pre;                // ... loaded ahead (have_pre)
+    bool have_pre = false;
     while (true) {
-        const T c = static_cast<T>((alpha * dang + 1.0 - alpha) * inv_n);
+        const T c = s_c;
         Fix3 facc;
-        int64_t t = bt0 + warp;
+        int t = t0;
         if (t < bt1 && !failed) {
-            TileInfo<T> cur = load_info<T>(t, n, in_ptr, meta, outdeg, wc, lane);
+            TileInfo<T> cur = have_pre ? pre : load_info<T>(t, ni, in_ptr, tcnt, outdeg, wc, lane);
             while (true) {
-                unsigned long long g = 0;
-                if (lane == 0) g = atomicAdd(&s_next, 1ULL);
-                const int64_t tn = static_cast<int64_t>(__shfl_sync(0xffffffffu, g, 0));
+                unsigned g = 0;
+                if (lane == 0) g = atomicAdd(&s_next, 1u);
+                const int tn = static_cast<int>(__shfl_sync(0xffffffffu, g, 0));
                 const bool has_next = tn < bt1;
                 TileInfo<T> nxt = cur;
-                if (has_next) nxt = load_info<T>(tn, n, in_ptr, meta, outdeg, wc, lane);
-                const int64_t v = (t << 5) + lane;
-                const bool row_ok = v < n;
+                if (has_next) nxt = load_info<T>(tn, ni, in_ptr, tcnt, outdeg, wc, lane);
+                const int v = (t << 5) + lane;
                 T s = T(0);
-                if (cur.nslots > 0) {
-                    if (!tile_sum_packed<T>(layout, cur, nxt, has_next, st, wc, acc, lane, s)) {
-                        failed = 1;
-                        break;
-                    }
-                } else {
-                    const int64_t p = row_ok ? __ldg(in_ptr + v) : cur.e1;
-                    int64_t p_next = __shfl_down_sync(0xffffffffu, p, 1);
-                    if (lane == 31 || v + 1 >= n) p_next = cur.e1;
-                    // the next packed tile's first segment streams in meanwhile
-                    if (!st.issued && has_next && nxt.nslots > 0 && nxt.nch() > 0) {
-                        const int n1 = nxt.nch();
-                        st.issue(layout, nxt.chunk0(), n1 < kSeg ? n1 : kSeg, st.buf, lane);
-                        st.issued = true;
-                    }
-                    s = tile_sum_csr<T>(in_idx, wc, acc, p, p_next, cur.e0, cur.e1, lane);
+                if (!tile_sum<T>(desc, cur, nxt, has_next, st, wc + v, 1u << lane, lane, s)) {
+                    failed = 1;
+                    break;
                 }
-                if (row_ok) {
+                if (v < ni) {
                     const T xo = cur.od ? cur.wv * static_cast<T>(cur.od) : cur.wv;
                     const T xn = a * s + c;
                     facc.r += to_fix(xn > xo ? xn - xo : xo - xn);
@@ -664,43 +627,55 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st, T *acc) {
             if (lane == 0) atomicCAS(&ctl->status, 0, (int)FFG_ERR_TIMEOUT);
             failed = 2;
         }
-        const Fix3 b = block_sum_fix(facc);
-        par ^= 1;
-        long long *pp = partials + size_t(par) * nb * 4;
+        const Fix3 b = block_sum_fix<W>(facc);
+        // The block's rows of w' are written (block barrier above), so the
+        // next iteration's first tile -- in this block's range -- loads its
+        // row data and its first descriptor segment while the grid barrier
+        // completes.  Unused if the solve stops here (drained below).
+        have_pre = false;
+        if (t0 < bt1 && !failed) {
+            pre = load_info<T>(t0, ni, in_ptr, tcnt, outdeg, wn, lane);
+            if (pre.cnt > 0 && !st.issued) {
+                st.issue(desc + pre.dbeg, pre.cnt < kSegD ? pre.cnt : kSegD, st.buf, lane);
+                st.issued = true;
+            }
+            have_pre = true;
+        }
+        buf = buf == 2 ? 0 : buf + 1;
         if (threadIdx.x == 0) {
-            long long *p = pp + 4 * rank;
-            p[0] = b.r;
-            p[1] = b.d;
-            p[2] = b.s;
-            s_next = static_cast<unsigned long long>(bt0 + kWarps);  // next iteration's counter
+            publish(ctl, buf, b, rank);
+            s_next = static_cast<unsigned>(bt0 + W);  // next iteration's counter
         }
         ++phase;
-        if (!group_barrier(ctl, phase * nb, nb)) return false;
-        tot = sum_partials(pp, nb);
-        prev_res = res;
-        res = tot.r;
-        dang = tot.d;
-        xs = tot.s;
-        ++it;
+        if (!group_barrier(ctl, phase * nb, nb)) {
+            st.drain();
+            st.issued = false;
+            return false;
+        }
+        if (threadIdx.x == 0) advance<T>(J, s_ls, ctl, buf, &s_c, true);
+        __syncthreads();
         T *tmp = wc;
         wc = wn;
         wn = tmp;
-        if (res < J.tol) { converged = 1; break; }
-        if (sizeof(T) == 4 && res >= prev_res) { converged = 1; break; }  // FP32 rounding floor
-        if (it >= J.max_iter) break;
+        if (s_ls.stop) break;
+    }
+    if (st.issued) {  // a segment loaded ahead for an iteration that did not run
+        st.drain();
+        st.issued = false;
     }
     // epilogue: x' normalised to sum 1
-    const double inv_s = 1.0 / xs;
-    const int64_t stride = int64_t(nb) * kPrThreads;
-    for (int64_t v = int64_t(rank) * kPrThreads + threadIdx.x; v < n; v += stride) {
+    const double inv_s = 1.0 / s_ls.xs;
+    T *ranks = static_cast<T *>(J.ranks);
+    const int64_t stride = int64_t(nb) * kThreads;
+    for (int64_t v = int64_t(rank) * kThreads + threadIdx.x; v < n; v += stride) {
         const int32_t od = __ldg(outdeg + v);
         const double x = od ? static_cast<double>(wc[v]) * od : static_cast<double>(wc[v]);
         ranks[v] = static_cast<T>(x * inv_s);
     }
     if (rank == 0 && threadIdx.x == 0) {
-        ctl->iters = it;
-        ctl->residual = res;
-        ctl->converged = converged;
+        ctl->iters = s_ls.it;
+        ctl->residual = s_ls.res;
+        ctl->converged = s_ls.converged;
         ctl->nblocks = nb;
     }
     return failed == 0;
@@ -710,19 +685,16 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st, T *acc) {
 // grid; otherwise block b runs the plan items [first[b], first[b+1]) in
 // order -- (job, rank) pairs, each block's multi-block job first, so that
 // no two groups ever wait on each other.
-template <typename T>
-__global__ void __launch_bounds__(kPrThreads, FFG_PR_MINBLOCKS)
+template <typename T, int W>
+__global__ void __launch_bounds__(32 * W, W >= 24 ? 1 : FFG_PR_MINBLOCKS)
     k_pagerank(const JobDev *__restrict__ jobs, const int2 *__restrict__ items,
                const int *__restrict__ first, int plan_blocks, JobDev single) {
     extern __shared__ __align__(128) unsigned char s_dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // shared memory: per-warp stages, then accumulators, then mbarriers
+    // shared memory: per-warp stages, then mbarriers
     Stream st;
-    st.stage = reinterpret_cast<uint32_t *>(s_dyn) + size_t(warp) * 2 * kSeg * 32;
-    T *acc = reinterpret_cast<T *>(s_dyn + size_t(kWarps) * 2 * kSeg * 32 * sizeof(uint32_t)) +
-             size_t(warp) * kAccElems;
-    st.bar = reinterpret_cast<uint64_t *>(s_dyn + size_t(kWarps) * 2 * kSeg * 32 * sizeof(uint32_t) +
-                                          size_t(kWarps) * kAccElems * sizeof(T)) +
+    st.stage = reinterpret_cast<uint2 *>(s_dyn) + size_t(warp) * 2 * kSegD;
+    st.bar = reinterpret_cast<uint64_t *>(s_dyn + size_t(W) * 2 * kSegD * sizeof(uint2)) +
              2 * warp;
     st.phase = 0;
     st.pending = 0;
@@ -735,14 +707,14 @@ __global__ void __launch_bounds__(kPrThreads, FFG_PR_MINBLOCKS)
     }
     __syncwarp();
     if (jobs == nullptr) {
-        run_job<T>(single, blockIdx.x, st, acc);
+        run_job<T, W>(single, blockIdx.x, st);
         return;
     }
     if (static_cast<int>(gridDim.x) != plan_blocks) return;  // the host checks this too
     for (int i = first[blockIdx.x]; i < first[blockIdx.x + 1]; ++i) {
         const int2 item = items[i];
         const JobDev J = jobs[item.x];
-        if (!run_job<T>(J, item.y, st, acc)) return;
+        if (!run_job<T, W>(J, item.y, st)) return;
     }
 }
 
@@ -751,8 +723,8 @@ __global__ void __launch_bounds__(kPrThreads, FFG_PR_MINBLOCKS)
 struct GraphDev {
     const int64_t *in_ptr;
     const int32_t *in_idx;
-    uint32_t *layout;
-    uint8_t *meta;
+    uint2 *desc;
+    int32_t *cnt;
     int64_t n;
     int64_t tile0;  // first global tile of this graph
 };
@@ -760,7 +732,6 @@ struct GraphDev {
 __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout_batch(const GraphDev *__restrict__ gr,
                                                                      int n_graphs,
                                                                      int64_t total_tiles) {
-    __shared__ int32_t s_src[kLayoutThreads / 32][kSortCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t step = int64_t(gridDim.x) * (kLayoutThreads / 32);
     for (int64_t gt = int64_t(blockIdx.x) * (kLayoutThreads / 32) + warp; gt < total_tiles;
@@ -772,7 +743,7 @@ __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout_batch(const GraphD
             else hi = mid - 1;
         }
         const GraphDev g = gr[lo];
-        layout_tiles(g.in_ptr, g.in_idx, g.n, g.layout, g.meta, gt - g.tile0, s_src[warp], lane);
+        layout_tile(g.in_ptr, g.in_idx, g.n, g.desc, g.cnt, gt - g.tile0, lane);
     }
 }
 
@@ -785,36 +756,38 @@ ffg_status launch_layout(const ffg_graph *g, PrWs &w, cudaStream_t stream) {
     const int64_t want = (tiles + kLayoutThreads / 32 - 1) / (kLayoutThreads / 32);
     const int64_t cap = int64_t(sms) * 32;
     const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
-    k_pr_layout<<<grid, kLayoutThreads, 0, stream>>>(g->in_ptr, g->in_idx, n, w.layout, w.meta);
+    k_pr_layout<<<grid, kLayoutThreads, 0, stream>>>(g->in_ptr, g->in_idx, n, w.desc, w.cnt);
     count_launch();
-    return check_launch("k_pr_layout");
+    FFG_TRY(check_launch("k_pr_layout"));
+    // tile cost prefix for the block split
+    return scan_exclusive(w.cnt, w.tpre, tiles, w.scan, stream);
 }
 
-template <typename T>
+template <typename T, int W>
 ffg_status kernel_config(int *blocks_per_sm, int *sms) {
     int dev = 0;
     FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
     FFG_TRY(check_cuda(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
-    auto kern = k_pagerank<T>;
-    const size_t smem = pr_smem_bytes<T>();
+    auto kern = k_pagerank<T, W>;
+    const size_t smem = pr_smem_bytes<W>();
     FFG_TRY(check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             static_cast<int>(smem)),
                        "smem attribute"));
     FFG_TRY(check_cuda(
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, kPrThreads, smem),
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, 32 * W, smem),
         "occupancy"));
     if (*blocks_per_sm < 1) return set_error("kernel does not fit on the device"), FFG_ERR_CUDA;
     return FFG_OK;
 }
 
-template <typename T>
+template <typename T, int W>
 ffg_status launch_pr(const JobDev *jobs, const int2 *items, const int *first, int nb,
                      const JobDev &single, cudaStream_t stream) {
-    auto kern = k_pagerank<T>;
-    const size_t smem = pr_smem_bytes<T>();
+    auto kern = k_pagerank<T, W>;
+    const size_t smem = pr_smem_bytes<W>();
     JobDev s = single;
     void *args[] = {(void *)&jobs, (void *)&items, (void *)&first, (void *)&nb, (void *)&s};
-    FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)kern, dim3(nb), dim3(kPrThreads),
+    FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)kern, dim3(nb), dim3(32 * W),
                                                    args, smem, stream),
                        "k_pagerank"));
     count_launch();
@@ -824,23 +797,23 @@ ffg_status launch_pr(const JobDev *jobs, const int2 *items, const int *first, in
 template <typename T>
 ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, int init,
                   T *ranks, PrWs &w, cudaStream_t stream) {
+    constexpr int W = kWarpsSingle;
     int per_sm = 0, sms = 0;
-    FFG_TRY(kernel_config<T>(&per_sm, &sms));
+    FFG_TRY((kernel_config<T, W>(&per_sm, &sms)));
     const int64_t tiles = (g->n_nodes + 31) / 32;
     int64_t max_res = int64_t(sms) * per_sm;
     if (max_res > kMaxBlocks) max_res = kMaxBlocks;
-    const int64_t want = (tiles + 4 * kWarps - 1) / (4 * kWarps);  // >= ~4 tiles per warp
+    const int64_t want = (tiles + 4 * W - 1) / (4 * W);  // >= ~4 tiles per warp
     const int nb = static_cast<int>(want < 1 ? 1 : (want > max_res ? max_res : want));
     JobDev J;
     J.in_ptr = g->in_ptr;
-    J.in_idx = g->in_idx;
     J.outdeg = g->outdeg;
-    J.layout = w.layout;
-    J.meta = w.meta;
+    J.desc = w.desc;
+    J.cnt = w.cnt;
+    J.tpre = w.tpre;
     J.ranks = ranks;
     J.w0 = w.w0;
     J.w1 = w.w1;
-    J.partials = w.partials;
     J.ctl = w.ctl;
     J.n = g->n_nodes;
     J.alpha = alpha;
@@ -849,7 +822,7 @@ ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, in
     J.init = init;
     J.group = nb;
     J.pad = 0;
-    return launch_pr<T>(nullptr, nullptr, nullptr, nb, J, stream);
+    return launch_pr<T, W>(nullptr, nullptr, nullptr, nb, J, stream);
 }
 
 ffg_status read_result(const PrCtl *dctl, int32_t *iters_out, double *residual_out,
@@ -1003,7 +976,7 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, const ffg_p
         P.graph_of_job[j] = it->second;
         cost[j] = double(g->n_edges + kRowCost * g->n_nodes) * est_iters(jobs[j].damping);
         const int64_t tiles = (g->n_nodes + 31) / 32;
-        useful += std::max<int64_t>(1, (tiles + 4 * kWarps - 1) / (4 * kWarps));
+        useful += std::max<int64_t>(1, (tiles + 4 * kWarpsBatch - 1) / (4 * kWarpsBatch));
     }
     int cap = nb_max;
     if (tu.max_blocks > 0 && tu.max_blocks < cap) cap = tu.max_blocks;
@@ -1025,7 +998,7 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, const ffg_p
         int k = cost[j] > tu.split * share
                     ? static_cast<int>(std::llround(cost[j] / (tu.grain * share)))
                     : 1;
-        k = static_cast<int>(std::min<int64_t>(k, std::max<int64_t>(1, tiles / kWarps)));
+        k = static_cast<int>(std::min<int64_t>(k, std::max<int64_t>(1, tiles / kWarpsBatch)));
         k = std::min(k, nb - next_block);
         if (k >= 2) {
             P.group[j] = k;
@@ -1065,10 +1038,13 @@ struct BatchWs {
     int *first;
     int2 *items;
     PrCtl *ctl;
+    int32_t *cnt;    // per tile of every graph
+    int64_t *tpre;   // its prefix sums
+    int64_t *scan;   // scan scratch
     size_t bytes;
 };
 
-// Workspace of a plan: tables, then per job ctl / partials / w buffers, then
+// Workspace of a plan: tables, then per job ctl / w buffers, then
 // per distinct graph the layout and tile metadata.  host_jobs / host_graphs
 // (if non-NULL) receive the device pointers of every job and graph.
 BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
@@ -1083,14 +1059,20 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
     w.first = c.take<int>(size_t(nb_max) + 1);
     w.items = c.take<int2>(size_t(n_jobs) + nb_max);
     w.ctl = c.take<PrCtl>(n_jobs);
+    int64_t total_tiles = 0;
+    for (const ffg_graph *g : P.graphs) total_tiles += (g->n_nodes + 31) / 32;
+    // per-tile descriptor counts of all graphs in one array, scanned at once
+    w.cnt = c.take<int32_t>(size_t(total_tiles));
+    w.tpre = c.take<int64_t>(size_t(total_tiles) + 1);
+    w.scan = c.take<int64_t>(size_t(scan_scratch_elems(total_tiles)));
     std::vector<GraphDev> gd(P.graphs.size());
     int64_t tile0 = 0;
     for (size_t k = 0; k < P.graphs.size(); ++k) {
         const ffg_graph *g = P.graphs[k];
         gd[k].in_ptr = g->in_ptr;
         gd[k].in_idx = g->in_idx;
-        gd[k].layout = c.take<uint32_t>(size_t(layout_chunks(g->n_nodes, g->n_edges)) * 32);
-        gd[k].meta = c.take<uint8_t>(size_t((g->n_nodes + 31) / 32));
+        gd[k].desc = c.take<uint2>(size_t(desc_capacity(g->n_nodes, g->n_edges)));
+        gd[k].cnt = w.cnt + tile0;
         gd[k].n = g->n_nodes;
         gd[k].tile0 = tile0;
         tile0 += (g->n_nodes + 31) / 32;
@@ -1101,16 +1083,13 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
         const GraphDev &G = gd[P.graph_of_job[j]];
         JobDev &J = jd[j];
         J.in_ptr = g->in_ptr;
-        J.in_idx = g->in_idx;
         J.outdeg = g->outdeg;
-        J.layout = G.layout;
-        J.meta = G.meta;
+        J.desc = G.desc;
+        J.cnt = G.cnt;
+        J.tpre = w.tpre + G.tile0;
         J.ranks = jobs[j].ranks;
         J.w0 = c.take<char>(size_t(g->n_nodes) * elem);
         J.w1 = c.take<char>(size_t(g->n_nodes) * elem);
-        // sized for any group (<= nb_max): the workspace size does not depend
-        // on the tuning
-        J.partials = c.take<long long>(size_t(2) * nb_max * 4);
         J.ctl = w.ctl + j;
         J.n = g->n_nodes;
         J.alpha = jobs[j].damping;
@@ -1128,8 +1107,8 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
 
 ffg_status batch_blocks(ffg_prec prec, int *nb_max) {
     int per_sm = 0, sms = 0;
-    if (prec == FFG_F64) FFG_TRY(kernel_config<double>(&per_sm, &sms));
-    else FFG_TRY(kernel_config<float>(&per_sm, &sms));
+    if (prec == FFG_F64) FFG_TRY((kernel_config<double, kWarpsBatch>(&per_sm, &sms)));
+    else FFG_TRY((kernel_config<float, kWarpsBatch>(&per_sm, &sms)));
     *nb_max = std::min(kMaxBlocks, sms * per_sm);
     return FFG_OK;
 }
@@ -1209,6 +1188,9 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     plan->items = w.items;
     plan->first = w.first;
     plan->ctl = w.ctl;
+    plan->tile_cnt = w.cnt;
+    plan->tile_pre = w.tpre;
+    plan->scan_tmp = w.scan;
     return FFG_OK;
 }
 
@@ -1235,12 +1217,15 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
                                                      plan->n_graphs, plan->total_tiles);
     count_launch();
     FFG_TRY(check_launch("k_pr_layout_batch"));
+    FFG_TRY(scan_exclusive(static_cast<const int32_t *>(plan->tile_cnt),
+                           static_cast<int64_t *>(plan->tile_pre), plan->total_tiles,
+                           static_cast<int64_t *>(plan->scan_tmp), stream));
     JobDev none{};
     const JobDev *jobs = static_cast<const JobDev *>(plan->jobs);
     const int2 *items = static_cast<const int2 *>(plan->items);
     const int *first = static_cast<const int *>(plan->first);
-    if (prec == FFG_F64) return launch_pr<double>(jobs, items, first, plan->n_blocks, none, stream);
-    return launch_pr<float>(jobs, items, first, plan->n_blocks, none, stream);
+    if (prec == FFG_F64) return launch_pr<double, kWarpsBatch>(jobs, items, first, plan->n_blocks, none, stream);
+    return launch_pr<float, kWarpsBatch>(jobs, items, first, plan->n_blocks, none, stream);
 }
 
 extern "C" ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *iters_out,
