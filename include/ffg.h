@@ -226,7 +226,8 @@ typedef struct {
     int32_t prec, n_jobs, n_graphs, n_blocks;
     int64_t total_tiles;
     void *jobs, *graphs, *items, *first, *ctl;
-    void *tile_cnt, *tile_pre, *scan_tmp;  /* per-tile cost tables of all graphs */
+    int64_t total_rows;
+    void *tables[8];  /* per-row and per-tile tables of all graphs (internal) */
 } ffg_pr_batch;
 
 size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec);

@@ -72,8 +72,7 @@ class ffg_pr_batch(C.Structure):
     _fields_ = [("prec", C.c_int32), ("n_jobs", C.c_int32), ("n_graphs", C.c_int32),
                 ("n_blocks", C.c_int32), ("total_tiles", C.c_int64), ("jobs", C.c_void_p),
                 ("graphs", C.c_void_p), ("items", C.c_void_p), ("first", C.c_void_p),
-                ("ctl", C.c_void_p), ("tile_cnt", C.c_void_p), ("tile_pre", C.c_void_p),
-                ("scan_tmp", C.c_void_p)]
+                ("ctl", C.c_void_p), ("total_rows", C.c_int64), ("tables", C.c_void_p * 8)]
 
 
 class ffg_pr_tuning(C.Structure):

@@ -66,12 +66,21 @@ constexpr uint64_t kTimeoutNs = 2000000000ULL;
 #ifndef FFG_PR_UNROLL
 #define FFG_PR_UNROLL 8
 #endif
+#ifndef FFG_PR_STEP32
+#define FFG_PR_STEP32 16
+#endif
 #ifndef FFG_PR_MINBLOCKS
 #define FFG_PR_MINBLOCKS 3
 #endif
 constexpr int kSegD = FFG_PR_SEG;       // descriptors per TMA segment
-constexpr int kU = FFG_PR_UNROLL;       // descriptors per step (gathers in flight per lane)
+constexpr int kU = FFG_PR_UNROLL;       // descriptor padding unit
 static_assert(kU % 2 == 0 && kSegD % kU == 0 && kU <= 32, "descriptor padding");
+// Descriptors per step of the gather loop (gathers in flight per lane): a
+// multiple of kU, the remainder of a segment is done in steps of kU.  FP64
+// stays at kU: its in-sums are bound by the FP64 pipe, where padding costs.
+template <typename T> struct Step { static constexpr int value = kU; };
+template <> struct Step<float> { static constexpr int value = FFG_PR_STEP32; };
+static_assert(FFG_PR_STEP32 % kU == 0 && kSegD % FFG_PR_STEP32 == 0, "gather step");
 constexpr int kLayoutThreads = 64;
 constexpr int64_t kRowCost = 20;        // per-row cost in in-edge units (batch plan)
 constexpr int64_t kTileCost = 19;       // per-tile cost in descriptor units (block split)
@@ -97,8 +106,13 @@ struct PrWs {
     void *w0, *w1;
     uint2 *desc;          // tile descriptors (off, mask)
     int32_t *cnt;         // per tile: descriptors, padded to a multiple of kU
+    uint2 *tinfo;         // per tile: (first descriptor / kU, cnt)
     int64_t *tpre;        // exclusive prefix sums of cnt (ntiles + 1)
-    int64_t *scan;        // scan scratch
+    int64_t *scan;        // scan scratch (tiles)
+    int32_t *perm;        // row of each tile slot
+    int32_t *aflag;       // per row: has in-edges
+    int64_t *apre;        // exclusive prefix sums of aflag (n + 1)
+    int64_t *ascan;       // scan scratch (rows)
     size_t bytes;
 };
 
@@ -108,6 +122,8 @@ __host__ __device__ __forceinline__ int64_t desc_begin(int64_t e0, int64_t t) {
     return (e0 + kU - 1) / kU * kU + 2 * kU * t;
 }
 inline int64_t desc_capacity(int64_t n, int64_t e) { return e + 2 * kU * ((n + 31) / 32 + 1); }
+// tile descriptors are addressed in units of kU by 32-bit indices
+inline bool desc_fits(int64_t n, int64_t e) { return desc_capacity(n, e) / kU < (int64_t(1) << 32); }
 
 PrWs carve(void *base, int64_t n, int64_t e, size_t elem) {
     Carver c(base);
@@ -117,8 +133,13 @@ PrWs carve(void *base, int64_t n, int64_t e, size_t elem) {
     w.w1 = c.take<char>(size_t(n) * elem);
     w.desc = c.take<uint2>(size_t(desc_capacity(n, e)));
     w.cnt = c.take<int32_t>(size_t((n + 31) / 32));
+    w.tinfo = c.take<uint2>(size_t((n + 31) / 32));
     w.tpre = c.take<int64_t>(size_t((n + 31) / 32) + 1);
     w.scan = c.take<int64_t>(size_t(scan_scratch_elems((n + 31) / 32)));
+    w.perm = c.take<int32_t>(size_t(n));
+    w.aflag = c.take<int32_t>(size_t(n));
+    w.apre = c.take<int64_t>(size_t(n) + 1);
+    w.ascan = c.take<int64_t>(size_t(scan_scratch_elems(n)));
     w.bytes = c.off;
     return w;
 }
@@ -301,24 +322,59 @@ __device__ __forceinline__ void publish(PrCtl *ctl, int buf, const Fix3 &b, int 
 // ---------------------------------------------------------------------------
 // descriptor layout of the in-edges (built once per graph)
 // ---------------------------------------------------------------------------
-// One tile (one warp): merge the 32 ascending in-lists by offset src - dst;
-// each distinct offset becomes one descriptor whose mask holds the lanes
-// that have it.  Offsets fit int32 (n < 2^31); INT32_MAX marks an exhausted
-// list.
+// Tiles are made of slots: the rows with in-edges first, ascending, then
+// the rows without (their sum is empty: x' = the teleport term), so that no
+// lane of a tile with descriptors idles on an empty row.  perm[slot] = row.
+// apre holds the exclusive prefix sums of (in-degree > 0) over the rows,
+// from any base apre[0]; the number of rows with in-edges is apre[n] -
+// apre[0].
+__device__ __forceinline__ void active_flag(const int64_t *__restrict__ in_ptr, int64_t v,
+                                            int32_t *__restrict__ flag) {
+    flag[v] = in_ptr[v + 1] > in_ptr[v] ? 1 : 0;
+}
+__device__ __forceinline__ void place_row(const int64_t *__restrict__ apre, int64_t n, int64_t v,
+                                          int32_t *__restrict__ perm) {
+    const int64_t base = apre[0];
+    const int64_t p = apre[v] - base;
+    const bool act = apre[v + 1] > apre[v];
+    perm[act ? p : apre[n] - base + v - p] = static_cast<int32_t>(v);
+}
+
+__global__ void k_active_flags(const int64_t *__restrict__ in_ptr, int64_t n,
+                               int32_t *__restrict__ flag) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
+         v += int64_t(gridDim.x) * blockDim.x)
+        active_flag(in_ptr, v, flag);
+}
+__global__ void k_perm(const int64_t *__restrict__ apre, int64_t n, int32_t *__restrict__ perm) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
+         v += int64_t(gridDim.x) * blockDim.x)
+        place_row(apre, n, v, perm);
+}
+
+// One tile (one warp): merge the 32 ascending in-lists of its slots' rows by
+// offset src - row; each distinct offset becomes one descriptor whose mask
+// holds the lanes that have it.  Offsets fit int32 (n < 2^31); INT32_MAX
+// marks an exhausted list.  The in-edges of the slots before this tile
+// number in_ptr[perm[32t]] when that row has in-edges (all earlier slots
+// hold smaller rows with in-edges), else all e of them.
 __device__ void layout_tile(const int64_t *__restrict__ in_ptr,
-                            const int32_t *__restrict__ in_idx, int64_t n,
-                            uint2 *__restrict__ desc, int32_t *__restrict__ cnt, int64_t t,
-                            int lane) {
-    const int64_t r0 = t << 5;
-    const int64_t v = r0 + lane;
+                            const int32_t *__restrict__ in_idx,
+                            const int32_t *__restrict__ perm, int64_t n, int64_t e,
+                            uint2 *__restrict__ desc, int32_t *__restrict__ cnt,
+                            uint2 *__restrict__ tinfo, int64_t t, int lane) {
+    const int64_t slot = (t << 5) + lane;
+    int32_t vi = 0;
     int64_t cur = 0, end = 0;
-    if (v < n) {
-        cur = in_ptr[v];
-        end = in_ptr[v + 1];
+    if (slot < n) {
+        vi = perm[slot];
+        cur = in_ptr[vi];
+        end = in_ptr[vi + 1];
     }
-    const int64_t e0 = __shfl_sync(0xffffffffu, cur, 0);  // in_ptr[r0]: row r0 exists
-    uint2 *out = desc + desc_begin(e0, t);
-    const int32_t vi = static_cast<int32_t>(v);
+    const int64_t c0 = __shfl_sync(0xffffffffu, cur, 0);  // slot 32t exists
+    const int64_t z0 = __shfl_sync(0xffffffffu, end, 0);
+    const int64_t dbeg = desc_begin(z0 > c0 ? c0 : e, t);
+    uint2 *out = desc + dbeg;
     int32_t head = cur < end ? __ldg(in_idx + cur) - vi : INT32_MAX;
     int k = 0;
     while (true) {
@@ -335,17 +391,21 @@ __device__ void layout_tile(const int64_t *__restrict__ in_ptr,
     }
     const int padded = (k + kU - 1) / kU * kU;
     if (k + lane < padded) out[k + lane] = make_uint2(0u, 0u);
-    if (lane == 0) cnt[t] = padded;
+    if (lane == 0) {
+        cnt[t] = padded;
+        tinfo[t] = make_uint2(static_cast<uint32_t>(dbeg / kU), static_cast<uint32_t>(padded));
+    }
 }
 
 __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout(
-    const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx, int64_t n,
-    uint2 *__restrict__ desc, int32_t *__restrict__ cnt) {
+    const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx,
+    const int32_t *__restrict__ perm, int64_t n, int64_t e, uint2 *__restrict__ desc,
+    int32_t *__restrict__ cnt, uint2 *__restrict__ tinfo) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t ntiles = (n + 31) >> 5;
     const int64_t step = int64_t(gridDim.x) * (kLayoutThreads / 32);
     for (int64_t t = int64_t(blockIdx.x) * (kLayoutThreads / 32) + warp; t < ntiles; t += step)
-        layout_tile(in_ptr, in_idx, n, desc, cnt, t, lane);
+        layout_tile(in_ptr, in_idx, perm, n, e, desc, cnt, tinfo, t, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -353,24 +413,34 @@ __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout(
 // ---------------------------------------------------------------------------
 template <typename T>
 struct TileInfo {
-    int64_t dbeg;  // first descriptor
+    uint32_t d8;   // first descriptor / kU
     int cnt;       // descriptors (multiple of kU)
-    int32_t od;    // out-degree of this lane's row
-    T wv;          // w of this lane's row
+    int32_t v;     // this lane's row (-1 past the last slot)
+    int32_t od;    // its out-degree
+    T wv;          // its w
 };
 
+// A tile's info loads in two steps, a tile apart, so that no load waits on
+// the one before it: its head (descriptor range and this lane's row), then
+// the row's data (out-degree and w), which need the row.
 template <typename T>
-__device__ __forceinline__ TileInfo<T> load_info(int t, int n, const int64_t *__restrict__ in_ptr,
-                                                 const int32_t *__restrict__ cnt,
-                                                 const int32_t *__restrict__ outdeg, const T *wc,
-                                                 int lane) {
+__device__ __forceinline__ TileInfo<T> load_head(int t, int n, const uint2 *__restrict__ tinfo,
+                                                 const int32_t *__restrict__ perm, int lane) {
     TileInfo<T> ti;
-    const int v = (t << 5) + lane;  // n < 2^31
-    ti.dbeg = desc_begin(__ldg(in_ptr + (t << 5)), t);
-    ti.cnt = __ldg(cnt + t);
-    ti.od = v < n ? __ldg(outdeg + v) : 0;
-    ti.wv = v < n ? wc[v] : T(0);
+    const int slot = (t << 5) + lane;  // n < 2^31
+    const uint2 h = __ldg(tinfo + t);
+    ti.d8 = h.x;
+    ti.cnt = static_cast<int>(h.y);
+    ti.v = slot < n ? __ldg(perm + slot) : -1;
+    ti.od = 0;
+    ti.wv = T(0);
     return ti;
+}
+template <typename T>
+__device__ __forceinline__ void load_row(TileInfo<T> &ti, const int32_t *__restrict__ outdeg,
+                                         const T *wc) {
+    ti.od = ti.v >= 0 ? __ldg(outdeg + ti.v) : 0;
+    ti.wv = ti.v >= 0 ? wc[ti.v] : T(0);
 }
 
 // Per-warp TMA stream of descriptor segments into a two-buffer stage.
@@ -405,10 +475,28 @@ struct Stream {
     }
 };
 
+// N descriptors (q: N/2 pairs, the same for every lane): the sum of this
+// lane's gathers, added pairwise.
+template <typename T, int N>
+__device__ __forceinline__ T gather_step(const uint4 *q, const T *wrow, uint32_t bit) {
+    T v[N];
+#pragma unroll
+    for (int j = 0; j < N / 2; ++j) {
+        const uint4 d = q[j];  // two descriptors, read by broadcast
+        v[2 * j] = (d.y & bit) ? wrow[static_cast<int32_t>(d.x)] : T(0);
+        v[2 * j + 1] = (d.w & bit) ? wrow[static_cast<int32_t>(d.z)] : T(0);
+    }
+#pragma unroll
+    for (int h = N / 2; h > 0; h >>= 1)  // depth log2(N)
+#pragma unroll
+        for (int j = 0; j < h; ++j) v[j] += v[j + h];
+    return v[0];
+}
+
 // Sum over the in-edges of this lane's row (wrow = w + row): the tile's
 // descriptors stream in segments of kSegD; the segment after the current one
 // (or the first segment of the next tile) is copied while the current one is
-// gathered.  kU descriptors per step: kU independent gathers per lane.
+// gathered.
 template <typename T>
 __device__ __forceinline__ bool tile_sum(const uint2 *__restrict__ desc, const TileInfo<T> &cur,
                                          const TileInfo<T> &nxt, bool has_next, Stream &st,
@@ -420,37 +508,30 @@ __device__ __forceinline__ bool tile_sum(const uint2 *__restrict__ desc, const T
     for (int sg = 0; sg < nseg; ++sg) {
         const int c0 = sg * kSegD;
         const int m = cnt - c0 < kSegD ? cnt - c0 : kSegD;
-        if (!st.issued) st.issue(desc + cur.dbeg + c0, m, st.buf, lane);
+        if (!st.issued) st.issue(desc + size_t(cur.d8) * kU + c0, m, st.buf, lane);
         if (sg + 1 < nseg) {
             const int c1 = c0 + kSegD;
-            st.issue(desc + cur.dbeg + c1, cnt - c1 < kSegD ? cnt - c1 : kSegD, st.buf ^ 1, lane);
+            st.issue(desc + size_t(cur.d8) * kU + c1, cnt - c1 < kSegD ? cnt - c1 : kSegD,
+                     st.buf ^ 1, lane);
             st.issued = true;
         } else if (next_any) {
-            st.issue(desc + nxt.dbeg, nxt.cnt < kSegD ? nxt.cnt : kSegD, st.buf ^ 1, lane);
+            st.issue(desc + size_t(nxt.d8) * kU, nxt.cnt < kSegD ? nxt.cnt : kSegD, st.buf ^ 1,
+                     lane);
             st.issued = true;
         } else {
             st.issued = false;
         }
         if (!st.wait(st.buf)) return false;
         const uint4 *q = reinterpret_cast<const uint4 *>(st.stage + st.buf * kSegD);
-        for (int k = 0; k < m; k += kU) {
-            T v[kU];
-#pragma unroll
-            for (int j = 0; j < kU / 2; ++j) {
-                const uint4 d = q[(k >> 1) + j];  // two descriptors, same for every lane
-                v[2 * j] = (d.y & bit) ? wrow[static_cast<int32_t>(d.x)] : T(0);
-                v[2 * j + 1] = (d.w & bit) ? wrow[static_cast<int32_t>(d.z)] : T(0);
-            }
-#pragma unroll
-            for (int h = kU / 2; h > 0; h >>= 1)  // pairwise: depth log2(kU)
-#pragma unroll
-                for (int j = 0; j < h; ++j) v[j] += v[j + h];
-            s += v[0];
-        }
+        constexpr int kS = Step<T>::value;
+        int k = 0;
+        for (; k + kS <= m; k += kS) s += gather_step<T, kS>(q + (k >> 1), wrow, bit);
+        if (kS > kU)
+            for (; k < m; k += kU) s += gather_step<T, kU>(q + (k >> 1), wrow, bit);
         st.buf ^= 1;
     }
     if (nseg == 0 && !st.issued && next_any) {
-        st.issue(desc + nxt.dbeg, nxt.cnt < kSegD ? nxt.cnt : kSegD, st.buf, lane);
+        st.issue(desc + size_t(nxt.d8) * kU, nxt.cnt < kSegD ? nxt.cnt : kSegD, st.buf, lane);
         st.issued = true;
     }
     sum = s;
@@ -486,11 +567,12 @@ constexpr size_t pr_smem_bytes() {
 // `group` blocks work on it together (ranks 0..group-1), synchronised by the
 // job's own bounded barrier in `ctl`.
 struct JobDev {
-    const int64_t *in_ptr;
     const int32_t *outdeg;
     const uint2 *desc;
-    const int32_t *cnt;
+    const uint2 *tinfo;
+    const int32_t *perm;
     const int64_t *tpre;
+    const int64_t *apre;  // rows with in-edges: apre[n] - apre[0]
     void *ranks, *w0, *w1;
     PrCtl *ctl;
     int64_t n;
@@ -498,8 +580,6 @@ struct JobDev {
     int max_iter, init, group, pad;
 };
 
-// A group of blocks runs all iterations of one job.  Returns false if the
-// block must stop (a bounded wait expired).
 // Loop state of a job, kept by thread 0 in shared memory: the tile loop
 // holds none of it in registers.
 struct LoopState {
@@ -507,15 +587,13 @@ struct LoopState {
     int it, stop, converged, pad;
 };
 
-// thread 0, after the barrier of a phase: read the job's sums, decide
+// thread 0, after the barrier of an iteration: read the job's sums, decide
 // whether to stop, and publish the next teleport term
 template <typename T>
 __device__ __forceinline__ void advance(const JobDev &J, LoopState &ls, const PrCtl *ctl, int buf,
                                         T *s_c, bool count_iter) {
     const double r = static_cast<double>(__ldcg(&ctl->acc[buf][0])) / kFix;
     const double d = static_cast<double>(__ldcg(&ctl->acc[buf][1])) / kFix;
-    const double x = static_cast<double>(__ldcg(&ctl->acc[buf][2])) / kFix;
-    ls.xs = x;
     *s_c = static_cast<T>((J.alpha * d + 1.0 - J.alpha) / static_cast<double>(J.n));
     if (!count_iter) return;  // the prologue: no iteration yet
     ls.prev_res = ls.res;
@@ -526,41 +604,56 @@ __device__ __forceinline__ void advance(const JobDev &J, LoopState &ls, const Pr
     else if (ls.it >= J.max_iter) ls.stop = 1;
 }
 
+// w' of a row from x': x'/outdeg (x' itself without out-edges).  FP32 takes
+// the correctly rounded reciprocal times x' (two roundings instead of one,
+// no division sequence); FP64 divides.
+__device__ __forceinline__ float w_of(float xn, int od) {
+    return od ? xn * __frcp_rn(static_cast<float>(od)) : xn;
+}
+__device__ __forceinline__ double w_of(double xn, int od) {
+    return od ? xn / static_cast<double>(od) : xn;
+}
+
 // A group of blocks runs all iterations of one job.  Returns false if the
 // block must stop (a bounded wait expired).
 template <typename T, int W>
 __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     constexpr int kThreads = 32 * W;
-    const int64_t *__restrict__ in_ptr = J.in_ptr;
     const int32_t *__restrict__ outdeg = J.outdeg;
     const uint2 *__restrict__ desc = J.desc;
-    const int32_t *__restrict__ tcnt = J.cnt;
+    const uint2 *__restrict__ tinfo = J.tinfo;
+    const int32_t *__restrict__ perm = J.perm;
     const int64_t n = J.n;
     const int nb = J.group;
     T *w0 = static_cast<T *>(J.w0), *w1 = static_cast<T *>(J.w1);
     PrCtl *ctl = J.ctl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    const int64_t ntiles = (n + 31) >> 5;
-    // the block's contiguous tile range (about equal cost per block); its
-    // warps take tiles from it in turn through a shared counter
-    __shared__ int s_range[2];
+    // Tiles hold the slots of the rows with in-edges (the last one may also
+    // hold rows without); the remaining slots, rows whose sum is empty, are
+    // done element-wise by every block.  The block's contiguous tile range has
+    // about equal cost per block.  Warp w starts with tiles bt0 + w and
+    // bt0 + W + w; the rest are taken in turn through a shared counter.
+    __shared__ int s_range[3];
     __shared__ unsigned s_next;
     __shared__ LoopState s_ls;
     __shared__ T s_c;
     __syncthreads();
     if (threadIdx.x == 0) {
+        const int64_t ntiles = (J.apre[n] - J.apre[0] + 31) >> 5;
+        s_range[2] = static_cast<int>(ntiles);
         s_range[0] = static_cast<int>(tile_split(J.tpre, ntiles, rank, nb));
         s_range[1] = static_cast<int>(tile_split(J.tpre, ntiles, rank + 1, nb));
-        s_next = static_cast<unsigned>(s_range[0] + W);
+        s_next = static_cast<unsigned>(s_range[0] + 2 * W);
         s_ls.res = __longlong_as_double(0x7ff0000000000000LL);
         s_ls.it = s_ls.stop = s_ls.converged = 0;
     }
     __syncthreads();
     const int bt0 = s_range[0], bt1 = s_range[1];
+    const int64_t slot_empty = int64_t(s_range[2]) << 5;  // first slot done element-wise
     const int ni = static_cast<int>(n);
 
-    // prologue: w from the start vector, D_0 and sum x_0 (grid-stride)
+    // prologue: w from the start vector and D_0 (grid-stride)
     {
         const double inv_n = 1.0 / static_cast<double>(n);
         const T *ranks = static_cast<const T *>(J.ranks);
@@ -570,9 +663,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
             const double x0 = J.init ? static_cast<double>(ranks[v]) : inv_n;
             const int32_t od = __ldg(outdeg + v);
             w0[v] = static_cast<T>(od ? x0 / od : x0);
-            const long long q = to_fix(x0);
-            if (od == 0) acc0.d += q;
-            acc0.s += q;
+            if (od == 0) acc0.d += to_fix(x0);
         }
         const Fix3 b = block_sum_fix<W>(acc0);
         if (threadIdx.x == 0) publish(ctl, 0, b, rank);
@@ -585,41 +676,66 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     T *wc = w0, *wn = w1;
     const T a = static_cast<T>(J.alpha);
     int failed = 0;
-    const int t0 = bt0 + warp;  // this warp's first tile in every iteration
-    TileInfo<T> pre;                // ... loaded ahead (have_pre)
+    const int t0 = bt0 + warp, t1 = bt0 + W + warp;  // this warp's first two tiles
+    TileInfo<T> pre0, pre1;  // ... loaded ahead (have_pre)
     bool have_pre = false;
     while (true) {
         const T c = s_c;
         Fix3 facc;
-        int t = t0;
-        if (t < bt1 && !failed) {
-            TileInfo<T> cur = have_pre ? pre : load_info<T>(t, ni, in_ptr, tcnt, outdeg, wc, lane);
+        if (t0 < bt1 && !failed) {
+            // cur: tile being summed; nxt: its successor (info loaded one tile
+            // ahead, so its first segment can be issued at once); the tile
+            // after nxt is taken and its info loaded while cur is summed
+            int t = t0, tn = t1;
+            TileInfo<T> cur, nxt;
+            if (have_pre) {
+                cur = pre0;
+                nxt = pre1;
+            } else {
+                cur = load_head<T>(t0, ni, tinfo, perm, lane);
+                nxt = load_head<T>(t1 < bt1 ? t1 : t0, ni, tinfo, perm, lane);
+                load_row<T>(cur, outdeg, wc);
+            }
             while (true) {
-                unsigned g = 0;
-                if (lane == 0) g = atomicAdd(&s_next, 1u);
-                const int tn = static_cast<int>(__shfl_sync(0xffffffffu, g, 0));
                 const bool has_next = tn < bt1;
-                TileInfo<T> nxt = cur;
-                if (has_next) nxt = load_info<T>(tn, ni, in_ptr, tcnt, outdeg, wc, lane);
-                const int v = (t << 5) + lane;
+                int tn2 = bt1;
+                if (has_next) {
+                    unsigned g = 0;
+                    if (lane == 0) g = atomicAdd(&s_next, 1u);
+                    tn2 = static_cast<int>(__shfl_sync(0xffffffffu, g, 0));
+                }
+                load_row<T>(nxt, outdeg, wc);
+                const TileInfo<T> nx2 = load_head<T>(tn2 < bt1 ? tn2 : t, ni, tinfo, perm, lane);
+                const int v = cur.v;
                 T s = T(0);
-                if (!tile_sum<T>(desc, cur, nxt, has_next, st, wc + v, 1u << lane, lane, s)) {
+                if (!tile_sum<T>(desc, cur, nxt, has_next, st, wc + (v < 0 ? 0 : v), 1u << lane,
+                                 lane, s)) {
                     failed = 1;
                     break;
                 }
-                if (v < ni) {
+                if (v >= 0) {
                     const T xo = cur.od ? cur.wv * static_cast<T>(cur.od) : cur.wv;
                     const T xn = a * s + c;
                     facc.r += to_fix(xn > xo ? xn - xo : xo - xn);
-                    const long long q = to_fix(xn);
-                    if (cur.od == 0) facc.d += q;
-                    facc.s += q;
-                    wn[v] = cur.od ? xn / static_cast<T>(cur.od) : xn;
+                    if (cur.od == 0) facc.d += to_fix(xn);
+                    wn[v] = w_of(xn, cur.od);
                 }
                 if (!has_next) break;
                 cur = nxt;
                 t = tn;
+                nxt = nx2;
+                tn = tn2;
             }
+        }
+        // rows without in-edges: x' = c
+        for (int64_t i = slot_empty + int64_t(rank) * kThreads + threadIdx.x; i < n;
+             i += int64_t(nb) * kThreads) {
+            const int v = __ldg(perm + i);
+            const int32_t od = __ldg(outdeg + v);
+            const T xo = od ? wc[v] * static_cast<T>(od) : wc[v];
+            facc.r += to_fix(c > xo ? c - xo : xo - c);
+            if (od == 0) facc.d += to_fix(c);
+            wn[v] = w_of(c, od);
         }
         if (failed == 1) {
             // let this warp's own copies land (bounded), then report
@@ -629,14 +745,18 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
         }
         const Fix3 b = block_sum_fix<W>(facc);
         // The block's rows of w' are written (block barrier above), so the
-        // next iteration's first tile -- in this block's range -- loads its
-        // row data and its first descriptor segment while the grid barrier
-        // completes.  Unused if the solve stops here (drained below).
+        // next iteration's first two tiles -- in this block's range -- load
+        // their row data, and the first one its first descriptor segment,
+        // while the grid barrier completes.  Unused if the solve stops here
+        // (drained below).
         have_pre = false;
         if (t0 < bt1 && !failed) {
-            pre = load_info<T>(t0, ni, in_ptr, tcnt, outdeg, wn, lane);
-            if (pre.cnt > 0 && !st.issued) {
-                st.issue(desc + pre.dbeg, pre.cnt < kSegD ? pre.cnt : kSegD, st.buf, lane);
+            pre0 = load_head<T>(t0, ni, tinfo, perm, lane);
+            pre1 = load_head<T>(t1 < bt1 ? t1 : t0, ni, tinfo, perm, lane);
+            load_row<T>(pre0, outdeg, wn);
+            if (pre0.cnt > 0 && !st.issued) {
+                st.issue(desc + size_t(pre0.d8) * kU, pre0.cnt < kSegD ? pre0.cnt : kSegD, st.buf,
+                         lane);
                 st.issued = true;
             }
             have_pre = true;
@@ -644,7 +764,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
         buf = buf == 2 ? 0 : buf + 1;
         if (threadIdx.x == 0) {
             publish(ctl, buf, b, rank);
-            s_next = static_cast<unsigned>(bt0 + W);  // next iteration's counter
+            s_next = static_cast<unsigned>(bt0 + 2 * W);  // next iteration's counter
         }
         ++phase;
         if (!group_barrier(ctl, phase * nb, nb)) {
@@ -663,10 +783,24 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
         st.drain();
         st.issued = false;
     }
-    // epilogue: x' normalised to sum 1
+    // epilogue: sum x' (one more phase), then x' normalised to sum 1
+    const int64_t stride = int64_t(nb) * kThreads;
+    {
+        Fix3 accs;
+        for (int64_t v = int64_t(rank) * kThreads + threadIdx.x; v < n; v += stride) {
+            const int32_t od = __ldg(outdeg + v);
+            accs.s += to_fix(od ? static_cast<double>(wc[v]) * od : static_cast<double>(wc[v]));
+        }
+        const Fix3 b = block_sum_fix<W>(accs);
+        buf = buf == 2 ? 0 : buf + 1;
+        if (threadIdx.x == 0) publish(ctl, buf, b, rank);
+        ++phase;
+        if (!group_barrier(ctl, phase * nb, nb)) return false;
+        if (threadIdx.x == 0) s_ls.xs = static_cast<double>(__ldcg(&ctl->acc[buf][2])) / kFix;
+        __syncthreads();
+    }
     const double inv_s = 1.0 / s_ls.xs;
     T *ranks = static_cast<T *>(J.ranks);
-    const int64_t stride = int64_t(nb) * kThreads;
     for (int64_t v = int64_t(rank) * kThreads + threadIdx.x; v < n; v += stride) {
         const int32_t od = __ldg(outdeg + v);
         const double x = od ? static_cast<double>(wc[v]) * od : static_cast<double>(wc[v]);
@@ -686,7 +820,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
 // order -- (job, rank) pairs, each block's multi-block job first, so that
 // no two groups ever wait on each other.
 template <typename T, int W>
-__global__ void __launch_bounds__(32 * W, W >= 24 ? 1 : FFG_PR_MINBLOCKS)
+__global__ void __launch_bounds__(32 * W, W > kWarpsBatch ? 1 : FFG_PR_MINBLOCKS)
     k_pagerank(const JobDev *__restrict__ jobs, const int2 *__restrict__ items,
                const int *__restrict__ first, int plan_blocks, JobDev single) {
     extern __shared__ __align__(128) unsigned char s_dyn[];
@@ -718,17 +852,48 @@ __global__ void __launch_bounds__(32 * W, W >= 24 ? 1 : FFG_PR_MINBLOCKS)
     }
 }
 
-// Layout kernel over every distinct graph of a batch: global tile index ->
-// graph by binary search over the graphs' first tiles.
+// Layout kernels over every distinct graph of a batch: a global row or tile
+// index -> graph by binary search over the graphs' first rows or tiles.
 struct GraphDev {
     const int64_t *in_ptr;
     const int32_t *in_idx;
     uint2 *desc;
     int32_t *cnt;
-    int64_t n;
-    int64_t tile0;  // first global tile of this graph
+    uint2 *tinfo;
+    int32_t *perm;
+    int32_t *aflag;  // this graph's part of the batch's row flags
+    int64_t *apre;   // ... and of their prefix sums
+    int64_t n, e;
+    int64_t tile0;   // first global tile of this graph
+    int64_t row0;    // first global row of this graph
 };
 
+__device__ __forceinline__ int graph_of(const GraphDev *__restrict__ gr, int n_graphs, int64_t x,
+                                        bool by_tile) {
+    int lo = 0, hi = n_graphs - 1;  // last graph starting at or before x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((by_tile ? gr[mid].tile0 : gr[mid].row0) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_active_flags_batch(const GraphDev *__restrict__ gr, int n_graphs,
+                                     int64_t total_rows) {
+    for (int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < total_rows;
+         x += int64_t(gridDim.x) * blockDim.x) {
+        const GraphDev &g = gr[graph_of(gr, n_graphs, x, false)];
+        active_flag(g.in_ptr, x - g.row0, g.aflag);
+    }
+}
+__global__ void k_perm_batch(const GraphDev *__restrict__ gr, int n_graphs, int64_t total_rows) {
+    for (int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < total_rows;
+         x += int64_t(gridDim.x) * blockDim.x) {
+        const GraphDev &g = gr[graph_of(gr, n_graphs, x, false)];
+        place_row(g.apre, g.n, x - g.row0, g.perm);
+    }
+}
 __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout_batch(const GraphDev *__restrict__ gr,
                                                                      int n_graphs,
                                                                      int64_t total_tiles) {
@@ -736,30 +901,41 @@ __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout_batch(const GraphD
     const int64_t step = int64_t(gridDim.x) * (kLayoutThreads / 32);
     for (int64_t gt = int64_t(blockIdx.x) * (kLayoutThreads / 32) + warp; gt < total_tiles;
          gt += step) {
-        int lo = 0, hi = n_graphs - 1;  // last graph with tile0 <= gt
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (gr[mid].tile0 <= gt) lo = mid;
-            else hi = mid - 1;
-        }
-        const GraphDev g = gr[lo];
-        layout_tile(g.in_ptr, g.in_idx, g.n, g.desc, g.cnt, gt - g.tile0, lane);
+        const GraphDev g = gr[graph_of(gr, n_graphs, gt, true)];
+        layout_tile(g.in_ptr, g.in_idx, g.perm, g.n, g.e, g.desc, g.cnt, g.tinfo, gt - g.tile0,
+                    lane);
     }
 }
 
-ffg_status launch_layout(const ffg_graph *g, PrWs &w, cudaStream_t stream) {
-    int dev = 0, sms = 0;
+unsigned grid_for(int64_t items, int per_block, int sms) {
+    const int64_t want = (items + per_block - 1) / per_block;
+    const int64_t cap = int64_t(sms) * 32;
+    return static_cast<unsigned>(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+ffg_status device_sms(int *sms) {
+    int dev = 0;
     FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
-    FFG_TRY(check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
+    return check_cuda(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+}
+
+// slots (rows with in-edges first), descriptors, tile cost prefix
+ffg_status launch_layout(const ffg_graph *g, PrWs &w, cudaStream_t stream) {
+    int sms = 0;
+    FFG_TRY(device_sms(&sms));
     const int64_t n = g->n_nodes;
     const int64_t tiles = (n + 31) / 32;
-    const int64_t want = (tiles + kLayoutThreads / 32 - 1) / (kLayoutThreads / 32);
-    const int64_t cap = int64_t(sms) * 32;
-    const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
-    k_pr_layout<<<grid, kLayoutThreads, 0, stream>>>(g->in_ptr, g->in_idx, n, w.desc, w.cnt);
+    k_active_flags<<<grid_for(n, 256, sms), 256, 0, stream>>>(g->in_ptr, n, w.aflag);
+    count_launch();
+    FFG_TRY(check_launch("k_active_flags"));
+    FFG_TRY(scan_exclusive(w.aflag, w.apre, n, w.ascan, stream));
+    k_perm<<<grid_for(n, 256, sms), 256, 0, stream>>>(w.apre, n, w.perm);
+    count_launch();
+    FFG_TRY(check_launch("k_perm"));
+    k_pr_layout<<<grid_for(tiles, kLayoutThreads / 32, sms), kLayoutThreads, 0, stream>>>(
+        g->in_ptr, g->in_idx, w.perm, n, g->n_edges, w.desc, w.cnt, w.tinfo);
     count_launch();
     FFG_TRY(check_launch("k_pr_layout"));
-    // tile cost prefix for the block split
     return scan_exclusive(w.cnt, w.tpre, tiles, w.scan, stream);
 }
 
@@ -806,11 +982,12 @@ ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, in
     const int64_t want = (tiles + 4 * W - 1) / (4 * W);  // >= ~4 tiles per warp
     const int nb = static_cast<int>(want < 1 ? 1 : (want > max_res ? max_res : want));
     JobDev J;
-    J.in_ptr = g->in_ptr;
     J.outdeg = g->outdeg;
     J.desc = w.desc;
-    J.cnt = w.cnt;
+    J.tinfo = w.tinfo;
+    J.perm = w.perm;
     J.tpre = w.tpre;
+    J.apre = w.apre;
     J.ranks = ranks;
     J.w0 = w.w0;
     J.w1 = w.w1;
@@ -859,7 +1036,8 @@ extern "C" ffg_status pagerank_solve(const ffg_graph *g, double damping, double 
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (!g || g->n_nodes <= 0 || !g->in_ptr || !g->outdeg || (g->n_edges > 0 && !g->in_idx))
         return set_error("graph is empty or incomplete"), FFG_ERR_INVALID_ARG;
-    if (g->n_nodes >= (int64_t(1) << 31)) return set_error("too many nodes"), FFG_ERR_OVERFLOW;
+    if (g->n_nodes >= (int64_t(1) << 31) || !desc_fits(g->n_nodes, g->n_edges))
+        return set_error("too many nodes or edges"), FFG_ERR_OVERFLOW;
     if (!(damping > 0.0 && damping < 1.0))
         return set_error("damping must lie in (0,1)"), FFG_ERR_INVALID_ARG;
     if (!(tol >= 0.0) || max_iter < 1)
@@ -892,7 +1070,8 @@ extern "C" ffg_status pagerank_prepare(const ffg_graph *g, ffg_prec prec, void *
     clear_error();
     if (!g || g->n_nodes <= 0 || !g->in_ptr || (g->n_edges > 0 && !g->in_idx))
         return set_error("graph is empty or incomplete"), FFG_ERR_INVALID_ARG;
-    if (g->n_nodes >= (int64_t(1) << 31)) return set_error("too many nodes"), FFG_ERR_OVERFLOW;
+    if (g->n_nodes >= (int64_t(1) << 31) || !desc_fits(g->n_nodes, g->n_edges))
+        return set_error("too many nodes or edges"), FFG_ERR_OVERFLOW;
     if (prec != FFG_F64 && prec != FFG_F32)
         return set_error("unknown precision %d", (int)prec), FFG_ERR_INVALID_ARG;
     if (!workspace || !aligned256(workspace))
@@ -946,8 +1125,8 @@ ffg_status check_job(const ffg_pr_job &j, int idx) {
         !j.ranks)
         return set_error("job %d: graph empty or incomplete, or ranks NULL", idx),
                FFG_ERR_INVALID_ARG;
-    if (g->n_nodes >= (int64_t(1) << 31))
-        return set_error("job %d: too many nodes", idx), FFG_ERR_OVERFLOW;
+    if (g->n_nodes >= (int64_t(1) << 31) || !desc_fits(g->n_nodes, g->n_edges))
+        return set_error("job %d: too many nodes or edges", idx), FFG_ERR_OVERFLOW;
     if (!(j.damping > 0.0 && j.damping < 1.0) || !(j.tol >= 0.0) || j.max_iter < 1 ||
         (j.init & ~FFG_INIT_RANKS))
         return set_error("job %d: bad damping, tol, max_iter or init", idx), FFG_ERR_INVALID_ARG;
@@ -1039,8 +1218,13 @@ struct BatchWs {
     int2 *items;
     PrCtl *ctl;
     int32_t *cnt;    // per tile of every graph
+    uint2 *tinfo;    // per tile of every graph
     int64_t *tpre;   // its prefix sums
-    int64_t *scan;   // scan scratch
+    int64_t *scan;   // scan scratch (tiles)
+    int32_t *aflag;  // per row of every graph: has in-edges
+    int64_t *apre;   // its prefix sums
+    int64_t *ascan;  // scan scratch (rows)
+    int64_t total_rows;
     size_t bytes;
 };
 
@@ -1063,29 +1247,44 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
     for (const ffg_graph *g : P.graphs) total_tiles += (g->n_nodes + 31) / 32;
     // per-tile descriptor counts of all graphs in one array, scanned at once
     w.cnt = c.take<int32_t>(size_t(total_tiles));
+    w.tinfo = c.take<uint2>(size_t(total_tiles));
     w.tpre = c.take<int64_t>(size_t(total_tiles) + 1);
     w.scan = c.take<int64_t>(size_t(scan_scratch_elems(total_tiles)));
+    int64_t total_rows = 0;
+    for (const ffg_graph *g : P.graphs) total_rows += g->n_nodes;
+    w.total_rows = total_rows;
+    w.aflag = c.take<int32_t>(size_t(total_rows));
+    w.apre = c.take<int64_t>(size_t(total_rows) + 1);
+    w.ascan = c.take<int64_t>(size_t(scan_scratch_elems(total_rows)));
     std::vector<GraphDev> gd(P.graphs.size());
-    int64_t tile0 = 0;
+    int64_t tile0 = 0, row0 = 0;
     for (size_t k = 0; k < P.graphs.size(); ++k) {
         const ffg_graph *g = P.graphs[k];
         gd[k].in_ptr = g->in_ptr;
         gd[k].in_idx = g->in_idx;
         gd[k].desc = c.take<uint2>(size_t(desc_capacity(g->n_nodes, g->n_edges)));
         gd[k].cnt = w.cnt + tile0;
+        gd[k].tinfo = w.tinfo + tile0;
+        gd[k].perm = c.take<int32_t>(size_t(g->n_nodes));
+        gd[k].aflag = w.aflag + row0;
+        gd[k].apre = w.apre + row0;
         gd[k].n = g->n_nodes;
+        gd[k].e = g->n_edges;
         gd[k].tile0 = tile0;
+        gd[k].row0 = row0;
         tile0 += (g->n_nodes + 31) / 32;
+        row0 += g->n_nodes;
     }
     std::vector<JobDev> jd(n_jobs);
     for (int j = 0; j < n_jobs; ++j) {
         const ffg_graph *g = jobs[j].g;
         const GraphDev &G = gd[P.graph_of_job[j]];
         JobDev &J = jd[j];
-        J.in_ptr = g->in_ptr;
         J.outdeg = g->outdeg;
         J.desc = G.desc;
-        J.cnt = G.cnt;
+        J.tinfo = G.tinfo;
+        J.perm = G.perm;
+        J.apre = G.apre;
         J.tpre = w.tpre + G.tile0;
         J.ranks = jobs[j].ranks;
         J.w0 = c.take<char>(size_t(g->n_nodes) * elem);
@@ -1188,9 +1387,13 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     plan->items = w.items;
     plan->first = w.first;
     plan->ctl = w.ctl;
-    plan->tile_cnt = w.cnt;
-    plan->tile_pre = w.tpre;
-    plan->scan_tmp = w.scan;
+    plan->total_rows = w.total_rows;
+    plan->tables[0] = w.cnt;
+    plan->tables[1] = w.tpre;
+    plan->tables[2] = w.scan;
+    plan->tables[3] = w.aflag;
+    plan->tables[4] = w.apre;
+    plan->tables[5] = w.ascan;
     return FFG_OK;
 }
 
@@ -1207,19 +1410,26 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
                FFG_ERR_INVALID_ARG;
     FFG_TRY(check_cuda(cudaMemsetAsync(plan->ctl, 0, sizeof(PrCtl) * plan->n_jobs, stream),
                        "memset"));
-    int dev = 0, sms = 0;
-    FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
-    FFG_TRY(check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
-    const int64_t want = (plan->total_tiles + kLayoutThreads / 32 - 1) / (kLayoutThreads / 32);
-    const int64_t cap = int64_t(sms) * 32;
-    k_pr_layout_batch<<<static_cast<unsigned>(std::max<int64_t>(1, std::min(want, cap))),
-                        kLayoutThreads, 0, stream>>>(static_cast<const GraphDev *>(plan->graphs),
-                                                     plan->n_graphs, plan->total_tiles);
+    int sms = 0;
+    FFG_TRY(device_sms(&sms));
+    const GraphDev *gr = static_cast<const GraphDev *>(plan->graphs);
+    const int64_t rows = plan->total_rows;
+    k_active_flags_batch<<<grid_for(rows, 256, sms), 256, 0, stream>>>(gr, plan->n_graphs, rows);
+    count_launch();
+    FFG_TRY(check_launch("k_active_flags_batch"));
+    FFG_TRY(scan_exclusive(static_cast<const int32_t *>(plan->tables[3]),
+                           static_cast<int64_t *>(plan->tables[4]), rows,
+                           static_cast<int64_t *>(plan->tables[5]), stream));
+    k_perm_batch<<<grid_for(rows, 256, sms), 256, 0, stream>>>(gr, plan->n_graphs, rows);
+    count_launch();
+    FFG_TRY(check_launch("k_perm_batch"));
+    k_pr_layout_batch<<<grid_for(plan->total_tiles, kLayoutThreads / 32, sms), kLayoutThreads, 0,
+                        stream>>>(gr, plan->n_graphs, plan->total_tiles);
     count_launch();
     FFG_TRY(check_launch("k_pr_layout_batch"));
-    FFG_TRY(scan_exclusive(static_cast<const int32_t *>(plan->tile_cnt),
-                           static_cast<int64_t *>(plan->tile_pre), plan->total_tiles,
-                           static_cast<int64_t *>(plan->scan_tmp), stream));
+    FFG_TRY(scan_exclusive(static_cast<const int32_t *>(plan->tables[0]),
+                           static_cast<int64_t *>(plan->tables[1]), plan->total_tiles,
+                           static_cast<int64_t *>(plan->tables[2]), stream));
     JobDev none{};
     const JobDev *jobs = static_cast<const JobDev *>(plan->jobs);
     const int2 *items = static_cast<const int2 *>(plan->items);
