@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -119,7 +120,8 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        out_dir = os.environ.get("FFG_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
@@ -172,7 +174,8 @@ def hbm_peak():
 
 
 def pagerank_bytes(n, e, iters, elem):
-    """Algorithmic DRAM bytes of one PageRank launch:
+    """Algorithmic DRAM bytes of one PageRank launch, for the CSR form of the
+    in-edges:
     per iteration in_idx 4E + in_ptr 8N + outdeg 4N + own w read + new w write
     (2 * elem * N); prologue outdeg + w write, epilogue outdeg + w read + ranks
     write."""
@@ -345,6 +348,9 @@ def run_gpu(args):
         cpu = {"value": u / s, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": ORACLE_SAMPLE + f" ({s:.1f} s)"}
 
+    scale = None
+    if not args.no_batched:
+        scale = run_scale(dev, stream)
     batched = sweep = None
     if not args.no_batched:
         batched = run_batched(dev, stream, steps=max(3, args.steps // 10), warmup=1,
@@ -374,7 +380,9 @@ def run_gpu(args):
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes": bytes_launch,
-                         "launch_ms": statistics.mean(durs)},
+                         "launch_ms": statistics.mean(durs),
+                         "l2_resident": True},
+            "beyond_l2": scale,
             "batched": batched,
             "sweep": sweep,
             "cpu_baseline": cpu,
@@ -389,6 +397,63 @@ def run_gpu(args):
 
 
 BATCH_P = [0.01, 0.02, 0.05, 0.10, 0.20]
+
+
+def run_scale(dev, stream, reps=3):
+    """The precision-at-scale space (the single large space plus two 3-valued
+    parameters: 19.5M raw / 12.8M valid configurations), Hamming FFG: FP32
+    PageRank timed per launch (L2 flushed before each), its working set far
+    beyond L2, and its error against an FP64 solve of the same graph."""
+    import torch
+    import ffg_inputs as fi
+    import paper_2210_01465_gb300 as ffg
+    spec = fi.precision_large()
+    fd = torch.from_numpy(fi.runtimes(spec, seed=1)).to(dev)
+    g = ffg.build_graph(ffg.Space.from_spec(spec), fd, ffg.HAMMING)
+    sh = stream.cuda_stream
+    need = ffg.pagerank_workspace_bytes(g.n_nodes, g.n_edges, ffg.F64)
+    ws = ffg.workspace(need, dev)
+    x32 = torch.empty(g.n_nodes, dtype=torch.float32, device=dev)
+    x64 = torch.empty(g.n_nodes, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
+    cp_ws = ffg.workspace(ffg.centrality_workspace_bytes(len(P_LIST)), dev)
+
+    def solve(prec, x):
+        assert ffg.pagerank_prepare(g.c, prec, ws.data_ptr(), need, sh) == 0
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, _, _ = ffg.pagerank_solve(g.c, DAMPING, TOL, 10000, prec, x.data_ptr(),
+                                      ffg.INIT_LAYOUT, ws.data_ptr(), need, sync=False,
+                                      stream=sh)
+        assert st == 0, st
+        e1.record(stream)
+        st, it, _ = ffg.pagerank_query(ws.data_ptr(), sh)
+        assert st == 0, st
+        cp = np.zeros(len(P_LIST))
+        assert ffg.centrality_proportion(g.c, fd.data_ptr(), x.data_ptr(), prec, P_LIST, cp,
+                                         cp_ws.data_ptr(), cp_ws.numel(), sh) == 0
+        return e0.elapsed_time(e1), it, cp
+
+    solve(ffg.F32, x32)
+    runs = [solve(ffg.F32, x32) for _ in range(reps)]
+    ms = statistics.median(r[0] for r in runs)
+    it, cp32 = runs[-1][1], runs[-1][2]
+    ms64, it64, cp64 = solve(ffg.F64, x64)
+    alg = pagerank_bytes(g.n_nodes, g.n_edges, it, 4)
+    peak, peak_kind = hbm_peak()
+    return {
+        "workload": "precision-at-scale space: 11 params, %d raw / %d valid configs, "
+                    "Hamming FFG, %d edges" % (g.n_raw, g.n_nodes, g.n_edges),
+        "pagerank_f32_ms": ms, "iters": it, "us_per_iter": 1e3 * ms / it,
+        "value": g.n_edges * it / (ms / 1e3), "unit": UNIT,
+        "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak,
+                     "peak_kind": peak_kind, "algorithmic_bytes": alg, "l2_resident": False},
+        "pagerank_f64_ms": ms64, "iters_f64": it64, "us_per_iter_f64": 1e3 * ms64 / it64,
+        "f32_vs_f64_rank_l1": float((x32.double() - x64).abs().sum()),
+        "f32_vs_f64_cp_max_abs": float(np.abs(cp32 - cp64).max()),
+    }
 
 
 def _build_all(ffg, spaces, fits, nbh, graphs=None, wss=None, stream=None):
