@@ -550,7 +550,7 @@ def run_batched(dev, stream, steps, warmup, rank=0, world=1):
             "plain_f64_edges_iters_per_s": units64 / (ms64 / 1e3),
             "batched_f32_vs_plain_f64_speedup": (units / (pr_ms / 1e3)) / (units64 / (ms64 / 1e3)),
             "blocks": int(batch.plan.n_blocks),
-            "autotune": {"chosen (split/grain/max_blocks)": "/".join(map(str, best)),
+            "autotune": {"chosen (split/grain/max_blocks/block_warps/claim)": "/".join(map(str, best)),
                          "ms_per_candidate": tried}}
 
 
@@ -605,7 +605,7 @@ def run_sweep(dev, stream, steps, warmup):
             "solves": len(E), "cuda_graph": captured, "ms_per_step": m,
             "solves_per_s": len(E) / (m / 1e3), "value": units / (m / 1e3), "unit": UNIT,
             "blocks": int(batch.plan.n_blocks),
-            "autotune": {"chosen (split/grain/max_blocks)": "/".join(map(str, best)),
+            "autotune": {"chosen (split/grain/max_blocks/block_warps/claim)": "/".join(map(str, best)),
                          "ms_per_candidate": tried}}
 
 

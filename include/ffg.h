@@ -223,19 +223,22 @@ typedef struct {
 /* Filled by pagerank_batch_plan; plain data owned by the caller (device
  * pointers point into the plan's workspace). */
 typedef struct {
-    int32_t prec, n_jobs, n_graphs, n_blocks;
+    int32_t prec, n_jobs, n_graphs, n_blocks, warps, n_items, claim, reserved;
     int64_t total_tiles;
-    void *jobs, *graphs, *items, *first, *ctl;
+    void *jobs, *graphs, *items, *first, *queue, *ctl;
     int64_t total_rows;
     void *tables[8];  /* per-row and per-tile tables of all graphs (internal) */
 } ffg_pr_batch;
 
 size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec);
 
-/* Host-side planning: validates the jobs, assigns every job a group of
- * blocks of one cooperative grid (large jobs get several dedicated blocks,
- * small ones one block each, longest first onto the least loaded block),
- * carves the workspace and uploads the tables.  Synchronises `stream`. */
+/* Host-side planning: validates the jobs, gives every job a group of blocks
+ * of one cooperative grid (large jobs several blocks, small ones one) and
+ * an order: per-block lists (one-block jobs longest first onto the least
+ * loaded block) or a claim order (the ranks of multi-block jobs first, then
+ * the one-block jobs longest first; a block takes the next unclaimed one
+ * whenever it is free).  Carves the workspace and uploads the tables.
+ * Synchronises `stream`. */
 ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec,
                                void *workspace, size_t ws_bytes, ffg_pr_batch *plan,
                                void *stream);
@@ -243,11 +246,13 @@ ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec 
 /* Planning options.  A job whose cost exceeds `split` times the per-block
  * share of the batch gets its own blocks, about one per `grain` shares (the
  * others run on one block each); `max_blocks` caps the grid (0 = every
- * co-resident block).  Defaults: 1.0, 1.0, 0.  They change only the
- * schedule, never results or the workspace size. */
+ * co-resident block); `block_warps` is 8 (256-thread blocks, several per SM)
+ * or 24 (one 768-thread block per SM), 0 = 24; `claim` 1 selects the claim
+ * order, 0 the per-block lists.  pagerank_batch_plan uses 1.0, 1.0, 0, 8, 0.
+ * They change only the schedule, never results or the workspace size. */
 typedef struct {
     double split, grain;
-    int32_t max_blocks, reserved;
+    int32_t max_blocks, block_warps, claim, reserved;
 } ffg_pr_tuning;
 
 ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec,

@@ -1,9 +1,12 @@
 """Autotuner for the batched PageRank schedule.
 
-The kernels' shapes are fixed at build time (the build-time sweep found the
-defaults best on the single large space); what varies with the workload is
-the schedule of a batch: which jobs get dedicated blocks (`split`), how many
-(`grain`) and how large the grid is (`max_blocks`).  ``tune`` runs the
+The tile shape is fixed (32 rows, one per lane; the gather step was chosen
+by a build-time sweep on the single large space); what varies with the
+workload is the schedule of a batch: which jobs get dedicated blocks
+(`split`), how many (`grain`), how large the grid is (`max_blocks`) and how
+wide its blocks are (`block_warps`: 8 warps, several blocks per SM, or 24,
+one block per SM) and whether blocks follow fixed per-block lists or claim
+jobs as they free up (`claim`).  ``tune`` runs the
 batch once per candidate (same workspace, re-planned), times it with CUDA
 events and leaves the fastest plan in place.  Results never depend on the
 tuning, only the time does.
@@ -13,18 +16,20 @@ from __future__ import annotations
 import json
 import os
 
+# (split, grain, max_blocks, block_warps, claim)
 CANDIDATES = (
-    (1.0, 1.0, 0),
-    (2.0, 1.0, 0),
-    (0.5, 0.5, 0),
-    (1.0, 0.5, 0),
-    (0.25, 0.25, 0),
+    (1.0, 1.0, 0, 8, 0),
+    (2.0, 1.0, 0, 8, 0),
+    (1.0, 1.0, 0, 24, 0),
+    (1.0, 1.0, 0, 8, 1),
+    (1.0, 1.0, 0, 24, 1),
+    (0.5, 0.5, 0, 24, 1),
 )
 
 
 def tune(batch, candidates=CANDIDATES, reps: int = 1, table_path: str | None = None):
     """Pick the fastest schedule for ``batch`` (a PageRankBatch); returns
-    (best (split, grain, max_blocks), {candidate: ms})."""
+    (best (split, grain, max_blocks, block_warps, claim), {candidate: ms})."""
     import torch
     times = {}
     for cand in candidates:
@@ -50,7 +55,7 @@ def tune(batch, candidates=CANDIDATES, reps: int = 1, table_path: str | None = N
             with open(table_path) as fh:
                 table = json.load(fh)
         table[key] = {"split": best[0], "grain": best[1], "max_blocks": best[2],
-                      "ms": times[best]}
+                      "block_warps": best[3], "claim": best[4], "ms": times[best]}
         with open(table_path, "w") as fh:
             json.dump(table, fh, indent=1)
-    return best, {f"{c[0]}/{c[1]}/{c[2]}": round(t, 3) for c, t in times.items()}
+    return best, {"/".join(map(str, c)): round(t, 3) for c, t in times.items()}

@@ -816,13 +816,20 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
 }
 
 // The persistent kernel.  With jobs == nullptr it runs `single` on the whole
-// grid; otherwise block b runs the plan items [first[b], first[b+1]) in
-// order -- (job, rank) pairs, each block's multi-block job first, so that
-// no two groups ever wait on each other.
+// grid.  Otherwise it runs the plan's items -- (job, rank) pairs -- in one
+// of two orders:
+// - lists (queue == nullptr): block b runs items [first[b], first[b+1]),
+//   its multi-block rank (if any) first, so no two groups wait on each other;
+// - claims: the blocks claim the items in order through a counter (`queue`,
+//   zero at launch).  The ranks of every multi-block job come first and
+//   number at most the grid size, so when all blocks wait at group barriers
+//   every multi-block rank has been claimed and no group waits forever;
+//   one-block jobs follow, longest first, and go to whichever block is free.
 template <typename T, int W>
 __global__ void __launch_bounds__(32 * W, W > kWarpsBatch ? 1 : FFG_PR_MINBLOCKS)
     k_pagerank(const JobDev *__restrict__ jobs, const int2 *__restrict__ items,
-               const int *__restrict__ first, int plan_blocks, JobDev single) {
+               const int *__restrict__ first, int *__restrict__ queue, int n_items,
+               JobDev single) {
     extern __shared__ __align__(128) unsigned char s_dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // shared memory: per-warp stages, then mbarriers
@@ -844,8 +851,21 @@ __global__ void __launch_bounds__(32 * W, W > kWarpsBatch ? 1 : FFG_PR_MINBLOCKS
         run_job<T, W>(single, blockIdx.x, st);
         return;
     }
-    if (static_cast<int>(gridDim.x) != plan_blocks) return;  // the host checks this too
-    for (int i = first[blockIdx.x]; i < first[blockIdx.x + 1]; ++i) {
+    if (queue == nullptr) {
+        for (int i = first[blockIdx.x]; i < first[blockIdx.x + 1]; ++i) {
+            const int2 item = items[i];
+            const JobDev J = jobs[item.x];
+            if (!run_job<T, W>(J, item.y, st)) return;
+        }
+        return;
+    }
+    __shared__ int s_item;
+    while (true) {
+        __syncthreads();  // every thread has read the previous item
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int i = s_item;
+        if (i >= n_items) return;
         const int2 item = items[i];
         const JobDev J = jobs[item.x];
         if (!run_job<T, W>(J, item.y, st)) return;
@@ -957,12 +977,13 @@ ffg_status kernel_config(int *blocks_per_sm, int *sms) {
 }
 
 template <typename T, int W>
-ffg_status launch_pr(const JobDev *jobs, const int2 *items, const int *first, int nb,
-                     const JobDev &single, cudaStream_t stream) {
+ffg_status launch_pr(const JobDev *jobs, const int2 *items, const int *first, int *queue,
+                     int n_items, int nb, const JobDev &single, cudaStream_t stream) {
     auto kern = k_pagerank<T, W>;
     const size_t smem = pr_smem_bytes<W>();
     JobDev s = single;
-    void *args[] = {(void *)&jobs, (void *)&items, (void *)&first, (void *)&nb, (void *)&s};
+    void *args[] = {(void *)&jobs, (void *)&items, (void *)&first, (void *)&queue,
+                    (void *)&n_items, (void *)&s};
     FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)kern, dim3(nb), dim3(32 * W),
                                                    args, smem, stream),
                        "k_pagerank"));
@@ -999,7 +1020,7 @@ ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, in
     J.init = init;
     J.group = nb;
     J.pad = 0;
-    return launch_pr<T, W>(nullptr, nullptr, nullptr, nb, J, stream);
+    return launch_pr<T, W>(nullptr, nullptr, nullptr, nullptr, 0, nb, J, stream);
 }
 
 ffg_status read_result(const PrCtl *dctl, int32_t *iters_out, double *residual_out,
@@ -1111,7 +1132,9 @@ namespace {
 struct PlanHost {
     int nb = 0;
     std::vector<int> group;           // per job
-    std::vector<int> first;           // nb + 1
+    int warps = kWarpsSingle;         // warps per block
+    int claim = 0;                    // claim order (else per-block lists)
+    std::vector<int> first;           // per-block lists: nb + 1
     std::vector<int2> items;          // (job, rank)
     std::vector<int> graph_of_job;    // job -> distinct graph index
     std::vector<const ffg_graph *> graphs;
@@ -1133,11 +1156,14 @@ ffg_status check_job(const ffg_pr_job &j, int idx) {
     return FFG_OK;
 }
 
-ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, const ffg_pr_tuning &tu,
-                     PlanHost &P) {
+// Group sizes and the order of the items (see k_pagerank).
+ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, int warps,
+                     const ffg_pr_tuning &tu, PlanHost &P) {
+    P.claim = tu.claim;
     // distinct graphs (jobs may share one)
     std::unordered_map<const int64_t *, int> gidx;
     P.graph_of_job.resize(n_jobs);
+    P.warps = warps;
     std::vector<double> cost(n_jobs);
     int64_t useful = 0;
     for (int j = 0; j < n_jobs; ++j) {
@@ -1155,7 +1181,7 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, const ffg_p
         P.graph_of_job[j] = it->second;
         cost[j] = double(g->n_edges + kRowCost * g->n_nodes) * est_iters(jobs[j].damping);
         const int64_t tiles = (g->n_nodes + 31) / 32;
-        useful += std::max<int64_t>(1, (tiles + 4 * kWarpsBatch - 1) / (4 * kWarpsBatch));
+        useful += std::max<int64_t>(1, (tiles + 4 * warps - 1) / (4 * warps));
     }
     int cap = nb_max;
     if (tu.max_blocks > 0 && tu.max_blocks < cap) cap = tu.max_blocks;
@@ -1167,39 +1193,46 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, const ffg_p
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     P.group.assign(n_jobs, 1);
+    P.items.clear();
+    int used = 0;  // ranks of multi-block jobs (blocks 0 .. used-1 in list order), at most nb
+    std::vector<int> small;
     std::vector<std::vector<int2>> per_block(nb);
     std::vector<double> load(nb, 0.0);
-    int next_block = 0;
-    std::vector<int> small;
     for (int j : order) {
         const int64_t tiles = (jobs[j].g->n_nodes + 31) / 32;
         // a job above `split` shares gets about one block per `grain` shares
         int k = cost[j] > tu.split * share
                     ? static_cast<int>(std::llround(cost[j] / (tu.grain * share)))
                     : 1;
-        k = static_cast<int>(std::min<int64_t>(k, std::max<int64_t>(1, tiles / kWarpsBatch)));
-        k = std::min(k, nb - next_block);
+        k = static_cast<int>(std::min<int64_t>(k, std::max<int64_t>(1, tiles / warps)));
+        k = std::min(k, nb - used);
         if (k >= 2) {
             P.group[j] = k;
             for (int r = 0; r < k; ++r) {
-                per_block[next_block + r].push_back(make_int2(j, r));
-                load[next_block + r] += cost[j] / k;
+                P.items.push_back(make_int2(j, r));
+                per_block[used + r].push_back(make_int2(j, r));
+                load[used + r] += cost[j] / k;
             }
-            next_block += k;
+            used += k;
         } else {
             small.push_back(j);
         }
     }
-    // one-block jobs, longest first, onto the least loaded block
+    P.first.clear();
+    if (P.claim) {
+        for (int j : small) P.items.push_back(make_int2(j, 0));  // longest first
+        return FFG_OK;
+    }
+    // per-block lists: one-block jobs, longest first, onto the least loaded block
     using Slot = std::pair<double, int>;
     std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
     for (int b = 0; b < nb; ++b) heap.push({load[b], b});
     for (int j : small) {
-        Slot s = heap.top();
+        Slot sl = heap.top();
         heap.pop();
-        per_block[s.second].push_back(make_int2(j, 0));
-        s.first += cost[j];
-        heap.push(s);
+        per_block[sl.second].push_back(make_int2(j, 0));
+        sl.first += cost[j];
+        heap.push(sl);
     }
     P.first.assign(nb + 1, 0);
     P.items.clear();
@@ -1214,6 +1247,7 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, const ffg_p
 struct BatchWs {
     JobDev *jobs;
     GraphDev *graphs;
+    int *queue;
     int *first;
     int2 *items;
     PrCtl *ctl;
@@ -1232,16 +1266,17 @@ struct BatchWs {
 // per distinct graph the layout and tile metadata.  host_jobs / host_graphs
 // (if non-NULL) receive the device pointers of every job and graph.
 BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
-                    const PlanHost &P, int nb_max, std::vector<JobDev> *host_jobs,
+                    const PlanHost &P, int cap, std::vector<JobDev> *host_jobs,
                     std::vector<GraphDev> *host_graphs) {
     Carver c(base);
     BatchWs w;
     w.jobs = c.take<JobDev>(n_jobs);
     w.graphs = c.take<GraphDev>(P.graphs.size());
-    // plan tables sized for any tuning: at most nb_max blocks, and a job in a
-    // group of k blocks adds k - 1 items, with sum(k) <= nb_max
-    w.first = c.take<int>(size_t(nb_max) + 1);
-    w.items = c.take<int2>(size_t(n_jobs) + nb_max);
+    // plan tables sized for any tuning: a job in a group of k blocks adds
+    // k - 1 items, with sum(k) <= the grid size <= cap
+    w.queue = c.take<int>(1);
+    w.first = c.take<int>(size_t(cap) + 1);
+    w.items = c.take<int2>(size_t(n_jobs) + cap);
     w.ctl = c.take<PrCtl>(n_jobs);
     int64_t total_tiles = 0;
     for (const ffg_graph *g : P.graphs) total_tiles += (g->n_nodes + 31) / 32;
@@ -1304,29 +1339,46 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
     return w;
 }
 
-ffg_status batch_blocks(ffg_prec prec, int *nb_max) {
+// co-resident blocks of the batch kernel with `warps` warps per block
+ffg_status batch_blocks(ffg_prec prec, int warps, int *nb_max) {
     int per_sm = 0, sms = 0;
-    if (prec == FFG_F64) FFG_TRY((kernel_config<double, kWarpsBatch>(&per_sm, &sms)));
-    else FFG_TRY((kernel_config<float, kWarpsBatch>(&per_sm, &sms)));
+    if (warps == kWarpsBatch) {
+        if (prec == FFG_F64) FFG_TRY((kernel_config<double, kWarpsBatch>(&per_sm, &sms)));
+        else FFG_TRY((kernel_config<float, kWarpsBatch>(&per_sm, &sms)));
+    } else {
+        if (prec == FFG_F64) FFG_TRY((kernel_config<double, kWarpsSingle>(&per_sm, &sms)));
+        else FFG_TRY((kernel_config<float, kWarpsSingle>(&per_sm, &sms)));
+    }
     *nb_max = std::min(kMaxBlocks, sms * per_sm);
+    return FFG_OK;
+}
+
+// plan tables are sized for the larger of the two grids, so that the
+// workspace does not depend on the tuning
+ffg_status batch_cap(ffg_prec prec, int *cap) {
+    int a = 0, b = 0;
+    FFG_TRY(batch_blocks(prec, kWarpsBatch, &a));
+    FFG_TRY(batch_blocks(prec, kWarpsSingle, &b));
+    *cap = std::max(a, b);
     return FFG_OK;
 }
 
 }  // namespace
 }  // namespace ffg
 
-const ffg_pr_tuning kDefaultTuning = {1.0, 1.0, 0, 0};
+// per-block lists of 8-warp blocks: the fastest on the 234-space batch
+const ffg_pr_tuning kDefaultTuning = {1.0, 1.0, 0, kWarpsBatch, 0, 0};
 
 extern "C" size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs,
                                                  ffg_prec prec) {
     clear_error();
     if (!jobs || n_jobs < 1 || (prec != FFG_F64 && prec != FFG_F32)) return 0;
-    int nb_max = 0;
-    if (batch_blocks(prec, &nb_max) != FFG_OK) return 0;
+    int cap = 0, nb_max = 0;
+    if (batch_cap(prec, &cap) != FFG_OK || batch_blocks(prec, kWarpsSingle, &nb_max) != FFG_OK)
+        return 0;
     PlanHost P;
-    if (make_plan(jobs, n_jobs, nb_max, kDefaultTuning, P) != FFG_OK) return 0;
-    return carve_batch(nullptr, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, nb_max, nullptr,
-                       nullptr)
+    if (make_plan(jobs, n_jobs, nb_max, kWarpsSingle, kDefaultTuning, P) != FFG_OK) return 0;
+    return carve_batch(nullptr, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, cap, nullptr, nullptr)
         .bytes;
 }
 
@@ -1351,28 +1403,33 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     if (!aligned256(workspace))
         return set_error("workspace not 256-byte aligned"), FFG_ERR_INVALID_ARG;
     const ffg_pr_tuning tu = tuning ? *tuning : kDefaultTuning;
-    if (!(tu.split > 0.0) || !(tu.grain > 0.0) || tu.max_blocks < 0)
-        return set_error("tuning: split and grain must be > 0, max_blocks >= 0"),
+    const int warps = tu.block_warps ? tu.block_warps : kWarpsSingle;
+    if (!(tu.split > 0.0) || !(tu.grain > 0.0) || tu.max_blocks < 0 ||
+        (warps != kWarpsBatch && warps != kWarpsSingle) || (tu.claim != 0 && tu.claim != 1))
+        return set_error("tuning: split and grain must be > 0, max_blocks >= 0, block_warps "
+                         "0, %d or %d, claim 0 or 1", kWarpsBatch, kWarpsSingle),
                FFG_ERR_INVALID_ARG;
-    int nb_max = 0;
-    FFG_TRY(batch_blocks(prec, &nb_max));
+    int cap = 0, nb_max = 0;
+    FFG_TRY(batch_cap(prec, &cap));
+    FFG_TRY(batch_blocks(prec, warps, &nb_max));
     PlanHost P;
-    FFG_TRY(make_plan(jobs, n_jobs, nb_max, tu, P));
+    FFG_TRY(make_plan(jobs, n_jobs, nb_max, warps, tu, P));
     std::vector<JobDev> jd;
     std::vector<GraphDev> gd;
-    BatchWs w = carve_batch(workspace, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, nb_max, &jd, &gd);
+    BatchWs w = carve_batch(workspace, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, cap, &jd, &gd);
     if (ws_bytes < w.bytes)
         return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
-    if (P.nb > nb_max || P.items.size() > size_t(n_jobs) + nb_max)
+    if (P.nb > nb_max || P.items.size() > size_t(n_jobs) + cap)
         return set_error("internal: plan exceeds its tables"), FFG_ERR_INVALID_ARG;
     FFG_TRY(check_cuda(cudaMemcpyAsync(w.jobs, jd.data(), sizeof(JobDev) * jd.size(),
                                        cudaMemcpyHostToDevice, stream), "upload jobs"));
     FFG_TRY(check_cuda(cudaMemcpyAsync(w.graphs, gd.data(), sizeof(GraphDev) * gd.size(),
                                        cudaMemcpyHostToDevice, stream), "upload graphs"));
-    FFG_TRY(check_cuda(cudaMemcpyAsync(w.first, P.first.data(), sizeof(int) * P.first.size(),
-                                       cudaMemcpyHostToDevice, stream), "upload plan"));
     if (!P.items.empty())
         FFG_TRY(check_cuda(cudaMemcpyAsync(w.items, P.items.data(), sizeof(int2) * P.items.size(),
+                                           cudaMemcpyHostToDevice, stream), "upload plan"));
+    if (!P.first.empty())
+        FFG_TRY(check_cuda(cudaMemcpyAsync(w.first, P.first.data(), sizeof(int) * P.first.size(),
                                            cudaMemcpyHostToDevice, stream), "upload plan"));
     FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync plan upload"));
     int64_t tiles = 0;
@@ -1381,10 +1438,14 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     plan->n_jobs = n_jobs;
     plan->n_graphs = static_cast<int32_t>(P.graphs.size());
     plan->n_blocks = P.nb;
+    plan->warps = P.warps;
+    plan->claim = P.claim;
+    plan->n_items = static_cast<int32_t>(P.items.size());
     plan->total_tiles = tiles;
     plan->jobs = w.jobs;
     plan->graphs = w.graphs;
     plan->items = w.items;
+    plan->queue = w.queue;
     plan->first = w.first;
     plan->ctl = w.ctl;
     plan->total_rows = w.total_rows;
@@ -1403,13 +1464,16 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
     if (!plan || plan->n_jobs < 1 || !plan->jobs || !plan->ctl || plan->n_blocks < 1)
         return set_error("plan is empty"), FFG_ERR_INVALID_ARG;
     const ffg_prec prec = static_cast<ffg_prec>(plan->prec);
+    if (plan->warps != kWarpsBatch && plan->warps != kWarpsSingle)
+        return set_error("plan has %d warps per block", plan->warps), FFG_ERR_INVALID_ARG;
     int nb_max = 0;
-    FFG_TRY(batch_blocks(prec, &nb_max));
+    FFG_TRY(batch_blocks(prec, plan->warps, &nb_max));
     if (plan->n_blocks > nb_max)
         return set_error("plan made for %d blocks, %d fit", plan->n_blocks, nb_max),
                FFG_ERR_INVALID_ARG;
     FFG_TRY(check_cuda(cudaMemsetAsync(plan->ctl, 0, sizeof(PrCtl) * plan->n_jobs, stream),
                        "memset"));
+    FFG_TRY(check_cuda(cudaMemsetAsync(plan->queue, 0, sizeof(int), stream), "memset"));
     int sms = 0;
     FFG_TRY(device_sms(&sms));
     const GraphDev *gr = static_cast<const GraphDev *>(plan->graphs);
@@ -1434,8 +1498,16 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
     const JobDev *jobs = static_cast<const JobDev *>(plan->jobs);
     const int2 *items = static_cast<const int2 *>(plan->items);
     const int *first = static_cast<const int *>(plan->first);
-    if (prec == FFG_F64) return launch_pr<double, kWarpsBatch>(jobs, items, first, plan->n_blocks, none, stream);
-    return launch_pr<float, kWarpsBatch>(jobs, items, first, plan->n_blocks, none, stream);
+    int *queue = plan->claim ? static_cast<int *>(plan->queue) : nullptr;
+    const int ni = plan->n_items, nb = plan->n_blocks;
+    if (plan->warps == kWarpsBatch) {
+        if (prec == FFG_F64)
+            return launch_pr<double, kWarpsBatch>(jobs, items, first, queue, ni, nb, none, stream);
+        return launch_pr<float, kWarpsBatch>(jobs, items, first, queue, ni, nb, none, stream);
+    }
+    if (prec == FFG_F64)
+        return launch_pr<double, kWarpsSingle>(jobs, items, first, queue, ni, nb, none, stream);
+    return launch_pr<float, kWarpsSingle>(jobs, items, first, queue, ni, nb, none, stream);
 }
 
 extern "C" ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *iters_out,

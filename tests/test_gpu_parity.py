@@ -335,7 +335,7 @@ def test_batched_centrality_matches_single():
 
 def test_bounded_wait_reports_timeout():
     """Fault injected on the host: the plan is edited so that one block of a
-    multi-block job never starts.  The job's other blocks give up at the
+    multi-block job never starts.  The job's other block gives up at the
     bounded barrier and the host reads FFG_ERR_TIMEOUT; the context stays
     usable."""
     spec = fi.single_large()
@@ -343,16 +343,13 @@ def test_bounded_wait_reports_timeout():
     small = fi.single_small()
     gs, _ = run_build(small, fi.runtimes(small, 2), "hamming")
     batch = ffg.PageRankBatch([(g, 0.85), (gs, 0.85)], prec=ffg.F32)
-    nb = batch.plan.n_blocks
+    batch.replan((1.0, 1.0, 0, 8, 1))   # claim order
     ws_base = batch.ws.data_ptr()
-    first = batch.ws[batch.plan.first - ws_base:batch.plan.first - ws_base + 4 * (nb + 1)]
-    first = first.view(torch.int32)
     items = batch.ws[batch.plan.items - ws_base:].view(torch.int32)
-    f = first.cpu().numpy()
-    # blocks 0 and 1 start with ranks 0 and 1 of the large job
-    assert items[2 * f[0]].item() == 0 and items[2 * f[0] + 1].item() == 0
-    assert items[2 * f[1]].item() == 0 and items[2 * f[1] + 1].item() == 1
-    first[1] = int(f[2])          # block 1 runs nothing; block 0 would run ranks 0 and 1
+    # the large job's ranks are claimed first: (0, 0), (0, 1), ...
+    assert items[0].item() == 0 and items[1].item() == 0
+    assert items[2].item() == 0 and items[3].item() == 1
+    batch.plan.n_items = 1        # only rank 0 of the large job is ever claimed
     torch.cuda.synchronize()
     batch.run()
     st, it, res, sts = ffg.pagerank_batch_query(batch.plan,
@@ -401,7 +398,8 @@ def test_batch_tuning_changes_schedule_not_results():
             refs.append(oracle.pagerank_exact(og, alpha))
     batch = ffg.PageRankBatch(specs, prec=ffg.F64, tol=1e-12)
     first = None
-    for tuning in ((1.0, 1.0, 0), (0.1, 0.1, 0), (5.0, 1.0, 3)):
+    for tuning in ((1.0, 1.0, 0), (0.1, 0.1, 0), (5.0, 1.0, 3), (1.0, 1.0, 0, 8),
+                   (0.1, 0.1, 0, 8), (0.1, 0.1, 0, 8, 1), (0.5, 0.5, 0, 24, 1)):
         batch.replan(tuning)
         batch.run()
         it, res, st = batch.query()
