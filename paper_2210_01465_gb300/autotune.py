@@ -19,10 +19,11 @@ import os
 # (split, grain, max_blocks, block_warps, claim)
 CANDIDATES = (
     (1.0, 1.0, 0, 8, 0),
-    (2.0, 1.0, 0, 8, 0),
-    (1.0, 1.0, 0, 24, 0),
-    (1.0, 1.0, 0, 8, 1),
-    (1.0, 1.0, 0, 24, 1),
+    (0.5, 0.25, 0, 8, 0),
+    (0.5, 0.5, 0, 24, 0),
+    (0.5, 0.1, 0, 24, 0),
+    (0.25, 0.05, 0, 24, 0),
+    (0.1, 0.02, 0, 24, 0),
     (0.5, 0.5, 0, 24, 1),
 )
 

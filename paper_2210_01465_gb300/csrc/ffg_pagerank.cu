@@ -1194,10 +1194,17 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, int warps,
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     P.group.assign(n_jobs, 1);
     P.items.clear();
-    int used = 0;  // ranks of multi-block jobs (blocks 0 .. used-1 in list order), at most nb
+    // Claim order: the multi-block ranks all fit in the grid (sum k <= nb).
+    // Lists: a block may hold ranks of several multi-block jobs; every block
+    // runs them in the same global order (largest job first), then its
+    // one-block jobs, so a group only ever waits for blocks busy with an
+    // earlier job and the first job in the order always completes.  A job's
+    // ranks go to the k least loaded blocks.
+    int used = 0;  // claim order: ranks of multi-block jobs so far
     std::vector<int> small;
     std::vector<std::vector<int2>> per_block(nb);
     std::vector<double> load(nb, 0.0);
+    std::vector<int> by_load(nb);
     for (int j : order) {
         const int64_t tiles = (jobs[j].g->n_nodes + 31) / 32;
         // a job above `split` shares gets about one block per `grain` shares
@@ -1205,17 +1212,26 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, int warps,
                     ? static_cast<int>(std::llround(cost[j] / (tu.grain * share)))
                     : 1;
         k = static_cast<int>(std::min<int64_t>(k, std::max<int64_t>(1, tiles / warps)));
-        k = std::min(k, nb - used);
-        if (k >= 2) {
-            P.group[j] = k;
-            for (int r = 0; r < k; ++r) {
-                P.items.push_back(make_int2(j, r));
-                per_block[used + r].push_back(make_int2(j, r));
-                load[used + r] += cost[j] / k;
-            }
-            used += k;
-        } else {
+        k = std::min(k, P.claim ? nb - used : nb);
+        if (k < 2) {
             small.push_back(j);
+            continue;
+        }
+        P.group[j] = k;
+        if (P.claim) {
+            for (int r = 0; r < k; ++r) P.items.push_back(make_int2(j, r));
+            used += k;
+            continue;
+        }
+        std::iota(by_load.begin(), by_load.end(), 0);
+        std::stable_sort(by_load.begin(), by_load.end(),
+                         [&](int a, int b) { return load[a] < load[b]; });
+        // the k least loaded blocks start together: they all wait for the
+        // most loaded of them
+        const double start = load[by_load[k - 1]];
+        for (int r = 0; r < k; ++r) {
+            per_block[by_load[r]].push_back(make_int2(j, r));
+            load[by_load[r]] = start + cost[j] / k;
         }
     }
     P.first.clear();
@@ -1272,11 +1288,10 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
     BatchWs w;
     w.jobs = c.take<JobDev>(n_jobs);
     w.graphs = c.take<GraphDev>(P.graphs.size());
-    // plan tables sized for any tuning: a job in a group of k blocks adds
-    // k - 1 items, with sum(k) <= the grid size <= cap
+    // plan tables sized for any tuning: a job has at most one item per block
     w.queue = c.take<int>(1);
     w.first = c.take<int>(size_t(cap) + 1);
-    w.items = c.take<int2>(size_t(n_jobs) + cap);
+    w.items = c.take<int2>(size_t(n_jobs) * cap);
     w.ctl = c.take<PrCtl>(n_jobs);
     int64_t total_tiles = 0;
     for (const ffg_graph *g : P.graphs) total_tiles += (g->n_nodes + 31) / 32;
@@ -1419,7 +1434,7 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     BatchWs w = carve_batch(workspace, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, cap, &jd, &gd);
     if (ws_bytes < w.bytes)
         return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
-    if (P.nb > nb_max || P.items.size() > size_t(n_jobs) + cap)
+    if (P.nb > nb_max || P.items.size() > size_t(n_jobs) * cap)
         return set_error("internal: plan exceeds its tables"), FFG_ERR_INVALID_ARG;
     FFG_TRY(check_cuda(cudaMemcpyAsync(w.jobs, jd.data(), sizeof(JobDev) * jd.size(),
                                        cudaMemcpyHostToDevice, stream), "upload jobs"));
