@@ -146,6 +146,49 @@ ffg_status ffg_build_fill(const ffg_space *space, const double *fitness_raw, ffg
                           double fail_thr, ffg_graph *g, void *workspace, size_t ws_bytes,
                           void *stream);
 
+/* ---- batched construction: many spaces in a few launches ----
+ * A build job: a space (HOST), its fitness (DEVICE, n_raw doubles), the
+ * neighbourhood, the failure threshold and its graph (HOST struct; DEVICE
+ * arrays).  Same graphs, bit for bit, as ffg_build_count + ffg_build_fill
+ * per job.
+ *
+ * ffg_build_batch_count runs the count phase of every job (a handful of
+ * launches over all jobs) and one read-back, and writes each graph's
+ * n_raw, n_nodes, n_edges, n_minima and f_opt; FFG_ERR_EMPTY if a job has
+ * no valid configuration (all sizes are written).  The caller then gives
+ * every graph its arrays and calls ffg_build_batch_fill, which records them
+ * in the workspace and fills every graph (synchronises `stream` once).
+ * ffg_build_batch_rerun repeats both phases from the tables in the
+ * workspace with launches only (no host work, no synchronisation: it can be
+ * captured in a CUDA graph); it is meant for unchanged inputs.  A job whose
+ * recomputed counts differ from the sizes of its arrays (its fitness
+ * changed) is left untouched and marked: ffg_build_batch_query reads the
+ * per-job status (FFG_OK or FFG_ERR_INVALID_ARG) into status_out (HOST,
+ * n_jobs) and returns the worst.  The workspace (DEVICE, 256-byte aligned,
+ * ffg_build_batch_workspace_bytes) and the plan must stay untouched between
+ * the calls. */
+typedef struct {
+    const ffg_space *space;
+    const double *fitness_raw;
+    int32_t nbh, reserved;
+    double fail_thr;
+    ffg_graph *g;
+} ffg_build_job;
+
+typedef struct {
+    int32_t n_jobs, reserved;
+    int64_t total_raw, total_words, total_blocks, total_rows;
+    void *tables[16]; /* device pointers into the workspace (internal) */
+} ffg_build_batch;
+
+size_t ffg_build_batch_workspace_bytes(const ffg_build_job *jobs, int32_t n_jobs);
+ffg_status ffg_build_batch_count(const ffg_build_job *jobs, int32_t n_jobs, void *workspace,
+                                 size_t ws_bytes, ffg_build_batch *plan, void *stream);
+ffg_status ffg_build_batch_fill(const ffg_build_job *jobs, int32_t n_jobs, ffg_build_batch *plan,
+                                void *stream);
+ffg_status ffg_build_batch_rerun(const ffg_build_batch *plan, void *stream);
+ffg_status ffg_build_batch_query(const ffg_build_batch *plan, int32_t *status_out, void *stream);
+
 /* ---- PageRank (Sec. VII-B) ----
  * Column-stochastic matrix A[v,u] = 1/outdeg(u) for every edge u -> v, with
  * damping `damping`, uniform teleport, and the mass of nodes without

@@ -78,6 +78,18 @@ class ffg_pr_batch(C.Structure):
                 ("ctl", C.c_void_p), ("total_rows", C.c_int64), ("tables", C.c_void_p * 8)]
 
 
+class ffg_build_job(C.Structure):
+    _fields_ = [("space", C.POINTER(ffg_space)), ("fitness_raw", C.c_void_p),
+                ("nbh", C.c_int32), ("reserved", C.c_int32), ("fail_thr", C.c_double),
+                ("g", C.POINTER(ffg_graph))]
+
+
+class ffg_build_batch(C.Structure):
+    _fields_ = [("n_jobs", C.c_int32), ("reserved", C.c_int32), ("total_raw", C.c_int64),
+                ("total_words", C.c_int64), ("total_blocks", C.c_int64),
+                ("total_rows", C.c_int64), ("tables", C.c_void_p * 16)]
+
+
 class ffg_pr_tuning(C.Structure):
     _fields_ = [("split", C.c_double), ("grain", C.c_double), ("max_blocks", C.c_int32),
                 ("block_warps", C.c_int32), ("claim", C.c_int32), ("reserved", C.c_int32)]
@@ -89,6 +101,8 @@ class ffg_cp_job(C.Structure):
 
 # names of include/ffg.h's entry points (the ABI test checks the header)
 ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
+                "ffg_build_batch_workspace_bytes", "ffg_build_batch_count",
+                "ffg_build_batch_fill", "ffg_build_batch_rerun", "ffg_build_batch_query",
                 "pagerank_workspace_bytes", "pagerank_prepare", "pagerank_solve",
                 "pagerank_solve_static",
                 "pagerank_query", "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
@@ -129,6 +143,12 @@ def load(path: str | None = None):
     lib.pagerank_batch_workspace_bytes.argtypes = [P(ffg_pr_job), i32, C.c_int]
     lib.pagerank_batch_workspace_bytes.restype = sz
     lib.pagerank_batch_plan.argtypes = [P(ffg_pr_job), i32, C.c_int, vp, sz, P(ffg_pr_batch), vp]
+    lib.ffg_build_batch_workspace_bytes.restype = sz
+    lib.ffg_build_batch_workspace_bytes.argtypes = [P(ffg_build_job), i32]
+    lib.ffg_build_batch_count.argtypes = [P(ffg_build_job), i32, vp, sz, P(ffg_build_batch), vp]
+    lib.ffg_build_batch_fill.argtypes = [P(ffg_build_job), i32, P(ffg_build_batch), vp]
+    lib.ffg_build_batch_rerun.argtypes = [P(ffg_build_batch), vp]
+    lib.ffg_build_batch_query.argtypes = [P(ffg_build_batch), vp, vp]
     lib.pagerank_batch_plan_tuned.argtypes = [P(ffg_pr_job), i32, C.c_int, P(ffg_pr_tuning), vp,
                                               sz, P(ffg_pr_batch), vp]
     lib.pagerank_batch_run.argtypes = [P(ffg_pr_batch), vp]
@@ -378,6 +398,58 @@ def build_graph(space: Space, fitness, nbh: int = HAMMING, fail_thr: float = 1e1
            "ffg_build_fill")
     g.nbh = nbh
     return g
+
+
+class BuildBatch:
+    """FFGs of many spaces built together: ``specs`` is a list of (Space,
+    fitness CUDA float64 tensor, nbh).  Counts all (one synchronisation),
+    allocates every Graph, fills all.  ``rerun()`` repeats the whole build
+    with launches only (capturable); ``query()`` returns the per-job status
+    array."""
+
+    def __init__(self, specs, fail_thr: float = 1e10, stream=None):
+        torch = _torch()
+        self.specs = list(specs)
+        n = len(self.specs)
+        self.jobs = (ffg_build_job * n)()
+        self._g0 = [ffg_graph() for _ in range(n)]
+        for k, (sp, fit, nbh) in enumerate(self.specs):
+            if not (fit.is_cuda and fit.dtype == torch.float64 and fit.is_contiguous()):
+                raise ValueError("fitness must be a contiguous CUDA float64 tensor")
+            self.jobs[k].space = C.pointer(sp.c)
+            self.jobs[k].fitness_raw = fit.data_ptr()
+            self.jobs[k].nbh = int(nbh)
+            self.jobs[k].fail_thr = float(fail_thr)
+            self.jobs[k].g = C.pointer(self._g0[k])
+        need = int(load().ffg_build_batch_workspace_bytes(self.jobs, n))
+        if need == 0:
+            raise FFGError(FFG_ERR_INVALID_ARG, "ffg_build_batch_workspace_bytes")
+        dev = self.specs[0][1].device
+        self.ws = workspace(need, dev)
+        self.plan = ffg_build_batch()
+        sh = _stream_handle(stream)
+        _check(int(load().ffg_build_batch_count(self.jobs, n, C.c_void_p(self.ws.data_ptr()),
+                                                need, C.byref(self.plan), C.c_void_p(sh))),
+               "ffg_build_batch_count")
+        self.graphs = []
+        for k, g0 in enumerate(self._g0):
+            g = Graph(g0.n_raw, g0.n_nodes, g0.n_edges, g0.n_minima, g0.f_opt, dev)
+            g.nbh = self.specs[k][2]
+            self.graphs.append(g)
+            self.jobs[k].g = C.pointer(g.c)
+        _check(int(load().ffg_build_batch_fill(self.jobs, n, C.byref(self.plan), C.c_void_p(sh))),
+               "ffg_build_batch_fill")
+
+    def rerun(self, stream=None):
+        _check(int(load().ffg_build_batch_rerun(C.byref(self.plan),
+                                                C.c_void_p(_stream_handle(stream)))),
+               "ffg_build_batch_rerun")
+
+    def query(self, stream=None):
+        st = np.zeros(len(self.specs), dtype=np.int32)
+        s = int(load().ffg_build_batch_query(C.byref(self.plan), C.c_void_p(st.ctypes.data),
+                                             C.c_void_p(_stream_handle(stream))))
+        return s, st
 
 
 def pagerank(g: Graph, damping: float = 0.85, tol: float = 1e-12, max_iter: int = 10000,

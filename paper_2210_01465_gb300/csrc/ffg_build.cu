@@ -23,6 +23,8 @@
 // For a warp of 32 consecutive raw points, the candidates for one (i, j)
 // are 32 shifted consecutive raw points, so the fitness and bitmap loads of
 // the enumeration are coalesced.
+#include <vector>
+
 #include "ffg_internal.cuh"
 
 namespace ffg {
@@ -96,10 +98,14 @@ __device__ __forceinline__ bool bit_of(const uint32_t *__restrict__ bm, uint32_t
     return (__ldg(bm + (r >> 5)) >> (r & 31)) & 1u;
 }
 
+// node id of valid raw point r; wprefix may be a slice of a longer scan
+// whose value at the space's first word is wbase
 __device__ __forceinline__ int32_t rank_of(const uint32_t *__restrict__ bm,
-                                           const int64_t *__restrict__ wprefix, uint32_t r) {
+                                           const int64_t *__restrict__ wprefix, int64_t wbase,
+                                           uint32_t r) {
     const uint32_t w = __ldg(bm + (r >> 5));
-    return static_cast<int32_t>(__ldg(wprefix + (r >> 5)) + __popc(w & ((1u << (r & 31)) - 1u)));
+    return static_cast<int32_t>(__ldg(wprefix + (r >> 5)) - wbase +
+                                __popc(w & ((1u << (r & 31)) - 1u)));
 }
 
 template <typename T>
@@ -146,18 +152,14 @@ __device__ __forceinline__ int64_t mask_product(const SmemSpace &s, const int64_
 }
 
 // ---------------------------------------------------------------------------
-// k_valid: validity bitmap, per-word counts, node count, f_opt
+// validity bitmap, per-word counts, node count, f_opt (raw point r, one
+// block: the space staged in s / vals)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_valid(const DevSpace sp,
-                                                    const double *__restrict__ fit,
-                                                    double fail_thr, uint32_t *__restrict__ bitmap,
-                                                    int32_t *__restrict__ wcount, BuildCtl *ctl) {
-    __shared__ SmemSpace s;
-    __shared__ int64_t vals[FFG_MAX_VALUES];
-    stage_space(sp, s, vals, true);
-    const int64_t R = sp.n_raw;
+__device__ __forceinline__ void valid_body(const SmemSpace &s, const int64_t *vals, int64_t R,
+                                           int64_t r, const double *__restrict__ fit,
+                                           double fail_thr, uint32_t *__restrict__ bitmap,
+                                           int32_t *__restrict__ wcount, BuildCtl *ctl) {
     const int64_t W = (R + 31) >> 5;
-    const int64_t r = int64_t(blockIdx.x) * kThreads + threadIdx.x;
     bool ok = false;
     unsigned long long fbits = ~0ULL;
     if (r < R) {
@@ -200,21 +202,27 @@ __global__ void __launch_bounds__(kThreads) k_valid(const DevSpace sp,
     }
 }
 
+__global__ void __launch_bounds__(kThreads) k_valid(const DevSpace sp,
+                                                    const double *__restrict__ fit,
+                                                    double fail_thr, uint32_t *__restrict__ bitmap,
+                                                    int32_t *__restrict__ wcount, BuildCtl *ctl) {
+    __shared__ SmemSpace s;
+    __shared__ int64_t vals[FFG_MAX_VALUES];
+    stage_space(sp, s, vals, true);
+    valid_body(s, vals, sp.n_raw, int64_t(blockIdx.x) * kThreads + threadIdx.x, fit, fail_thr,
+               bitmap, wcount, ctl);
+}
+
 // ---------------------------------------------------------------------------
-// k_count: out/in degree of every node
+// out/in degree of every node
 // ---------------------------------------------------------------------------
 template <int NBH>
-__global__ void __launch_bounds__(kThreads) k_count(const DevSpace sp,
-                                                    const double *__restrict__ fit,
-                                                    double fail_thr,
-                                                    const uint32_t *__restrict__ bitmap,
-                                                    const int64_t *__restrict__ wprefix,
-                                                    int32_t *__restrict__ outdeg,
-                                                    int32_t *__restrict__ indeg, BuildCtl *ctl) {
-    __shared__ SmemSpace s;
-    stage_space(sp, s, nullptr, false);
-    const int64_t R = sp.n_raw;
-    const int64_t r64 = int64_t(blockIdx.x) * kThreads + threadIdx.x;
+__device__ __forceinline__ void count_body(const SmemSpace &s, int64_t R, int64_t r64,
+                                           const double *__restrict__ fit, double fail_thr,
+                                           const uint32_t *__restrict__ bitmap,
+                                           const int64_t *__restrict__ wprefix, int64_t wbase,
+                                           int32_t *__restrict__ outdeg,
+                                           int32_t *__restrict__ indeg, BuildCtl *ctl) {
     unsigned long long n_out = 0, n_in = 0, n_min = 0;
     if (r64 < R && bit_of(bitmap, static_cast<uint32_t>(r64))) {
         const uint32_t r = static_cast<uint32_t>(r64);
@@ -239,7 +247,7 @@ __global__ void __launch_bounds__(kThreads) k_count(const DevSpace sp,
                 in += kk > k0;
             }
         }
-        const int32_t node = rank_of(bitmap, wprefix, r);
+        const int32_t node = rank_of(bitmap, wprefix, wbase, r);
         outdeg[node] = out;
         indeg[node] = in;
         n_out = out;
@@ -256,24 +264,34 @@ __global__ void __launch_bounds__(kThreads) k_count(const DevSpace sp,
     }
 }
 
+template <int NBH>
+__global__ void __launch_bounds__(kThreads) k_count(const DevSpace sp,
+                                                    const double *__restrict__ fit,
+                                                    double fail_thr,
+                                                    const uint32_t *__restrict__ bitmap,
+                                                    const int64_t *__restrict__ wprefix,
+                                                    int32_t *__restrict__ outdeg,
+                                                    int32_t *__restrict__ indeg, BuildCtl *ctl) {
+    __shared__ SmemSpace s;
+    stage_space(sp, s, nullptr, false);
+    count_body<NBH>(s, sp.n_raw, int64_t(blockIdx.x) * kThreads + threadIdx.x, fit, fail_thr,
+                    bitmap, wprefix, 0, outdeg, indeg, ctl);
+}
+
 // ---------------------------------------------------------------------------
-// k_emit: canonical CSR rows, outdeg, node_raw, is_min
+// canonical CSR rows, outdeg, node_raw, is_min
 // ---------------------------------------------------------------------------
 template <int NBH>
-__global__ void __launch_bounds__(kThreads) k_emit(
-    const DevSpace sp, const double *__restrict__ fit, double fail_thr,
-    const uint32_t *__restrict__ bitmap, const int64_t *__restrict__ wprefix,
+__device__ __forceinline__ void emit_body(
+    const SmemSpace &s, int64_t R, int64_t r64, const double *__restrict__ fit, double fail_thr,
+    const uint32_t *__restrict__ bitmap, const int64_t *__restrict__ wprefix, int64_t wbase,
     const int64_t *__restrict__ out_ptr, const int64_t *__restrict__ in_ptr,
     int32_t *__restrict__ out_idx, int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg,
     int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min) {
-    __shared__ SmemSpace s;
-    stage_space(sp, s, nullptr, false);
-    const int64_t R = sp.n_raw;
-    const int64_t r64 = int64_t(blockIdx.x) * kThreads + threadIdx.x;
     if (r64 >= R || !bit_of(bitmap, static_cast<uint32_t>(r64))) return;
     const uint32_t r = static_cast<uint32_t>(r64);
     const double k0 = fit_key(__ldg(fit + r), fail_thr);
-    const int32_t node = rank_of(bitmap, wprefix, r);
+    const int32_t node = rank_of(bitmap, wprefix, wbase, r);
     const int64_t o0 = out_ptr[node];
     int64_t o = o0, q = in_ptr[node];
 
@@ -293,8 +311,8 @@ __global__ void __launch_bounds__(kThreads) k_emit(
     auto visit = [&](uint32_t rr) {
         if (!bit_of(bitmap, rr)) return;
         const double kk = fit_key(__ldg(fit + rr), fail_thr);
-        if (kk < k0) out_idx[o++] = rank_of(bitmap, wprefix, rr);
-        else if (kk > k0) in_idx[q++] = rank_of(bitmap, wprefix, rr);
+        if (kk < k0) out_idx[o++] = rank_of(bitmap, wprefix, wbase, rr);
+        else if (kk > k0) in_idx[q++] = rank_of(bitmap, wprefix, wbase, rr);
     };
     // negative offsets: slowest parameter first, values ascending
 #pragma unroll
@@ -319,6 +337,19 @@ __global__ void __launch_bounds__(kThreads) k_emit(
     outdeg[node] = od;
     node_raw[node] = r;
     is_min[node] = (k0 < fail_thr && od == 0) ? 1 : 0;
+}
+
+template <int NBH>
+__global__ void __launch_bounds__(kThreads) k_emit(
+    const DevSpace sp, const double *__restrict__ fit, double fail_thr,
+    const uint32_t *__restrict__ bitmap, const int64_t *__restrict__ wprefix,
+    const int64_t *__restrict__ out_ptr, const int64_t *__restrict__ in_ptr,
+    int32_t *__restrict__ out_idx, int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg,
+    int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min) {
+    __shared__ SmemSpace s;
+    stage_space(sp, s, nullptr, false);
+    emit_body<NBH>(s, sp.n_raw, int64_t(blockIdx.x) * kThreads + threadIdx.x, fit, fail_thr,
+                   bitmap, wprefix, 0, out_ptr, in_ptr, out_idx, in_idx, outdeg, node_raw, is_min);
 }
 
 ffg_status check_common(const ffg_space *space, const double *fitness_raw, ffg_nbh nbh,
@@ -422,4 +453,417 @@ extern "C" ffg_status ffg_build_fill(const ffg_space *space, const double *fitne
             g->in_idx, g->outdeg, g->node_raw, g->is_min);
     count_launch();
     return check_launch("k_emit");
+}
+
+// ---------------------------------------------------------------------------
+// batched construction: every job's count phase in four launches and one
+// read-back, every fill in four launches.  Blocks map to jobs through a
+// prefix of per-job block counts; per-job arrays are slices of arrays over
+// all jobs, so each scan runs once over all jobs and a job's offsets are its
+// slice minus the slice's first value.
+// ---------------------------------------------------------------------------
+namespace ffg {
+namespace {
+
+struct BJob {
+    const DevSpace *sp;
+    const double *fit;
+    double fail_thr;
+    int32_t nbh, pad;
+    int64_t n_raw;
+    int64_t woff, roff;  // first word / raw slot of the job in the arrays over all jobs
+    // graph arrays (recorded by the fill) and the sizes the count reported
+    int64_t *out_ptr, *in_ptr;
+    int32_t *out_idx, *in_idx, *outdeg;
+    int64_t *node_raw;
+    uint8_t *is_min;
+    int64_t n_nodes, n_edges;
+};
+
+struct BatchBuildWs {
+    DevSpace *dsp;
+    BJob *jobs;
+    int64_t *blk0;    // n + 1: first block of every job
+    int64_t *row0;    // n + 1: first row-pointer slot of every job (N + 1 per job)
+    BuildCtl *ctl;    // n
+    int32_t *status;  // n
+    uint32_t *bitmap;
+    int32_t *wcount;
+    int64_t *wpre;
+    int32_t *odeg, *ideg;
+    int64_t *opre, *ipre;
+    int64_t *scratch;
+    size_t bytes;
+};
+
+BatchBuildWs carve_bb(void *base, int n, int64_t total_raw, int64_t total_words) {
+    Carver c(base);
+    BatchBuildWs w;
+    w.dsp = c.take<DevSpace>(n);
+    w.jobs = c.take<BJob>(n);
+    w.blk0 = c.take<int64_t>(size_t(n) + 1);
+    w.row0 = c.take<int64_t>(size_t(n) + 1);
+    w.ctl = c.take<BuildCtl>(n);
+    w.status = c.take<int32_t>(n);
+    w.bitmap = c.take<uint32_t>(total_words);
+    w.wcount = c.take<int32_t>(total_words);
+    w.wpre = c.take<int64_t>(total_words + 1);
+    w.odeg = c.take<int32_t>(total_raw);
+    w.ideg = c.take<int32_t>(total_raw);
+    w.opre = c.take<int64_t>(total_raw + 1);
+    w.ipre = c.take<int64_t>(total_raw + 1);
+    w.scratch = c.take<int64_t>(scan_scratch_elems(total_raw > total_words ? total_raw
+                                                                           : total_words));
+    w.bytes = c.off;
+    return w;
+}
+
+// the job of a block (thread 0 searches, the block reads it from shared)
+__device__ __forceinline__ int job_of_block(const int64_t *__restrict__ blk0, int n) {
+    __shared__ int s_job;
+    if (threadIdx.x == 0) {
+        const int64_t b = blockIdx.x;
+        int lo = 0, hi = n - 1;  // last job starting at or before b
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (blk0[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    return s_job;
+}
+
+__global__ void k_bctl_init(BuildCtl *ctl, int32_t *status, int n) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        ctl[s].fopt_bits = ~0ULL;
+        ctl[s].n_nodes = ctl[s].n_out = ctl[s].n_in = ctl[s].n_minima = 0;
+        status[s] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_valid_batch(const BJob *__restrict__ jobs,
+                                                          const int64_t *__restrict__ blk0, int n,
+                                                          uint32_t *bitmap, int32_t *wcount,
+                                                          BuildCtl *ctl) {
+    __shared__ SmemSpace s;
+    __shared__ int64_t vals[FFG_MAX_VALUES];
+    const int j = job_of_block(blk0, n);
+    const BJob &J = jobs[j];
+    stage_space(*J.sp, s, vals, true);
+    const int64_t r = (int64_t(blockIdx.x) - blk0[j]) * kThreads + threadIdx.x;
+    valid_body(s, vals, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff, wcount + J.woff, ctl + j);
+}
+
+__global__ void __launch_bounds__(kThreads) k_count_batch(const BJob *__restrict__ jobs,
+                                                          const int64_t *__restrict__ blk0, int n,
+                                                          const uint32_t *__restrict__ bitmap,
+                                                          const int64_t *__restrict__ wpre,
+                                                          int32_t *odeg, int32_t *ideg,
+                                                          BuildCtl *ctl) {
+    __shared__ SmemSpace s;
+    const int j = job_of_block(blk0, n);
+    const BJob &J = jobs[j];
+    stage_space(*J.sp, s, nullptr, false);
+    const int64_t r = (int64_t(blockIdx.x) - blk0[j]) * kThreads + threadIdx.x;
+    const int64_t wb = wpre[J.woff];
+    if (J.nbh == FFG_HAMMING)
+        count_body<FFG_HAMMING>(s, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff, wpre + J.woff,
+                                wb, odeg + J.roff, ideg + J.roff, ctl + j);
+    else
+        count_body<FFG_ADJACENT>(s, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff,
+                                 wpre + J.woff, wb, odeg + J.roff, ideg + J.roff, ctl + j);
+}
+
+// the device counts of job j equal the sizes its graph arrays were made for
+__device__ __forceinline__ bool sizes_match(const BJob &J, const BuildCtl &c) {
+    return static_cast<int64_t>(c.n_nodes) == J.n_nodes &&
+           static_cast<int64_t>(c.n_out) == J.n_edges && c.n_in == c.n_out;
+}
+
+// out_ptr / in_ptr of every job: its slice of the scans, rebased
+__global__ void k_rebase(const BJob *__restrict__ jobs, const int64_t *__restrict__ row0, int n,
+                         int64_t total, const int64_t *__restrict__ opre,
+                         const int64_t *__restrict__ ipre, const BuildCtl *__restrict__ ctl,
+                         int32_t *status) {
+    for (int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < total;
+         x += int64_t(gridDim.x) * blockDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row0[mid] <= x) lo = mid;
+            else hi = mid - 1;
+        }
+        const BJob &J = jobs[lo];
+        const int64_t i = x - row0[lo];
+        if (!sizes_match(J, ctl[lo])) {
+            if (i == 0) status[lo] = FFG_ERR_INVALID_ARG;
+            continue;
+        }
+        J.out_ptr[i] = opre[J.roff + i] - opre[J.roff];
+        J.in_ptr[i] = ipre[J.roff + i] - ipre[J.roff];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_emit_batch(const BJob *__restrict__ jobs,
+                                                         const int64_t *__restrict__ blk0, int n,
+                                                         const uint32_t *__restrict__ bitmap,
+                                                         const int64_t *__restrict__ wpre,
+                                                         const BuildCtl *__restrict__ ctl) {
+    __shared__ SmemSpace s;
+    const int j = job_of_block(blk0, n);
+    const BJob &J = jobs[j];
+    if (!sizes_match(J, ctl[j])) return;  // uniform over the block
+    stage_space(*J.sp, s, nullptr, false);
+    const int64_t r = (int64_t(blockIdx.x) - blk0[j]) * kThreads + threadIdx.x;
+    const int64_t wb = wpre[J.woff];
+    if (J.nbh == FFG_HAMMING)
+        emit_body<FFG_HAMMING>(s, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff, wpre + J.woff,
+                               wb, J.out_ptr, J.in_ptr, J.out_idx, J.in_idx, J.outdeg,
+                               J.node_raw, J.is_min);
+    else
+        emit_body<FFG_ADJACENT>(s, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff,
+                                wpre + J.woff, wb, J.out_ptr, J.in_ptr, J.out_idx, J.in_idx,
+                                J.outdeg, J.node_raw, J.is_min);
+}
+
+struct BatchSizes {
+    int64_t total_raw = 0, total_words = 0, total_blocks = 0;
+};
+
+ffg_status batch_sizes(const ffg_build_job *jobs, int n, std::vector<DevSpace> *dsp,
+                       BatchSizes *z) {
+    if (!jobs || n < 1) return set_error("jobs NULL or n_jobs < 1"), FFG_ERR_INVALID_ARG;
+    if (dsp) dsp->resize(n);
+    DevSpace d;
+    for (int j = 0; j < n; ++j) {
+        const ffg_build_job &b = jobs[j];
+        FFG_TRY(make_dev_space(b.space, dsp ? &(*dsp)[j] : &d));
+        const DevSpace &x = dsp ? (*dsp)[j] : d;
+        if (b.nbh != FFG_HAMMING && b.nbh != FFG_ADJACENT)
+            return set_error("job %d: unknown neighbourhood %d", j, (int)b.nbh),
+                   FFG_ERR_INVALID_ARG;
+        if (!b.fitness_raw || !b.g || b.fail_thr != b.fail_thr)
+            return set_error("job %d: fitness or graph NULL, or fail_thr NaN", j),
+                   FFG_ERR_INVALID_ARG;
+        z->total_raw += x.n_raw;
+        z->total_words += (x.n_raw + 31) / 32;
+        z->total_blocks += (x.n_raw + kThreads - 1) / kThreads;
+    }
+    if (z->total_blocks >= (int64_t(1) << 31))
+        return set_error("too many raw points in one batch"), FFG_ERR_OVERFLOW;
+    return FFG_OK;
+}
+
+unsigned grid_of(int64_t items, int threads) {
+    const int64_t g = (items + threads - 1) / threads;
+    return static_cast<unsigned>(g < 1 ? 1 : (g > 65535 * 32 ? 65535 * 32 : g));
+}
+
+// the count phase on the device (tables already in the workspace)
+ffg_status launch_count_phase(const BatchBuildWs &w, int n, int64_t total_raw,
+                              int64_t total_words, int64_t total_blocks, cudaStream_t stream) {
+    k_bctl_init<<<grid_of(n, 128), 128, 0, stream>>>(w.ctl, w.status, n);
+    count_launch();
+    FFG_TRY(check_launch("k_bctl_init"));
+    FFG_TRY(check_cuda(cudaMemsetAsync(w.odeg, 0, sizeof(int32_t) * total_raw, stream), "memset"));
+    FFG_TRY(check_cuda(cudaMemsetAsync(w.ideg, 0, sizeof(int32_t) * total_raw, stream), "memset"));
+    k_valid_batch<<<static_cast<unsigned>(total_blocks), kThreads, 0, stream>>>(
+        w.jobs, w.blk0, n, w.bitmap, w.wcount, w.ctl);
+    count_launch();
+    FFG_TRY(check_launch("k_valid_batch"));
+    FFG_TRY(scan_exclusive(w.wcount, w.wpre, total_words, w.scratch, stream));
+    k_count_batch<<<static_cast<unsigned>(total_blocks), kThreads, 0, stream>>>(
+        w.jobs, w.blk0, n, w.bitmap, w.wpre, w.odeg, w.ideg, w.ctl);
+    count_launch();
+    return check_launch("k_count_batch");
+}
+
+// the fill phase on the device (graph pointers and sizes already recorded)
+ffg_status launch_fill_phase(const BatchBuildWs &w, int n, int64_t total_raw, int64_t total_rows,
+                             int64_t total_blocks, cudaStream_t stream) {
+    FFG_TRY(scan_exclusive(w.odeg, w.opre, total_raw, w.scratch, stream));
+    FFG_TRY(scan_exclusive(w.ideg, w.ipre, total_raw, w.scratch, stream));
+    k_rebase<<<grid_of(total_rows, 256), 256, 0, stream>>>(w.jobs, w.row0, n, total_rows, w.opre,
+                                                           w.ipre, w.ctl, w.status);
+    count_launch();
+    FFG_TRY(check_launch("k_rebase"));
+    k_emit_batch<<<static_cast<unsigned>(total_blocks), kThreads, 0, stream>>>(
+        w.jobs, w.blk0, n, w.bitmap, w.wpre, w.ctl);
+    count_launch();
+    return check_launch("k_emit_batch");
+}
+
+BatchBuildWs ws_of(const ffg_build_batch *plan) {
+    BatchBuildWs w{};
+    w.dsp = static_cast<DevSpace *>(plan->tables[0]);
+    w.jobs = static_cast<BJob *>(plan->tables[1]);
+    w.blk0 = static_cast<int64_t *>(plan->tables[2]);
+    w.row0 = static_cast<int64_t *>(plan->tables[3]);
+    w.ctl = static_cast<BuildCtl *>(plan->tables[4]);
+    w.status = static_cast<int32_t *>(plan->tables[5]);
+    w.bitmap = static_cast<uint32_t *>(plan->tables[6]);
+    w.wcount = static_cast<int32_t *>(plan->tables[7]);
+    w.wpre = static_cast<int64_t *>(plan->tables[8]);
+    w.odeg = static_cast<int32_t *>(plan->tables[9]);
+    w.ideg = static_cast<int32_t *>(plan->tables[10]);
+    w.opre = static_cast<int64_t *>(plan->tables[11]);
+    w.ipre = static_cast<int64_t *>(plan->tables[12]);
+    w.scratch = static_cast<int64_t *>(plan->tables[13]);
+    return w;
+}
+
+}  // namespace
+}  // namespace ffg
+
+extern "C" size_t ffg_build_batch_workspace_bytes(const ffg_build_job *jobs, int32_t n_jobs) {
+    clear_error();
+    BatchSizes z;
+    if (batch_sizes(jobs, n_jobs, nullptr, &z) != FFG_OK) return 0;
+    return carve_bb(nullptr, n_jobs, z.total_raw, z.total_words).bytes;
+}
+
+extern "C" ffg_status ffg_build_batch_count(const ffg_build_job *jobs, int32_t n_jobs,
+                                            void *workspace, size_t ws_bytes,
+                                            ffg_build_batch *plan, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    std::vector<DevSpace> dsp;
+    BatchSizes z;
+    FFG_TRY(batch_sizes(jobs, n_jobs, &dsp, &z));
+    if (!plan || !workspace || !aligned256(workspace))
+        return set_error("plan NULL or workspace NULL / not 256-byte aligned"),
+               FFG_ERR_INVALID_ARG;
+    BatchBuildWs w = carve_bb(workspace, n_jobs, z.total_raw, z.total_words);
+    if (ws_bytes < w.bytes)
+        return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
+    std::vector<BJob> bj(n_jobs);
+    std::vector<int64_t> blk0(n_jobs + 1, 0);
+    int64_t woff = 0, roff = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        BJob &b = bj[j];
+        b = BJob{};
+        b.sp = w.dsp + j;
+        b.fit = jobs[j].fitness_raw;
+        b.fail_thr = jobs[j].fail_thr;
+        b.nbh = jobs[j].nbh;
+        b.n_raw = dsp[j].n_raw;
+        b.woff = woff;
+        b.roff = roff;
+        b.n_nodes = b.n_edges = -1;  // no arrays yet: the fill kernels skip the job
+        woff += (dsp[j].n_raw + 31) / 32;
+        roff += dsp[j].n_raw;
+        blk0[j + 1] = blk0[j] + (dsp[j].n_raw + kThreads - 1) / kThreads;
+    }
+    FFG_TRY(check_cuda(cudaMemcpyAsync(w.dsp, dsp.data(), sizeof(DevSpace) * n_jobs,
+                                       cudaMemcpyHostToDevice, stream), "upload spaces"));
+    FFG_TRY(check_cuda(cudaMemcpyAsync(w.jobs, bj.data(), sizeof(BJob) * n_jobs,
+                                       cudaMemcpyHostToDevice, stream), "upload jobs"));
+    FFG_TRY(check_cuda(cudaMemcpyAsync(w.blk0, blk0.data(), sizeof(int64_t) * (n_jobs + 1),
+                                       cudaMemcpyHostToDevice, stream), "upload jobs"));
+    FFG_TRY(launch_count_phase(w, n_jobs, z.total_raw, z.total_words, z.total_blocks, stream));
+    std::vector<BuildCtl> h(n_jobs);
+    FFG_TRY(check_cuda(cudaMemcpyAsync(h.data(), w.ctl, sizeof(BuildCtl) * n_jobs,
+                                       cudaMemcpyDeviceToHost, stream), "read counts"));
+    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync counts"));
+    bool empty = false;
+    for (int j = 0; j < n_jobs; ++j) {
+        if (h[j].n_out != h[j].n_in) {
+            set_error("internal: job %d out-degree sum != in-degree sum", j);
+            return FFG_ERR_CUDA;
+        }
+        ffg_graph *g = jobs[j].g;
+        g->n_raw = dsp[j].n_raw;
+        g->n_nodes = static_cast<int64_t>(h[j].n_nodes);
+        g->n_edges = static_cast<int64_t>(h[j].n_out);
+        g->n_minima = static_cast<int64_t>(h[j].n_minima);
+        g->f_opt = h[j].fopt_bits == ~0ULL ? __builtin_inf() : from_ordered_bits(h[j].fopt_bits);
+        empty = empty || g->n_nodes == 0;
+    }
+    plan->n_jobs = n_jobs;
+    plan->reserved = 0;
+    plan->total_raw = z.total_raw;
+    plan->total_words = z.total_words;
+    plan->total_blocks = z.total_blocks;
+    plan->total_rows = 0;
+    void *t[] = {w.dsp, w.jobs, w.blk0, w.row0, w.ctl, w.status, w.bitmap, w.wcount,
+                 w.wpre, w.odeg, w.ideg, w.opre, w.ipre, w.scratch};
+    for (int k = 0; k < 14; ++k) plan->tables[k] = t[k];
+    plan->tables[14] = plan->tables[15] = nullptr;
+    if (empty) return set_error("a job has no valid configuration"), FFG_ERR_EMPTY;
+    return FFG_OK;
+}
+
+extern "C" ffg_status ffg_build_batch_fill(const ffg_build_job *jobs, int32_t n_jobs,
+                                           ffg_build_batch *plan, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!jobs || !plan || n_jobs != plan->n_jobs || !plan->tables[1])
+        return set_error("jobs do not match the plan of ffg_build_batch_count"),
+               FFG_ERR_INVALID_ARG;
+    BatchBuildWs w = ws_of(plan);
+    std::vector<BJob> bj(n_jobs);
+    FFG_TRY(check_cuda(cudaMemcpyAsync(bj.data(), w.jobs, sizeof(BJob) * n_jobs,
+                                       cudaMemcpyDeviceToHost, stream), "read jobs"));
+    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync jobs"));
+    std::vector<int64_t> row0(n_jobs + 1, 0);
+    for (int j = 0; j < n_jobs; ++j) {
+        const ffg_graph *g = jobs[j].g;
+        if (!g || g->n_raw != bj[j].n_raw || g->n_nodes <= 0 || g->n_nodes > g->n_raw ||
+            g->n_edges < 0)
+            return set_error("job %d: graph sizes do not come from ffg_build_batch_count", j),
+                   FFG_ERR_INVALID_ARG;
+        if (!g->out_ptr || !g->in_ptr || !g->outdeg || !g->node_raw || !g->is_min ||
+            (g->n_edges > 0 && (!g->out_idx || !g->in_idx)))
+            return set_error("job %d: a graph buffer is NULL", j), FFG_ERR_INVALID_ARG;
+        BJob &b = bj[j];
+        b.out_ptr = g->out_ptr;
+        b.in_ptr = g->in_ptr;
+        b.out_idx = g->out_idx;
+        b.in_idx = g->in_idx;
+        b.outdeg = g->outdeg;
+        b.node_raw = g->node_raw;
+        b.is_min = g->is_min;
+        b.n_nodes = g->n_nodes;
+        b.n_edges = g->n_edges;
+        row0[j + 1] = row0[j] + g->n_nodes + 1;
+    }
+    FFG_TRY(check_cuda(cudaMemcpyAsync(w.jobs, bj.data(), sizeof(BJob) * n_jobs,
+                                       cudaMemcpyHostToDevice, stream), "upload jobs"));
+    FFG_TRY(check_cuda(cudaMemcpyAsync(w.row0, row0.data(), sizeof(int64_t) * (n_jobs + 1),
+                                       cudaMemcpyHostToDevice, stream), "upload rows"));
+    plan->total_rows = row0[n_jobs];
+    FFG_TRY(launch_fill_phase(w, n_jobs, plan->total_raw, plan->total_rows, plan->total_blocks,
+                              stream));
+    // the host vectors die here: the copies above must have been read
+    return check_cuda(cudaStreamSynchronize(stream), "sync fill upload");
+}
+
+extern "C" ffg_status ffg_build_batch_rerun(const ffg_build_batch *plan, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!plan || plan->n_jobs < 1 || !plan->tables[1] || plan->total_rows <= 0)
+        return set_error("plan has not been filled"), FFG_ERR_INVALID_ARG;
+    const BatchBuildWs w = ws_of(plan);
+    FFG_TRY(launch_count_phase(w, plan->n_jobs, plan->total_raw, plan->total_words,
+                               plan->total_blocks, stream));
+    return launch_fill_phase(w, plan->n_jobs, plan->total_raw, plan->total_rows,
+                             plan->total_blocks, stream);
+}
+
+extern "C" ffg_status ffg_build_batch_query(const ffg_build_batch *plan, int32_t *status_out,
+                                            void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!plan || plan->n_jobs < 1 || !plan->tables[5] || !status_out)
+        return set_error("plan or status_out NULL"), FFG_ERR_INVALID_ARG;
+    FFG_TRY(check_cuda(cudaMemcpyAsync(status_out, plan->tables[5], sizeof(int32_t) * plan->n_jobs,
+                                       cudaMemcpyDeviceToHost, stream), "read status"));
+    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync status"));
+    ffg_status worst = FFG_OK;
+    for (int j = 0; j < plan->n_jobs; ++j)
+        if (status_out[j] != FFG_OK) worst = static_cast<ffg_status>(status_out[j]);
+    if (worst != FFG_OK) set_error("a job's counts differ from the sizes of its arrays");
+    return worst;
 }

@@ -125,3 +125,33 @@ def test_batch_tuning_validated_on_host(lib):
         assert ffg.pagerank_batch_plan_tuned(jobs, ffg.F32, tuning, 256, 1 << 20, plan) == \
             ffg.FFG_ERR_INVALID_ARG
         assert "tuning" in ffg.ffg_last_error()
+
+
+def test_batched_build_validated_on_host(lib):
+    sp = ffg.Space.from_spec(fi.single_small())
+    g = ffg.ffg_graph()
+    jobs = (ffg.ffg_build_job * 2)()
+    for j in jobs:
+        j.space = C.pointer(sp.c)
+        j.fitness_raw = 256
+        j.nbh = ffg.HAMMING
+        j.fail_thr = 1e10
+        j.g = C.pointer(g)
+    assert lib.ffg_build_batch_workspace_bytes(jobs, 2) > 2 * ffg.ffg_workspace_bytes(sp, 0) // 2
+    assert lib.ffg_build_batch_workspace_bytes(jobs, 0) == 0
+    plan = ffg.ffg_build_batch()
+    jobs[1].nbh = 7
+    assert lib.ffg_build_batch_workspace_bytes(jobs, 2) == 0
+    assert lib.ffg_build_batch_count(jobs, 2, C.c_void_p(256), 1 << 30, C.byref(plan),
+                                     None) == ffg.FFG_ERR_INVALID_ARG
+    jobs[1].nbh = ffg.HAMMING
+    jobs[1].fitness_raw = None
+    assert lib.ffg_build_batch_count(jobs, 2, C.c_void_p(256), 1 << 30, C.byref(plan),
+                                     None) == ffg.FFG_ERR_INVALID_ARG
+    jobs[1].fitness_raw = 256
+    assert lib.ffg_build_batch_count(jobs, 2, C.c_void_p(258), 1 << 30, C.byref(plan),
+                                     None) == ffg.FFG_ERR_INVALID_ARG
+    assert lib.ffg_build_batch_count(jobs, 2, C.c_void_p(256), 16, C.byref(plan),
+                                     None) == ffg.FFG_ERR_NO_MEMORY
+    assert lib.ffg_build_batch_rerun(C.byref(ffg.ffg_build_batch()), None) == \
+        ffg.FFG_ERR_INVALID_ARG

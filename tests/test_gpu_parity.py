@@ -414,3 +414,69 @@ def test_batch_tuning_changes_schedule_not_results():
             np.testing.assert_array_equal(it, first[0])
             for x, x0 in zip(xs, first[1]):
                 np.testing.assert_array_equal(x, x0)
+
+
+def test_batched_build_matches_per_space_builds():
+    """All FFGs of many spaces at once (both neighbourhoods, ragged sizes,
+    failures and ties): bit-exact against the oracle; a re-run from the
+    workspace, plain and replayed from a CUDA graph, gives the same arrays."""
+    cases = [(fi.single_small(), 1, 0.03, None), (fi.pnpoly_space(), 2, 0.7, None),
+             (fi.conv_mi50_space(), 3, 0.3, 0.25), (fi.gemm_space(), 4, 0.7, None)]
+    cases += [(sp, 10 + k, (0.03, 0.3, 0.7)[k % 3], 0.5 if k % 4 == 0 else None)
+              for k, sp in enumerate(fi.tiny_spaces(12, seed0=14000, max_raw=4000))]
+    specs, fits, refs = [], [], []
+    for k, (spec, seed, fail, quantum) in enumerate(cases):
+        f = fi.runtimes(spec, seed, fail_frac=fail, quantum=quantum)
+        nbh = "hamming" if k % 2 == 0 else "adjacent"
+        og = oracle.build(spec, f, NBH[nbh][1])
+        if og.n_nodes == 0:
+            continue
+        fd = torch.from_numpy(f).cuda()
+        fits.append(fd)
+        specs.append((ffg.Space.from_spec(spec), fd, NBH[nbh][0]))
+        refs.append(og)
+    bb = ffg.BuildBatch(specs)
+    for g, og in zip(bb.graphs, refs):
+        assert_same_graph(g, og)
+    # re-run: clobber the arrays first, the re-run must restore them
+    for g in bb.graphs:
+        g.out_idx.fill_(-1)
+        g.in_ptr.fill_(-1)
+    bb.rerun()
+    st, sts = bb.query()
+    assert st == ffg.FFG_OK and (sts == 0).all()
+    for g, og in zip(bb.graphs, refs):
+        assert_same_graph(g, og)
+    cg = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(cg, stream=side):
+            bb.rerun(stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    for g in bb.graphs:
+        g.out_idx.fill_(-1)
+    cg.replay()
+    torch.cuda.synchronize()
+    for g, og in zip(bb.graphs, refs):
+        assert_same_graph(g, og)
+
+
+def test_batched_build_rerun_refuses_changed_sizes():
+    """A re-run whose counts no longer match the arrays (fitness changed)
+    leaves that graph untouched and reports it; the others are rebuilt."""
+    a, b = fi.single_small(), fi.conv_mi50_space()
+    fa = torch.from_numpy(fi.runtimes(a, 1)).cuda()
+    fb = torch.from_numpy(fi.runtimes(b, 2)).cuda()
+    bb = ffg.BuildBatch([(ffg.Space.from_spec(a), fa, ffg.HAMMING),
+                         (ffg.Space.from_spec(b), fb, ffg.HAMMING)])
+    before = [_np(t).copy() for t in (bb.graphs[0].out_ptr, bb.graphs[0].out_idx)]
+    fa.copy_(torch.from_numpy(fi.runtimes(a, 99)))   # other edges, other edge count
+    og_b = oracle.build(b, fi.runtimes(b, 2), oracle.HAMMING)
+    bb.graphs[1].out_idx.fill_(-1)
+    bb.rerun()
+    st, sts = bb.query()
+    assert st == ffg.FFG_ERR_INVALID_ARG and sts[0] == ffg.FFG_ERR_INVALID_ARG and sts[1] == 0
+    np.testing.assert_array_equal(_np(bb.graphs[0].out_ptr), before[0])
+    np.testing.assert_array_equal(_np(bb.graphs[0].out_idx), before[1])
+    assert_same_graph(bb.graphs[1], og_b)
