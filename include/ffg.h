@@ -276,12 +276,16 @@ typedef struct {
 size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec);
 
 /* Host-side planning: validates the jobs, gives every job a group of blocks
- * of one cooperative grid (large jobs several blocks, small ones one) and
- * an order: per-block lists (one-block jobs longest first onto the least
- * loaded block) or a claim order (the ranks of multi-block jobs first, then
- * the one-block jobs longest first; a block takes the next unclaimed one
- * whenever it is free).  Carves the workspace and uploads the tables.
- * Synchronises `stream`. */
+ * of one cooperative grid (large jobs several blocks, up to the whole grid;
+ * small ones one) and an order:
+ * - per-block lists: a job's ranks go to the least loaded blocks; every
+ *   block runs its multi-block ranks in one global order (largest job
+ *   first), then its one-block jobs (longest first onto the least loaded
+ *   block), so a group only waits for blocks busy with an earlier job;
+ * - claim order: the ranks of multi-block jobs (at most one per block)
+ *   first, then the one-block jobs longest first; a block takes the next
+ *   unclaimed item whenever it is free.
+ * Carves the workspace and uploads the tables.  Synchronises `stream`. */
 ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec,
                                void *workspace, size_t ws_bytes, ffg_pr_batch *plan,
                                void *stream);
