@@ -493,6 +493,71 @@ __device__ __forceinline__ T gather_step(const uint4 *q, const T *wrow, uint32_t
     return v[0];
 }
 
+// Per-lane accumulator of a row's in-sum.  FP32: pairwise partial sums
+// added in order.  FP64: the sum is exact -- every gathered w is added as a
+// 128-bit fixed-point integer (quantum 2^-120; w < 2 and sums < 2^7 fit, and
+// a w below 2^-120 would lose at most one quantum) with integer instructions
+// only, and rounded to double once per row.  A warp-wide FP64 add occupies
+// the FP64 units of an SM for 16 cycles on this part, so the integer form is
+// also the faster one.
+template <typename T>
+struct Accum;
+
+template <>
+struct Accum<float> {
+    float s = 0.f;
+    template <int N>
+    __device__ __forceinline__ void step(const uint4 *q, const float *wrow, uint32_t bit) {
+        s += gather_step<float, N>(q, wrow, bit);
+    }
+    __device__ __forceinline__ float value() const { return s; }
+};
+
+template <>
+struct Accum<double> {
+    unsigned long long lo = 0, hi = 0;  // sum / 2^-120, 128 bits
+    __device__ __forceinline__ void add(double w) {  // w >= 0
+        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(w));
+        const int e = static_cast<int>(b >> 52);
+        const unsigned long long m =
+            (b & 0xfffffffffffffULL) | (e ? 0x10000000000000ULL : 0ULL);
+        const int sh = e - 955;  // w / 2^-120 = m * 2^sh, sh < 75
+        unsigned long long l, h;
+        if (sh >= 64) {
+            l = 0;
+            h = m << (sh - 64);
+        } else if (sh > 0) {
+            l = m << sh;
+            h = m >> (64 - sh);
+        } else if (sh > -64) {
+            l = m >> -sh;
+            h = 0;
+        } else {
+            l = 0;
+            h = 0;
+        }
+        lo += l;
+        hi += h + (lo < l ? 1ULL : 0ULL);
+    }
+    template <int N>
+    __device__ __forceinline__ void step(const uint4 *q, const double *wrow, uint32_t bit) {
+        double v[N];
+#pragma unroll
+        for (int j = 0; j < N / 2; ++j) {
+            const uint4 d = q[j];
+            v[2 * j] = (d.y & bit) ? wrow[static_cast<int32_t>(d.x)] : 0.0;
+            v[2 * j + 1] = (d.w & bit) ? wrow[static_cast<int32_t>(d.z)] : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) add(v[j]);
+    }
+    __device__ __forceinline__ double value() const {
+        // hi * 2^-56 + lo * 2^-120 (scalings by powers of two are exact)
+        return fma(__ull2double_rn(lo), 7.52316384526264005e-37,
+                   __ull2double_rn(hi) * 1.38777878078144568e-17);
+    }
+};
+
 // Sum over the in-edges of this lane's row (wrow = w + row): the tile's
 // descriptors stream in segments of kSegD; the segment after the current one
 // (or the first segment of the next tile) is copied while the current one is
@@ -504,7 +569,7 @@ __device__ __forceinline__ bool tile_sum(const uint2 *__restrict__ desc, const T
     const int cnt = cur.cnt;
     const int nseg = (cnt + kSegD - 1) / kSegD;
     const bool next_any = has_next && nxt.cnt > 0;
-    T s = T(0);
+    Accum<T> acc;
     for (int sg = 0; sg < nseg; ++sg) {
         const int c0 = sg * kSegD;
         const int m = cnt - c0 < kSegD ? cnt - c0 : kSegD;
@@ -525,16 +590,16 @@ __device__ __forceinline__ bool tile_sum(const uint2 *__restrict__ desc, const T
         const uint4 *q = reinterpret_cast<const uint4 *>(st.stage + st.buf * kSegD);
         constexpr int kS = Step<T>::value;
         int k = 0;
-        for (; k + kS <= m; k += kS) s += gather_step<T, kS>(q + (k >> 1), wrow, bit);
+        for (; k + kS <= m; k += kS) acc.template step<kS>(q + (k >> 1), wrow, bit);
         if (kS > kU)
-            for (; k < m; k += kU) s += gather_step<T, kU>(q + (k >> 1), wrow, bit);
+            for (; k < m; k += kU) acc.template step<kU>(q + (k >> 1), wrow, bit);
         st.buf ^= 1;
     }
     if (nseg == 0 && !st.issued && next_any) {
         st.issue(desc + size_t(nxt.d8) * kU, nxt.cnt < kSegD ? nxt.cnt : kSegD, st.buf, lane);
         st.issued = true;
     }
-    sum = s;
+    sum = acc.value();
     return true;
 }
 
@@ -604,14 +669,14 @@ __device__ __forceinline__ void advance(const JobDev &J, LoopState &ls, const Pr
     else if (ls.it >= J.max_iter) ls.stop = 1;
 }
 
-// w' of a row from x': x'/outdeg (x' itself without out-edges).  FP32 takes
-// the correctly rounded reciprocal times x' (two roundings instead of one,
-// no division sequence); FP64 divides.
+// w' of a row from x': x'/outdeg (x' itself without out-edges), as the
+// correctly rounded reciprocal times x' (two roundings instead of one, no
+// division sequence).
 __device__ __forceinline__ float w_of(float xn, int od) {
     return od ? xn * __frcp_rn(static_cast<float>(od)) : xn;
 }
 __device__ __forceinline__ double w_of(double xn, int od) {
-    return od ? xn / static_cast<double>(od) : xn;
+    return od ? xn * __drcp_rn(static_cast<double>(od)) : xn;
 }
 
 // A group of blocks runs all iterations of one job.  Returns false if the
