@@ -266,7 +266,8 @@ typedef struct {
 /* Filled by pagerank_batch_plan; plain data owned by the caller (device
  * pointers point into the plan's workspace). */
 typedef struct {
-    int32_t prec, n_jobs, n_graphs, n_blocks, warps, n_items, claim, reserved;
+    int32_t prec, n_jobs, n_graphs, n_blocks, warps, n_items, claim;
+    int32_t w_form;  /* FP64: 1 = w kept as exact fixed point, 0 = as double */
     int64_t total_tiles;
     void *jobs, *graphs, *items, *first, *queue, *ctl;
     int64_t total_rows;
@@ -295,11 +296,14 @@ ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec 
  * others run on one block each); `max_blocks` caps the grid (0 = every
  * co-resident block); `block_warps` is 8 (256-thread blocks, several per SM)
  * or 24 (one 768-thread block per SM), 0 = 24; `claim` 1 selects the claim
- * order, 0 the per-block lists.  pagerank_batch_plan uses 1.0, 1.0, 0, 8, 0.
+ * order, 0 the per-block lists; `fp64_form` (FFG_F64 only) keeps w as exact
+ * 128-bit fixed point (1) or as double (2), 0 = fixed point when every
+ * graph has at most 2^21 nodes.  pagerank_batch_plan uses 1.0, 1.0, 0, 8,
+ * 0, 0.
  * They change only the schedule, never results or the workspace size. */
 typedef struct {
     double split, grain;
-    int32_t max_blocks, block_warps, claim, reserved;
+    int32_t max_blocks, block_warps, claim, fp64_form;
 } ffg_pr_tuning;
 
 ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec,

@@ -71,7 +71,7 @@ class ffg_pr_job(C.Structure):
 class ffg_pr_batch(C.Structure):
     _fields_ = [("prec", C.c_int32), ("n_jobs", C.c_int32), ("n_graphs", C.c_int32),
                 ("n_blocks", C.c_int32), ("warps", C.c_int32), ("n_items", C.c_int32),
-                ("claim", C.c_int32), ("reserved", C.c_int32),
+                ("claim", C.c_int32), ("w_form", C.c_int32),
                 ("total_tiles", C.c_int64), ("jobs", C.c_void_p),
                 ("graphs", C.c_void_p), ("items", C.c_void_p), ("first", C.c_void_p),
                 ("queue", C.c_void_p),
@@ -92,7 +92,7 @@ class ffg_build_batch(C.Structure):
 
 class ffg_pr_tuning(C.Structure):
     _fields_ = [("split", C.c_double), ("grain", C.c_double), ("max_blocks", C.c_int32),
-                ("block_warps", C.c_int32), ("claim", C.c_int32), ("reserved", C.c_int32)]
+                ("block_warps", C.c_int32), ("claim", C.c_int32), ("fp64_form", C.c_int32)]
 
 
 class ffg_cp_job(C.Structure):
@@ -247,10 +247,11 @@ def pagerank_batch_plan(jobs, prec: int, ws: int, ws_bytes: int, plan: "ffg_pr_b
 
 def pagerank_batch_plan_tuned(jobs, prec: int, tuning, ws: int, ws_bytes: int,
                               plan: "ffg_pr_batch", stream: int = 0) -> int:
-    """``tuning``: (split, grain, max_blocks[, block_warps[, claim]])."""
+    """``tuning``: (split, grain, max_blocks[, block_warps[, claim[, fp64_form]]])."""
     t = ffg_pr_tuning(float(tuning[0]), float(tuning[1]), int(tuning[2]),
                       int(tuning[3]) if len(tuning) > 3 else 0,
-                      int(tuning[4]) if len(tuning) > 4 else 0, 0)
+                      int(tuning[4]) if len(tuning) > 4 else 0,
+                      int(tuning[5]) if len(tuning) > 5 else 0)
     return int(load().pagerank_batch_plan_tuned(jobs, len(jobs), int(prec), C.byref(t),
                                                 C.c_void_p(ws), int(ws_bytes), C.byref(plan),
                                                 C.c_void_p(stream)))

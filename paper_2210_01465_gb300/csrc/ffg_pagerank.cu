@@ -78,6 +78,14 @@ static_assert(kU % 2 == 0 && kSegD % kU == 0 && kU <= 32, "descriptor padding");
 // Descriptors per step of the gather loop (gathers in flight per lane): a
 // multiple of kU, the remainder of a segment is done in steps of kU.  FP64
 // stays at kU: its in-sums are bound by the FP64 pipe, where padding costs.
+// The FP64 form whose w is stored as 128-bit fixed point (see Rows below);
+// `double` is the FP64 form with w stored as double.
+struct F64x {};
+// graphs up to this many nodes keep the 16-byte fixed-point w (two buffers
+// of 16 N bytes stay well inside L2 next to the descriptors); larger ones
+// store w as double and convert each gathered value instead
+constexpr int64_t kFxMaxNodes = int64_t(1) << 21;
+
 template <typename T> struct Step { static constexpr int value = kU; };
 template <> struct Step<float> { static constexpr int value = FFG_PR_STEP32; };
 static_assert(FFG_PR_STEP32 % kU == 0 && kSegD % FFG_PR_STEP32 == 0, "gather step");
@@ -104,6 +112,7 @@ struct PrCtl {
 struct PrWs {
     PrCtl *ctl;
     void *w0, *w1;
+    double *rinv;         // FP64: 1 / outdeg per row
     uint2 *desc;          // tile descriptors (off, mask)
     int32_t *cnt;         // per tile: descriptors, padded to a multiple of kU
     uint2 *tinfo;         // per tile: (first descriptor / kU, cnt)
@@ -125,12 +134,17 @@ inline int64_t desc_capacity(int64_t n, int64_t e) { return e + 2 * kU * ((n + 3
 // tile descriptors are addressed in units of kU by 32-bit indices
 inline bool desc_fits(int64_t n, int64_t e) { return desc_capacity(n, e) / kU < (int64_t(1) << 32); }
 
-PrWs carve(void *base, int64_t n, int64_t e, size_t elem) {
+// w is stored in 4 bytes (FP32) or 16 (FP64 fixed point); FP64 also keeps
+// 1 / outdeg per row
+inline size_t w_bytes(ffg_prec prec) { return prec == FFG_F32 ? 4 : 16; }
+
+PrWs carve(void *base, int64_t n, int64_t e, ffg_prec prec) {
     Carver c(base);
     PrWs w;
     w.ctl = c.take<PrCtl>(1);
-    w.w0 = c.take<char>(size_t(n) * elem);
-    w.w1 = c.take<char>(size_t(n) * elem);
+    w.w0 = c.take<char>(size_t(n) * w_bytes(prec));
+    w.w1 = c.take<char>(size_t(n) * w_bytes(prec));
+    w.rinv = prec == FFG_F64 ? c.take<double>(size_t(n)) : nullptr;
     w.desc = c.take<uint2>(size_t(desc_capacity(n, e)));
     w.cnt = c.take<int32_t>(size_t((n + 31) / 32));
     w.tinfo = c.take<uint2>(size_t((n + 31) / 32));
@@ -411,13 +425,189 @@ __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout(
 // ---------------------------------------------------------------------------
 // per-iteration tile work
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// per-precision storage of w and the update of one row
+// ---------------------------------------------------------------------------
+// FP32: w is a float; in-sums, x' and w' are FP32.
+// FP64: w is stored exactly as a 128-bit fixed-point integer (Fx, quantum
+// 2^-120; w < 2 fits, and a w below 2^-120 would lose at most one quantum),
+// so a row's in-sum is exact, formed by integer additions, and rounded to
+// double once.  x' = alpha*S + c and w' = x' * (1/outdeg) are the only FP64
+// operations per row; the residual and the dangling mass are taken from the
+// fixed-point values.  A warp-wide FP64 add occupies the FP64 units of an SM
+// for 16 cycles on this part, so the integer form is the fast one as well
+// as the exact one.
+struct __align__(16) Fx {
+    unsigned long long lo, hi;  // value / 2^-120
+};
+
+__device__ __forceinline__ Fx fx_add(Fx a, Fx b) {
+    Fx r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < b.lo ? 1ULL : 0ULL);
+    return r;
+}
+
+// w >= 0 (truncated to the quantum)
+__device__ __forceinline__ Fx fx_of(double w) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(w));
+    const int e = static_cast<int>(b >> 52);
+    const unsigned long long m = (b & 0xfffffffffffffULL) | (e ? 0x10000000000000ULL : 0ULL);
+    const int sh = e - 955;  // w / 2^-120 = m * 2^sh, sh < 75 for w < 2
+    Fx r;
+    if (sh >= 64) {
+        r.lo = 0;
+        r.hi = m << (sh - 64);
+    } else if (sh > 0) {
+        r.lo = m << sh;
+        r.hi = m >> (64 - sh);
+    } else if (sh > -64) {
+        r.lo = m >> -sh;
+        r.hi = 0;
+    } else {
+        r.lo = r.hi = 0;
+    }
+    return r;
+}
+
+// to double, rounded to nearest even, with integer instructions
+__device__ __forceinline__ double dbl_of(Fx a) {
+    if ((a.hi | a.lo) == 0) return 0.0;
+    const int lz = a.hi ? __clzll(static_cast<long long>(a.hi))
+                        : 64 + __clzll(static_cast<long long>(a.lo));
+    unsigned long long h;  // the value shifted so that its leading one is bit 127
+    bool tail;             // a one below the 64 bits of h
+    if (lz >= 64) {
+        h = a.lo << (lz - 64);
+        tail = false;
+    } else if (lz > 0) {
+        h = (a.hi << lz) | (a.lo >> (64 - lz));
+        tail = (a.lo << lz) != 0;
+    } else {
+        h = a.hi;
+        tail = a.lo != 0;
+    }
+    unsigned long long mant = h >> 11;  // 53 bits with the leading one
+    const bool round = (h >> 10) & 1ULL;
+    const bool sticky = (h & 0x3ffULL) != 0 || tail;
+    long long e = 127 - lz - 120 + 1023;  // biased exponent of the leading one
+    if (round && (sticky || (mant & 1ULL))) {
+        ++mant;
+        if (mant >> 53) {
+            mant >>= 1;
+            ++e;
+        }
+    }
+    return __longlong_as_double((e << 52) | static_cast<long long>(mant & 0xfffffffffffffULL));
+}
+
+// a * k for an out-degree k
+__device__ __forceinline__ Fx fx_mul(Fx a, uint32_t k) {
+    Fx r;
+    r.lo = a.lo * k;
+    r.hi = a.hi * k + __umul64hi(a.lo, k);
+    return r;
+}
+
+__device__ __forceinline__ Fx fx_absdiff(Fx a, Fx b) {
+    const bool ge = a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo);
+    const Fx x = ge ? a : b, y = ge ? b : a;
+    Fx r;
+    r.lo = x.lo - y.lo;
+    r.hi = x.hi - y.hi - (x.lo < y.lo ? 1ULL : 0ULL);
+    return r;
+}
+
+// the 2^-60 fixed-point form of the reductions (value < 8)
+__device__ __forceinline__ long long fix60(Fx a) {
+    return static_cast<long long>((a.hi << 4) | (a.lo >> 60));
+}
+
+template <typename T>
+struct Rows;
+
+template <>
+struct Rows<float> {
+    using Real = float;
+    using W = float;
+    struct Extra {};
+    __device__ static W init(double x0, int od) { return static_cast<float>(od ? x0 / od : x0); }
+    __device__ static double x_of(W w, int od) {
+        return od ? static_cast<double>(w) * od : static_cast<double>(w);
+    }
+    __device__ static long long fix_x(W w, int od) { return to_fix(x_of(w, od)); }
+    __device__ static void load_extra(Extra &, const double *, int) {}
+    // x' = alpha*s + c from the row's in-sum; w' = x'/outdeg as x' times the
+    // correctly rounded reciprocal (two roundings, no division sequence)
+    __device__ static void update(float s, float a, float c, int od, W wold, const Extra &,
+                                  W *dst, Fix3 &f) {
+        const float xo = od ? wold * static_cast<float>(od) : wold;
+        const float xn = a * s + c;
+        f.r += to_fix(xn > xo ? xn - xo : xo - xn);
+        if (od == 0) f.d += to_fix(xn);
+        *dst = od ? xn * __frcp_rn(static_cast<float>(od)) : xn;
+    }
+};
+
+template <>
+struct Rows<double> {
+    using Real = double;
+    using W = double;
+    struct Extra {
+        double rinv;  // 1 / outdeg (1 without out-edges)
+    };
+    __device__ static W init(double x0, int od) { return od ? x0 / od : x0; }
+    __device__ static double x_of(W w, int od) { return od ? w * od : w; }
+    __device__ static long long fix_x(W w, int od) { return to_fix(x_of(w, od)); }
+    __device__ static void load_extra(Extra &e, const double *rinv, int v) {
+        e.rinv = v >= 0 ? __ldg(rinv + v) : 1.0;
+    }
+    __device__ static void update(double s, double a, double c, int od, W wold, const Extra &e,
+                                  W *dst, Fix3 &f) {
+        const double xo = od ? wold * od : wold;
+        const double xn = fma(a, s, c);
+        f.r += to_fix(xn > xo ? xn - xo : xo - xn);
+        if (od == 0) f.d += to_fix(xn);
+        *dst = od ? xn * e.rinv : xn;
+    }
+};
+
+template <>
+struct Rows<F64x> {
+    using Real = double;
+    using W = Fx;
+    struct Extra {
+        double rinv;  // 1 / outdeg (1 without out-edges)
+    };
+    __device__ static W init(double x0, int od) { return fx_of(od ? x0 / od : x0); }
+    __device__ static double x_of(W w, int od) {
+        return dbl_of(od ? fx_mul(w, static_cast<uint32_t>(od)) : w);
+    }
+    __device__ static long long fix_x(W w, int od) {
+        return fix60(od ? fx_mul(w, static_cast<uint32_t>(od)) : w);
+    }
+    __device__ static void load_extra(Extra &e, const double *rinv, int v) {
+        e.rinv = v >= 0 ? __ldg(rinv + v) : 1.0;
+    }
+    __device__ static void update(double s, double a, double c, int od, W wold, const Extra &e,
+                                  W *dst, Fix3 &f) {
+        const double xn = fma(a, s, c);
+        const Fx xf = fx_of(xn);
+        const Fx xo = od ? fx_mul(wold, static_cast<uint32_t>(od)) : wold;
+        f.r += fix60(fx_absdiff(xf, xo));
+        if (od == 0) f.d += fix60(xf);
+        *dst = od ? fx_of(xn * e.rinv) : xf;
+    }
+};
+
 template <typename T>
 struct TileInfo {
-    uint32_t d8;   // first descriptor / kU
-    int cnt;       // descriptors (multiple of kU)
-    int32_t v;     // this lane's row (-1 past the last slot)
-    int32_t od;    // its out-degree
-    T wv;          // its w
+    uint32_t d8;                        // first descriptor / kU
+    int cnt;                            // descriptors (multiple of kU)
+    int32_t v;                          // this lane's row (-1 past the last slot)
+    int32_t od;                         // its out-degree
+    typename Rows<T>::W wv;             // its w
+    typename Rows<T>::Extra ex;         // its per-precision row data
 };
 
 // A tile's info loads in two steps, a tile apart, so that no load waits on
@@ -433,14 +623,16 @@ __device__ __forceinline__ TileInfo<T> load_head(int t, int n, const uint2 *__re
     ti.cnt = static_cast<int>(h.y);
     ti.v = slot < n ? __ldg(perm + slot) : -1;
     ti.od = 0;
-    ti.wv = T(0);
+    ti.wv = typename Rows<T>::W{};
+    ti.ex = typename Rows<T>::Extra{};
     return ti;
 }
 template <typename T>
 __device__ __forceinline__ void load_row(TileInfo<T> &ti, const int32_t *__restrict__ outdeg,
-                                         const T *wc) {
+                                         const typename Rows<T>::W *wc, const double *rinv) {
     ti.od = ti.v >= 0 ? __ldg(outdeg + ti.v) : 0;
-    ti.wv = ti.v >= 0 ? wc[ti.v] : T(0);
+    ti.wv = ti.v >= 0 ? wc[ti.v] : typename Rows<T>::W{};
+    Rows<T>::load_extra(ti.ex, rinv, ti.v);
 }
 
 // Per-warp TMA stream of descriptor segments into a two-buffer stage.
@@ -493,13 +685,9 @@ __device__ __forceinline__ T gather_step(const uint4 *q, const T *wrow, uint32_t
     return v[0];
 }
 
-// Per-lane accumulator of a row's in-sum.  FP32: pairwise partial sums
-// added in order.  FP64: the sum is exact -- every gathered w is added as a
-// 128-bit fixed-point integer (quantum 2^-120; w < 2 and sums < 2^7 fit, and
-// a w below 2^-120 would lose at most one quantum) with integer instructions
-// only, and rounded to double once per row.  A warp-wide FP64 add occupies
-// the FP64 units of an SM for 16 cycles on this part, so the integer form is
-// also the faster one.
+// Per-lane accumulator of a row's in-sum: FP32 pairwise partial sums added
+// in order; FP64 exact 128-bit integer sums (of stored fixed-point values, or
+// of doubles converted as they are gathered).
 template <typename T>
 struct Accum;
 
@@ -515,30 +703,7 @@ struct Accum<float> {
 
 template <>
 struct Accum<double> {
-    unsigned long long lo = 0, hi = 0;  // sum / 2^-120, 128 bits
-    __device__ __forceinline__ void add(double w) {  // w >= 0
-        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(w));
-        const int e = static_cast<int>(b >> 52);
-        const unsigned long long m =
-            (b & 0xfffffffffffffULL) | (e ? 0x10000000000000ULL : 0ULL);
-        const int sh = e - 955;  // w / 2^-120 = m * 2^sh, sh < 75
-        unsigned long long l, h;
-        if (sh >= 64) {
-            l = 0;
-            h = m << (sh - 64);
-        } else if (sh > 0) {
-            l = m << sh;
-            h = m >> (64 - sh);
-        } else if (sh > -64) {
-            l = m >> -sh;
-            h = 0;
-        } else {
-            l = 0;
-            h = 0;
-        }
-        lo += l;
-        hi += h + (lo < l ? 1ULL : 0ULL);
-    }
+    Fx s{0ULL, 0ULL};
     template <int N>
     __device__ __forceinline__ void step(const uint4 *q, const double *wrow, uint32_t bit) {
         double v[N];
@@ -549,13 +714,27 @@ struct Accum<double> {
             v[2 * j + 1] = (d.w & bit) ? wrow[static_cast<int32_t>(d.z)] : 0.0;
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) add(v[j]);
+        for (int j = 0; j < N; ++j) s = fx_add(s, fx_of(v[j]));
     }
-    __device__ __forceinline__ double value() const {
-        // hi * 2^-56 + lo * 2^-120 (scalings by powers of two are exact)
-        return fma(__ull2double_rn(lo), 7.52316384526264005e-37,
-                   __ull2double_rn(hi) * 1.38777878078144568e-17);
+    __device__ __forceinline__ double value() const { return dbl_of(s); }
+};
+
+template <>
+struct Accum<F64x> {
+    Fx s{0ULL, 0ULL};
+    template <int N>
+    __device__ __forceinline__ void step(const uint4 *q, const Fx *wrow, uint32_t bit) {
+        Fx v[N];
+#pragma unroll
+        for (int j = 0; j < N / 2; ++j) {
+            const uint4 d = q[j];
+            v[2 * j] = (d.y & bit) ? wrow[static_cast<int32_t>(d.x)] : Fx{0ULL, 0ULL};
+            v[2 * j + 1] = (d.w & bit) ? wrow[static_cast<int32_t>(d.z)] : Fx{0ULL, 0ULL};
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fx_add(s, v[j]);
     }
+    __device__ __forceinline__ double value() const { return dbl_of(s); }
 };
 
 // Sum over the in-edges of this lane's row (wrow = w + row): the tile's
@@ -565,7 +744,8 @@ struct Accum<double> {
 template <typename T>
 __device__ __forceinline__ bool tile_sum(const uint2 *__restrict__ desc, const TileInfo<T> &cur,
                                          const TileInfo<T> &nxt, bool has_next, Stream &st,
-                                         const T *wrow, uint32_t bit, int lane, T &sum) {
+                                         const typename Rows<T>::W *wrow, uint32_t bit, int lane,
+                                         typename Rows<T>::Real &sum) {
     const int cnt = cur.cnt;
     const int nseg = (cnt + kSegD - 1) / kSegD;
     const bool next_any = has_next && nxt.cnt > 0;
@@ -636,6 +816,7 @@ struct JobDev {
     const uint2 *desc;
     const uint2 *tinfo;
     const int32_t *perm;
+    double *rinv;  // FP64 only: 1 / outdeg per row
     const int64_t *tpre;
     const int64_t *apre;  // rows with in-edges: apre[n] - apre[0]
     void *ranks, *w0, *w1;
@@ -669,28 +850,21 @@ __device__ __forceinline__ void advance(const JobDev &J, LoopState &ls, const Pr
     else if (ls.it >= J.max_iter) ls.stop = 1;
 }
 
-// w' of a row from x': x'/outdeg (x' itself without out-edges), as the
-// correctly rounded reciprocal times x' (two roundings instead of one, no
-// division sequence).
-__device__ __forceinline__ float w_of(float xn, int od) {
-    return od ? xn * __frcp_rn(static_cast<float>(od)) : xn;
-}
-__device__ __forceinline__ double w_of(double xn, int od) {
-    return od ? xn * __drcp_rn(static_cast<double>(od)) : xn;
-}
-
 // A group of blocks runs all iterations of one job.  Returns false if the
 // block must stop (a bounded wait expired).
 template <typename T, int W>
 __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     constexpr int kThreads = 32 * W;
+    using R = typename Rows<T>::Real;  // arithmetic type
     const int32_t *__restrict__ outdeg = J.outdeg;
     const uint2 *__restrict__ desc = J.desc;
     const uint2 *__restrict__ tinfo = J.tinfo;
     const int32_t *__restrict__ perm = J.perm;
     const int64_t n = J.n;
     const int nb = J.group;
-    T *w0 = static_cast<T *>(J.w0), *w1 = static_cast<T *>(J.w1);
+    using WS = typename Rows<T>::W;
+    WS *w0 = static_cast<WS *>(J.w0), *w1 = static_cast<WS *>(J.w1);
+    double *rinv = J.rinv;  // FP64: 1 / outdeg per row
     PrCtl *ctl = J.ctl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -702,7 +876,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     __shared__ int s_range[3];
     __shared__ unsigned s_next;
     __shared__ LoopState s_ls;
-    __shared__ T s_c;
+    __shared__ R s_c;
     __syncthreads();
     if (threadIdx.x == 0) {
         const int64_t ntiles = (J.apre[n] - J.apre[0] + 31) >> 5;
@@ -721,13 +895,14 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     // prologue: w from the start vector and D_0 (grid-stride)
     {
         const double inv_n = 1.0 / static_cast<double>(n);
-        const T *ranks = static_cast<const T *>(J.ranks);
+        const R *ranks = static_cast<const R *>(J.ranks);
         Fix3 acc0;
         const int64_t stride = int64_t(nb) * kThreads;
         for (int64_t v = int64_t(rank) * kThreads + threadIdx.x; v < n; v += stride) {
             const double x0 = J.init ? static_cast<double>(ranks[v]) : inv_n;
             const int32_t od = __ldg(outdeg + v);
-            w0[v] = static_cast<T>(od ? x0 / od : x0);
+            w0[v] = Rows<T>::init(x0, od);
+            if (rinv) rinv[v] = od ? 1.0 / od : 1.0;
             if (od == 0) acc0.d += to_fix(x0);
         }
         const Fix3 b = block_sum_fix<W>(acc0);
@@ -736,16 +911,16 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     unsigned phase = 1;
     int buf = 0;
     if (!group_barrier(ctl, phase * nb, nb)) return false;
-    if (threadIdx.x == 0) advance<T>(J, s_ls, ctl, buf, &s_c, false);
+    if (threadIdx.x == 0) advance<R>(J, s_ls, ctl, buf, &s_c, false);
     __syncthreads();
-    T *wc = w0, *wn = w1;
-    const T a = static_cast<T>(J.alpha);
+    WS *wc = w0, *wn = w1;
+    const R a = static_cast<R>(J.alpha);
     int failed = 0;
     const int t0 = bt0 + warp, t1 = bt0 + W + warp;  // this warp's first two tiles
     TileInfo<T> pre0, pre1;  // ... loaded ahead (have_pre)
     bool have_pre = false;
     while (true) {
-        const T c = s_c;
+        const R c = s_c;
         Fix3 facc;
         if (t0 < bt1 && !failed) {
             // cur: tile being summed; nxt: its successor (info loaded one tile
@@ -759,7 +934,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
             } else {
                 cur = load_head<T>(t0, ni, tinfo, perm, lane);
                 nxt = load_head<T>(t1 < bt1 ? t1 : t0, ni, tinfo, perm, lane);
-                load_row<T>(cur, outdeg, wc);
+                load_row<T>(cur, outdeg, wc, rinv);
             }
             while (true) {
                 const bool has_next = tn < bt1;
@@ -769,22 +944,16 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
                     if (lane == 0) g = atomicAdd(&s_next, 1u);
                     tn2 = static_cast<int>(__shfl_sync(0xffffffffu, g, 0));
                 }
-                load_row<T>(nxt, outdeg, wc);
+                load_row<T>(nxt, outdeg, wc, rinv);
                 const TileInfo<T> nx2 = load_head<T>(tn2 < bt1 ? tn2 : t, ni, tinfo, perm, lane);
                 const int v = cur.v;
-                T s = T(0);
+                R s = R(0);
                 if (!tile_sum<T>(desc, cur, nxt, has_next, st, wc + (v < 0 ? 0 : v), 1u << lane,
                                  lane, s)) {
                     failed = 1;
                     break;
                 }
-                if (v >= 0) {
-                    const T xo = cur.od ? cur.wv * static_cast<T>(cur.od) : cur.wv;
-                    const T xn = a * s + c;
-                    facc.r += to_fix(xn > xo ? xn - xo : xo - xn);
-                    if (cur.od == 0) facc.d += to_fix(xn);
-                    wn[v] = w_of(xn, cur.od);
-                }
+                if (v >= 0) Rows<T>::update(s, a, c, cur.od, cur.wv, cur.ex, wn + v, facc);
                 if (!has_next) break;
                 cur = nxt;
                 t = tn;
@@ -797,10 +966,9 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
              i += int64_t(nb) * kThreads) {
             const int v = __ldg(perm + i);
             const int32_t od = __ldg(outdeg + v);
-            const T xo = od ? wc[v] * static_cast<T>(od) : wc[v];
-            facc.r += to_fix(c > xo ? c - xo : xo - c);
-            if (od == 0) facc.d += to_fix(c);
-            wn[v] = w_of(c, od);
+            typename Rows<T>::Extra ex;
+            Rows<T>::load_extra(ex, rinv, v);
+            Rows<T>::update(R(0), a, c, od, wc[v], ex, wn + v, facc);
         }
         if (failed == 1) {
             // let this warp's own copies land (bounded), then report
@@ -818,7 +986,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
         if (t0 < bt1 && !failed) {
             pre0 = load_head<T>(t0, ni, tinfo, perm, lane);
             pre1 = load_head<T>(t1 < bt1 ? t1 : t0, ni, tinfo, perm, lane);
-            load_row<T>(pre0, outdeg, wn);
+            load_row<T>(pre0, outdeg, wn, rinv);
             if (pre0.cnt > 0 && !st.issued) {
                 st.issue(desc + size_t(pre0.d8) * kU, pre0.cnt < kSegD ? pre0.cnt : kSegD, st.buf,
                          lane);
@@ -837,9 +1005,9 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
             st.issued = false;
             return false;
         }
-        if (threadIdx.x == 0) advance<T>(J, s_ls, ctl, buf, &s_c, true);
+        if (threadIdx.x == 0) advance<R>(J, s_ls, ctl, buf, &s_c, true);
         __syncthreads();
-        T *tmp = wc;
+        WS *tmp = wc;
         wc = wn;
         wn = tmp;
         if (s_ls.stop) break;
@@ -854,7 +1022,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
         Fix3 accs;
         for (int64_t v = int64_t(rank) * kThreads + threadIdx.x; v < n; v += stride) {
             const int32_t od = __ldg(outdeg + v);
-            accs.s += to_fix(od ? static_cast<double>(wc[v]) * od : static_cast<double>(wc[v]));
+            accs.s += Rows<T>::fix_x(wc[v], od);
         }
         const Fix3 b = block_sum_fix<W>(accs);
         buf = buf == 2 ? 0 : buf + 1;
@@ -865,11 +1033,10 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
         __syncthreads();
     }
     const double inv_s = 1.0 / s_ls.xs;
-    T *ranks = static_cast<T *>(J.ranks);
+    R *ranks = static_cast<R *>(J.ranks);
     for (int64_t v = int64_t(rank) * kThreads + threadIdx.x; v < n; v += stride) {
         const int32_t od = __ldg(outdeg + v);
-        const double x = od ? static_cast<double>(wc[v]) * od : static_cast<double>(wc[v]);
-        ranks[v] = static_cast<T>(x * inv_s);
+        ranks[v] = static_cast<R>(Rows<T>::x_of(wc[v], od) * inv_s);
     }
     if (rank == 0 && threadIdx.x == 0) {
         ctl->iters = s_ls.it;
@@ -1058,7 +1225,7 @@ ffg_status launch_pr(const JobDev *jobs, const int2 *items, const int *first, in
 
 template <typename T>
 ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, int init,
-                  T *ranks, PrWs &w, cudaStream_t stream) {
+                  void *ranks, PrWs &w, cudaStream_t stream) {
     constexpr int W = kWarpsSingle;
     int per_sm = 0, sms = 0;
     FFG_TRY((kernel_config<T, W>(&per_sm, &sms)));
@@ -1077,6 +1244,7 @@ ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, in
     J.ranks = ranks;
     J.w0 = w.w0;
     J.w1 = w.w1;
+    J.rinv = w.rinv;
     J.ctl = w.ctl;
     J.n = g->n_nodes;
     J.alpha = alpha;
@@ -1111,7 +1279,7 @@ using namespace ffg;
 
 extern "C" size_t pagerank_workspace_bytes(int64_t n_nodes, int64_t n_edges, ffg_prec prec) {
     if (n_nodes < 0 || n_edges < 0) return 0;
-    return carve(nullptr, n_nodes, n_edges, prec == FFG_F32 ? 4 : 8).bytes;
+    return carve(nullptr, n_nodes, n_edges, prec).bytes;
 }
 
 extern "C" ffg_status pagerank_solve(const ffg_graph *g, double damping, double tol,
@@ -1133,7 +1301,7 @@ extern "C" ffg_status pagerank_solve(const ffg_graph *g, double damping, double 
     if (!ranks || !workspace) return set_error("ranks/workspace NULL"), FFG_ERR_INVALID_ARG;
     if (!aligned256(workspace))
         return set_error("workspace not 256-byte aligned"), FFG_ERR_INVALID_ARG;
-    PrWs w = carve(workspace, g->n_nodes, g->n_edges, prec == FFG_F32 ? 4 : 8);
+    PrWs w = carve(workspace, g->n_nodes, g->n_edges, prec);
     if (ws_bytes < w.bytes)
         return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
     if (init & ~(FFG_INIT_RANKS | FFG_INIT_LAYOUT))
@@ -1141,12 +1309,12 @@ extern "C" ffg_status pagerank_solve(const ffg_graph *g, double damping, double 
     FFG_TRY(check_cuda(cudaMemsetAsync(w.ctl, 0, sizeof(PrCtl), stream), "memset"));
     if (!(init & FFG_INIT_LAYOUT)) FFG_TRY(launch_layout(g, w, stream));
     const int warm = (init & FFG_INIT_RANKS) ? 1 : 0;
-    if (prec == FFG_F64)
-        FFG_TRY(launch<double>(g, damping, tol, max_iter, warm, static_cast<double *>(ranks), w,
-                               stream));
+    if (prec == FFG_F32)
+        FFG_TRY(launch<float>(g, damping, tol, max_iter, warm, ranks, w, stream));
+    else if (g->n_nodes <= kFxMaxNodes)
+        FFG_TRY(launch<F64x>(g, damping, tol, max_iter, warm, ranks, w, stream));
     else
-        FFG_TRY(launch<float>(g, damping, tol, max_iter, warm, static_cast<float *>(ranks), w,
-                              stream));
+        FFG_TRY(launch<double>(g, damping, tol, max_iter, warm, ranks, w, stream));
     if (!iters_out && !residual_out) return FFG_OK;
     return read_result(w.ctl, iters_out, residual_out, stream);
 }
@@ -1162,7 +1330,7 @@ extern "C" ffg_status pagerank_prepare(const ffg_graph *g, ffg_prec prec, void *
         return set_error("unknown precision %d", (int)prec), FFG_ERR_INVALID_ARG;
     if (!workspace || !aligned256(workspace))
         return set_error("workspace NULL or not 256-byte aligned"), FFG_ERR_INVALID_ARG;
-    PrWs w = carve(workspace, g->n_nodes, g->n_edges, prec == FFG_F32 ? 4 : 8);
+    PrWs w = carve(workspace, g->n_nodes, g->n_edges, prec);
     if (ws_bytes < w.bytes)
         return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
     return launch_layout(g, w, static_cast<cudaStream_t>(stream_));
@@ -1346,7 +1514,7 @@ struct BatchWs {
 // Workspace of a plan: tables, then per job ctl / w buffers, then
 // per distinct graph the layout and tile metadata.  host_jobs / host_graphs
 // (if non-NULL) receive the device pointers of every job and graph.
-BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
+BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, ffg_prec prec,
                     const PlanHost &P, int cap, std::vector<JobDev> *host_jobs,
                     std::vector<GraphDev> *host_graphs) {
     Carver c(base);
@@ -1402,8 +1570,9 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
         J.apre = G.apre;
         J.tpre = w.tpre + G.tile0;
         J.ranks = jobs[j].ranks;
-        J.w0 = c.take<char>(size_t(g->n_nodes) * elem);
-        J.w1 = c.take<char>(size_t(g->n_nodes) * elem);
+        J.w0 = c.take<char>(size_t(g->n_nodes) * w_bytes(prec));
+        J.w1 = c.take<char>(size_t(g->n_nodes) * w_bytes(prec));
+        J.rinv = prec == FFG_F64 ? c.take<double>(size_t(g->n_nodes)) : nullptr;
         J.ctl = w.ctl + j;
         J.n = g->n_nodes;
         J.alpha = jobs[j].damping;
@@ -1422,12 +1591,23 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, size_t elem,
 // co-resident blocks of the batch kernel with `warps` warps per block
 ffg_status batch_blocks(ffg_prec prec, int warps, int *nb_max) {
     int per_sm = 0, sms = 0;
+    int a = 0, b = 0;
     if (warps == kWarpsBatch) {
-        if (prec == FFG_F64) FFG_TRY((kernel_config<double, kWarpsBatch>(&per_sm, &sms)));
-        else FFG_TRY((kernel_config<float, kWarpsBatch>(&per_sm, &sms)));
+        if (prec == FFG_F64) {
+            FFG_TRY((kernel_config<double, kWarpsBatch>(&a, &sms)));
+            FFG_TRY((kernel_config<F64x, kWarpsBatch>(&b, &sms)));
+            per_sm = std::min(a, b);
+        } else {
+            FFG_TRY((kernel_config<float, kWarpsBatch>(&per_sm, &sms)));
+        }
     } else {
-        if (prec == FFG_F64) FFG_TRY((kernel_config<double, kWarpsSingle>(&per_sm, &sms)));
-        else FFG_TRY((kernel_config<float, kWarpsSingle>(&per_sm, &sms)));
+        if (prec == FFG_F64) {
+            FFG_TRY((kernel_config<double, kWarpsSingle>(&a, &sms)));
+            FFG_TRY((kernel_config<F64x, kWarpsSingle>(&b, &sms)));
+            per_sm = std::min(a, b);
+        } else {
+            FFG_TRY((kernel_config<float, kWarpsSingle>(&per_sm, &sms)));
+        }
     }
     *nb_max = std::min(kMaxBlocks, sms * per_sm);
     return FFG_OK;
@@ -1458,7 +1638,7 @@ extern "C" size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t
         return 0;
     PlanHost P;
     if (make_plan(jobs, n_jobs, nb_max, kWarpsSingle, kDefaultTuning, P) != FFG_OK) return 0;
-    return carve_batch(nullptr, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, cap, nullptr, nullptr)
+    return carve_batch(nullptr, jobs, n_jobs, prec, P, cap, nullptr, nullptr)
         .bytes;
 }
 
@@ -1485,9 +1665,11 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     const ffg_pr_tuning tu = tuning ? *tuning : kDefaultTuning;
     const int warps = tu.block_warps ? tu.block_warps : kWarpsSingle;
     if (!(tu.split > 0.0) || !(tu.grain > 0.0) || tu.max_blocks < 0 ||
-        (warps != kWarpsBatch && warps != kWarpsSingle) || (tu.claim != 0 && tu.claim != 1))
+        (warps != kWarpsBatch && warps != kWarpsSingle) || (tu.claim != 0 && tu.claim != 1) ||
+        tu.fp64_form < 0 || tu.fp64_form > 2)
         return set_error("tuning: split and grain must be > 0, max_blocks >= 0, block_warps "
-                         "0, %d or %d, claim 0 or 1", kWarpsBatch, kWarpsSingle),
+                         "0, %d or %d, claim 0 or 1, fp64_form 0, 1 or 2",
+                         kWarpsBatch, kWarpsSingle),
                FFG_ERR_INVALID_ARG;
     int cap = 0, nb_max = 0;
     FFG_TRY(batch_cap(prec, &cap));
@@ -1496,7 +1678,7 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     FFG_TRY(make_plan(jobs, n_jobs, nb_max, warps, tu, P));
     std::vector<JobDev> jd;
     std::vector<GraphDev> gd;
-    BatchWs w = carve_batch(workspace, jobs, n_jobs, prec == FFG_F32 ? 4 : 8, P, cap, &jd, &gd);
+    BatchWs w = carve_batch(workspace, jobs, n_jobs, prec, P, cap, &jd, &gd);
     if (ws_bytes < w.bytes)
         return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
     if (P.nb > nb_max || P.items.size() > size_t(n_jobs) * cap)
@@ -1520,6 +1702,12 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     plan->n_blocks = P.nb;
     plan->warps = P.warps;
     plan->claim = P.claim;
+    int64_t n_max = 0;
+    for (const ffg_graph *g : P.graphs) n_max = std::max<int64_t>(n_max, g->n_nodes);
+    plan->w_form = prec == FFG_F64 && (tu.fp64_form == 1 ||
+                                       (tu.fp64_form == 0 && n_max <= kFxMaxNodes))
+                       ? 1
+                       : 0;
     plan->n_items = static_cast<int32_t>(P.items.size());
     plan->total_tiles = tiles;
     plan->jobs = w.jobs;
@@ -1580,14 +1768,19 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
     const int *first = static_cast<const int *>(plan->first);
     int *queue = plan->claim ? static_cast<int *>(plan->queue) : nullptr;
     const int ni = plan->n_items, nb = plan->n_blocks;
+    const bool fx = plan->w_form != 0;  // FP64 w stored in fixed point
     if (plan->warps == kWarpsBatch) {
-        if (prec == FFG_F64)
-            return launch_pr<double, kWarpsBatch>(jobs, items, first, queue, ni, nb, none, stream);
-        return launch_pr<float, kWarpsBatch>(jobs, items, first, queue, ni, nb, none, stream);
+        if (prec == FFG_F32)
+            return launch_pr<float, kWarpsBatch>(jobs, items, first, queue, ni, nb, none, stream);
+        if (fx)
+            return launch_pr<F64x, kWarpsBatch>(jobs, items, first, queue, ni, nb, none, stream);
+        return launch_pr<double, kWarpsBatch>(jobs, items, first, queue, ni, nb, none, stream);
     }
-    if (prec == FFG_F64)
-        return launch_pr<double, kWarpsSingle>(jobs, items, first, queue, ni, nb, none, stream);
-    return launch_pr<float, kWarpsSingle>(jobs, items, first, queue, ni, nb, none, stream);
+    if (prec == FFG_F32)
+        return launch_pr<float, kWarpsSingle>(jobs, items, first, queue, ni, nb, none, stream);
+    if (fx)
+        return launch_pr<F64x, kWarpsSingle>(jobs, items, first, queue, ni, nb, none, stream);
+    return launch_pr<double, kWarpsSingle>(jobs, items, first, queue, ni, nb, none, stream);
 }
 
 extern "C" ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *iters_out,
