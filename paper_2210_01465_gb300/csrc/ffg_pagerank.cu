@@ -1047,9 +1047,9 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     return failed == 0;
 }
 
-// The persistent kernel.  With jobs == nullptr it runs `single` on the whole
-// grid.  Otherwise it runs the plan's items -- (job, rank) pairs -- in one
-// of two orders:
+// The persistent kernels: k_pagerank runs one solve on the whole grid,
+// k_pagerank_batch the plan's items -- (job, rank) pairs -- in one of two
+// orders:
 // - lists (queue == nullptr): block b runs items [first[b], first[b+1]),
 //   its multi-block rank (if any) first, so no two groups wait on each other;
 // - claims: the blocks claim the items in order through a counter (`queue`,
@@ -1057,14 +1057,10 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
 //   number at most the grid size, so when all blocks wait at group barriers
 //   every multi-block rank has been claimed and no group waits forever;
 //   one-block jobs follow, longest first, and go to whichever block is free.
-template <typename T, int W>
-__global__ void __launch_bounds__(32 * W, W > kWarpsBatch ? 1 : FFG_PR_MINBLOCKS)
-    k_pagerank(const JobDev *__restrict__ jobs, const int2 *__restrict__ items,
-               const int *__restrict__ first, int *__restrict__ queue, int n_items,
-               JobDev single) {
-    extern __shared__ __align__(128) unsigned char s_dyn[];
+// shared memory: per-warp stages, then mbarriers
+template <int W>
+__device__ __forceinline__ Stream make_stream(unsigned char *s_dyn) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // shared memory: per-warp stages, then mbarriers
     Stream st;
     st.stage = reinterpret_cast<uint2 *>(s_dyn) + size_t(warp) * 2 * kSegD;
     st.bar = reinterpret_cast<uint64_t *>(s_dyn + size_t(W) * 2 * kSegD * sizeof(uint2)) +
@@ -1079,10 +1075,24 @@ __global__ void __launch_bounds__(32 * W, W > kWarpsBatch ? 1 : FFG_PR_MINBLOCKS
         fence_mbar_init();
     }
     __syncwarp();
-    if (jobs == nullptr) {
-        run_job<T, W>(single, blockIdx.x, st);
-        return;
-    }
+    return st;
+}
+
+// One solve on the whole grid.
+template <typename T, int W>
+__global__ void __launch_bounds__(32 * W, W > kWarpsBatch ? 1 : FFG_PR_MINBLOCKS)
+    k_pagerank(JobDev single) {
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    Stream st = make_stream<W>(s_dyn);
+    run_job<T, W>(single, blockIdx.x, st);
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(32 * W, W > kWarpsBatch ? 1 : FFG_PR_MINBLOCKS)
+    k_pagerank_batch(const JobDev *__restrict__ jobs, const int2 *__restrict__ items,
+                     const int *__restrict__ first, int *__restrict__ queue, int n_items) {
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    Stream st = make_stream<W>(s_dyn);
     if (queue == nullptr) {
         for (int i = first[blockIdx.x]; i < first[blockIdx.x + 1]; ++i) {
             const int2 item = items[i];
@@ -1192,12 +1202,13 @@ ffg_status launch_layout(const ffg_graph *g, PrWs &w, cudaStream_t stream) {
 }
 
 template <typename T, int W>
-ffg_status kernel_config(int *blocks_per_sm, int *sms) {
+ffg_status kernel_config(int *blocks_per_sm, int *sms, bool batch = false) {
     int dev = 0;
     FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
     FFG_TRY(check_cuda(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
-    auto kern = k_pagerank<T, W>;
     const size_t smem = pr_smem_bytes<W>();
+    const void *kern = batch ? reinterpret_cast<const void *>(k_pagerank_batch<T, W>)
+                             : reinterpret_cast<const void *>(k_pagerank<T, W>);
     FFG_TRY(check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             static_cast<int>(smem)),
                        "smem attribute"));
@@ -1211,14 +1222,21 @@ ffg_status kernel_config(int *blocks_per_sm, int *sms) {
 template <typename T, int W>
 ffg_status launch_pr(const JobDev *jobs, const int2 *items, const int *first, int *queue,
                      int n_items, int nb, const JobDev &single, cudaStream_t stream) {
-    auto kern = k_pagerank<T, W>;
     const size_t smem = pr_smem_bytes<W>();
-    JobDev s = single;
-    void *args[] = {(void *)&jobs, (void *)&items, (void *)&first, (void *)&queue,
-                    (void *)&n_items, (void *)&s};
-    FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)kern, dim3(nb), dim3(32 * W),
-                                                   args, smem, stream),
-                       "k_pagerank"));
+    if (jobs == nullptr) {
+        JobDev s = single;
+        void *args[] = {(void *)&s};
+        FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)k_pagerank<T, W>, dim3(nb),
+                                                       dim3(32 * W), args, smem, stream),
+                           "k_pagerank"));
+    } else {
+        void *args[] = {(void *)&jobs, (void *)&items, (void *)&first, (void *)&queue,
+                        (void *)&n_items};
+        FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)k_pagerank_batch<T, W>,
+                                                       dim3(nb), dim3(32 * W), args, smem,
+                                                       stream),
+                           "k_pagerank_batch"));
+    }
     count_launch();
     return FFG_OK;
 }
@@ -1594,19 +1612,19 @@ ffg_status batch_blocks(ffg_prec prec, int warps, int *nb_max) {
     int a = 0, b = 0;
     if (warps == kWarpsBatch) {
         if (prec == FFG_F64) {
-            FFG_TRY((kernel_config<double, kWarpsBatch>(&a, &sms)));
-            FFG_TRY((kernel_config<F64x, kWarpsBatch>(&b, &sms)));
+            FFG_TRY((kernel_config<double, kWarpsBatch>(&a, &sms, true)));
+            FFG_TRY((kernel_config<F64x, kWarpsBatch>(&b, &sms, true)));
             per_sm = std::min(a, b);
         } else {
-            FFG_TRY((kernel_config<float, kWarpsBatch>(&per_sm, &sms)));
+            FFG_TRY((kernel_config<float, kWarpsBatch>(&per_sm, &sms, true)));
         }
     } else {
         if (prec == FFG_F64) {
-            FFG_TRY((kernel_config<double, kWarpsSingle>(&a, &sms)));
-            FFG_TRY((kernel_config<F64x, kWarpsSingle>(&b, &sms)));
+            FFG_TRY((kernel_config<double, kWarpsSingle>(&a, &sms, true)));
+            FFG_TRY((kernel_config<F64x, kWarpsSingle>(&b, &sms, true)));
             per_sm = std::min(a, b);
         } else {
-            FFG_TRY((kernel_config<float, kWarpsSingle>(&per_sm, &sms)));
+            FFG_TRY((kernel_config<float, kWarpsSingle>(&per_sm, &sms, true)));
         }
     }
     *nb_max = std::min(kMaxBlocks, sms * per_sm);
