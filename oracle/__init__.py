@@ -102,6 +102,10 @@ def _load():
                                               C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
             lib.or_centrality.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_double, C.c_void_p, C.c_int32, C.c_void_p]
+            lib.or_dag_values.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
+            lib.or_absorption.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = lib
     return _lib
 
@@ -206,6 +210,60 @@ def pagerank_exact(g: Graph, alpha: float = 0.85) -> np.ndarray:
     if st:
         raise OracleError(st, "pagerank_exact")
     return x[:g.n_nodes]
+
+
+def dag_values(g: Graph, d: float) -> np.ndarray:
+    """y[v] = 1 + d * sum_{u -> v} y[u] / outdeg[u] (unnormalised exact solve)."""
+    y = np.zeros(max(g.n_nodes, 1), dtype=np.float64)
+    failed = g.failed.astype(np.uint8)
+    st = _load().or_dag_values(g.n_nodes, _ptr(g.in_ptr), _ptr(g.in_idx), _ptr(g.outdeg),
+                               _ptr(failed), _ptr(g.node_fit), d, _ptr(y))
+    if st:
+        raise OracleError(st, "dag_values")
+    return y[:g.n_nodes]
+
+
+def absorption(g: Graph) -> np.ndarray:
+    """Probability that an improving walk from a uniform start passes / ends
+    at each node."""
+    a = np.zeros(max(g.n_nodes, 1), dtype=np.float64)
+    failed = g.failed.astype(np.uint8)
+    st = _load().or_absorption(g.n_nodes, _ptr(g.in_ptr), _ptr(g.in_idx), _ptr(g.outdeg),
+                               _ptr(failed), _ptr(g.node_fit), _ptr(a))
+    if st:
+        raise OracleError(st, "absorption")
+    return a[:g.n_nodes]
+
+
+def dag_values_csr(in_ptr, in_idx, outdeg, key, d):
+    """``key``: per-node fitness; edges must run from higher to lower key."""
+    in_ptr = np.ascontiguousarray(in_ptr, dtype=np.int64)
+    in_idx = np.ascontiguousarray(in_idx if len(in_idx) else [0], dtype=np.int32)
+    outdeg = np.ascontiguousarray(outdeg, dtype=np.int32)
+    key = np.ascontiguousarray(key, dtype=np.float64)
+    n = len(outdeg)
+    failed = np.zeros(n, dtype=np.uint8)
+    y = np.zeros(n, dtype=np.float64)
+    st = _load().or_dag_values(n, _ptr(in_ptr), _ptr(in_idx), _ptr(outdeg), _ptr(failed),
+                               _ptr(key), d, _ptr(y))
+    if st:
+        raise OracleError(st, "dag_values")
+    return y
+
+
+def absorption_csr(in_ptr, in_idx, outdeg, key):
+    in_ptr = np.ascontiguousarray(in_ptr, dtype=np.int64)
+    in_idx = np.ascontiguousarray(in_idx if len(in_idx) else [0], dtype=np.int32)
+    outdeg = np.ascontiguousarray(outdeg, dtype=np.int32)
+    key = np.ascontiguousarray(key, dtype=np.float64)
+    n = len(outdeg)
+    failed = np.zeros(n, dtype=np.uint8)
+    a = np.zeros(n, dtype=np.float64)
+    st = _load().or_absorption(n, _ptr(in_ptr), _ptr(in_idx), _ptr(outdeg), _ptr(failed),
+                               _ptr(key), _ptr(a))
+    if st:
+        raise OracleError(st, "absorption")
+    return a
 
 
 def centrality(g: Graph, x: np.ndarray, p) -> np.ndarray:

@@ -15,6 +15,10 @@
  *                      chain / star / tournament closed forms, contraction
  *                      bound against or_pagerank_exact.
  *   or_pagerank_exact  pinned: the same dense solve and closed forms.
+ *   or_dag_values      pinned: dense solve of (I - d A) y = 1, chain and star
+ *                      closed forms, and y / sum y = or_pagerank_exact.
+ *   or_absorption      pinned: dense solve of (I - A) a = 1/n, chain and star
+ *                      closed forms, the mass of the sinks sums to 1.
  *   or_centrality      pinned: hand examples, monotonicity, limits.
  */
 #include "ffg_oracle.h"
@@ -352,6 +356,50 @@ int or_pagerank_exact(int64_t n, const int64_t *in_ptr, const int32_t *in_idx,
     for (int64_t v = 0; v < n; ++v) sum = neumaier_add(sum, x[v], &comp);
     sum += comp;
     for (int64_t v = 0; v < n; ++v) x[v] = x[v] / sum;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* the same recurrence, unnormalised and for any damping in [0, 1]:          */
+/* y[v] = 1 + d * sum_{u -> v} y[u] / outdeg[u], nodes in descending key      */
+/* (every edge runs to a strictly smaller key, so that order is topological) */
+/* ------------------------------------------------------------------------ */
+
+int or_dag_values(int64_t n, const int64_t *in_ptr, const int32_t *in_idx,
+                  const int32_t *outdeg, const uint8_t *failed, const double *node_fit,
+                  double d, double *y)
+{
+    if (n <= 0 || !(d >= 0.0 && d <= 1.0)) return OR_BAD_ARG;
+    keyed *order = (keyed *)malloc(sizeof(keyed) * (size_t)n);
+    if (!order) return OR_NO_MEMORY;
+    for (int64_t v = 0; v < n; ++v) {
+        order[v].key = failed[v] ? INFINITY : node_fit[v];
+        order[v].id = v;
+    }
+    qsort(order, (size_t)n, sizeof(keyed), cmp_desc);
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t v = order[k].id;
+        double s = 0.0;
+        for (int64_t e = in_ptr[v]; e < in_ptr[v + 1]; ++e)
+            s += y[in_idx[e]] / (double)outdeg[in_idx[e]];
+        y[v] = 1.0 + d * s;
+    }
+    free(order);
+    return OR_OK;
+}
+
+/* A walk starts at a uniformly random node and moves to a uniformly random   */
+/* strictly better neighbour (an out-edge) until it reaches a node without    */
+/* one.  a[v] = probability that it passes v; at a node without out-edges     */
+/* the probability that it ends there (Sec. VII-B: the chance of arriving in  */
+/* a minimum).  a = y / n for d = 1.                                          */
+int or_absorption(int64_t n, const int64_t *in_ptr, const int32_t *in_idx,
+                  const int32_t *outdeg, const uint8_t *failed, const double *node_fit,
+                  double *a)
+{
+    int st = or_dag_values(n, in_ptr, in_idx, outdeg, failed, node_fit, 1.0, a);
+    if (st) return st;
+    for (int64_t v = 0; v < n; ++v) a[v] = a[v] / (double)n;
     return OR_OK;
 }
 

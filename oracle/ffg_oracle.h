@@ -77,6 +77,18 @@ int or_pagerank_exact(int64_t n, const int64_t *in_ptr, const int32_t *in_idx,
                       const int32_t *outdeg, const uint8_t *failed, const double *node_fit,
                       double alpha, double *x);
 
+/* y[v] = 1 + d * sum_{u -> v} y[u] / outdeg[u] in topological order, d in
+ * [0, 1]; y / sum y is or_pagerank_exact's result for d < 1. */
+int or_dag_values(int64_t n, const int64_t *in_ptr, const int32_t *in_idx,
+                  const int32_t *outdeg, const uint8_t *failed, const double *node_fit,
+                  double d, double *y);
+
+/* Probability that a walk from a uniformly random node, moving to uniformly
+ * random better neighbours, passes each node (ends there, at sinks). */
+int or_absorption(int64_t n, const int64_t *in_ptr, const int32_t *in_idx,
+                  const int32_t *outdeg, const uint8_t *failed, const double *node_fit,
+                  double *a);
+
 /* C_p for every threshold p[k] (fractions, e.g. 0.05). */
 int or_centrality(int64_t n, const uint8_t *is_min, const double *node_fit, const double *x,
                   double f_opt, const double *p, int32_t n_p, double *cp);

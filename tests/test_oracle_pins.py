@@ -287,3 +287,68 @@ def test_centrality_properties():
     gc = oracle.build(chain, np.arange(6, 0, -1, dtype=np.float64), oracle.ADJACENT)
     assert np.all(oracle.centrality(gc, oracle.pagerank_exact(gc), ps) == 1.0)
     assert spec.n_raw == 2162688
+
+
+# ---------------------------------------------------------------- exact DAG solve, absorbing walk
+
+def _dense_A(g):
+    """A[v, u] = 1/outdeg(u) for every edge u -> v."""
+    A = np.zeros((g.n_nodes, g.n_nodes))
+    for u in range(g.n_nodes):
+        for v in g.out_idx[g.out_ptr[u]:g.out_ptr[u + 1]]:
+            A[v, u] += 1.0 / g.outdeg[u]
+    return A
+
+
+@pytest.mark.parametrize("d", [0.0, 0.5, 0.85, 1.0])
+def test_dag_values_dense_solve(d):
+    """(I - d A) y = 1 solved densely; y / sum y is the exact PageRank."""
+    for k, spec in enumerate(fi.tiny_spaces(5, seed0=9100, max_raw=1200)):
+        f = fi.runtimes(spec, seed=k + 31, fail_frac=(0.03, 0.3, 0.7)[k % 3])
+        g = oracle.build(spec, f, oracle.HAMMING if k % 2 else oracle.ADJACENT)
+        y = oracle.dag_values(g, d)
+        ref = np.linalg.solve(np.eye(g.n_nodes) - d * _dense_A(g), np.ones(g.n_nodes))
+        assert np.abs(y - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+        if d < 1.0:
+            assert np.abs(y / y.sum() - oracle.pagerank_exact(g, d)).sum() < 1e-14
+
+
+def test_absorption_dense_solve_and_mass():
+    """(I - A) a = 1/n; every walk ends at a node without out-edges, so their
+    probabilities sum to 1."""
+    for k, spec in enumerate(fi.tiny_spaces(6, seed0=9200, max_raw=1500)):
+        f = fi.runtimes(spec, seed=k + 41, fail_frac=(0.03, 0.3, 0.7)[k % 3],
+                        quantum=0.5 if k % 2 else None)
+        g = oracle.build(spec, f, oracle.HAMMING if k % 2 else oracle.ADJACENT)
+        a = oracle.absorption(g)
+        n = g.n_nodes
+        ref = np.linalg.solve(np.eye(n) - _dense_A(g), np.full(n, 1.0 / n))
+        assert np.abs(a - ref).max() < 1e-13
+        assert abs(a[g.outdeg == 0].sum() - 1.0) < 1e-13
+        assert (a >= 1.0 / n - 1e-15).all()     # every node is at least a start
+
+
+def test_absorption_closed_forms():
+    # chain 0 -> 1 -> ... -> n-1 (strictly decreasing fitness): a_k = (k+1)/n,
+    # the last node collects every walk
+    n = 7
+    spec = _one_param(list(range(n)))
+    g = oracle.build(spec, np.arange(n, 0, -1, dtype=np.float64), oracle.ADJACENT)
+    assert np.abs(oracle.absorption(g) - np.arange(1, n + 1) / n).max() < 1e-15
+    # out-star: centre -> k leaves, each leaf 1/n + (1/n)/k
+    for k in (1, 3, 8):
+        ins = [[]] + [[0] for _ in range(k)]
+        ptr, idx = brute.csr(ins)
+        deg = np.array([k] + [0] * k)
+        key = np.array([2.0] + [1.0] * k)
+        n = k + 1
+        want = np.array([1.0 / n] + [1.0 / n + 1.0 / (n * k)] * k)
+        assert np.abs(oracle.absorption_csr(ptr, idx, deg, key) - want).max() < 1e-15
+    # in-star: k leaves -> centre: the centre collects everything
+    k = 5
+    ins = [list(range(1, k + 1))] + [[] for _ in range(k)]
+    ptr, idx = brute.csr(ins)
+    deg = np.array([0] + [1] * k)
+    key = np.array([1.0] + [2.0] * k)
+    a = oracle.absorption_csr(ptr, idx, deg, key)
+    assert abs(a[0] - 1.0) < 1e-15 and np.abs(a[1:] - 1.0 / (k + 1)).max() < 1e-15
