@@ -249,6 +249,33 @@ ffg_status pagerank_solve_static(const ffg_graph *g, double damping, double tol,
                                  int32_t max_iter, ffg_prec prec, void *ranks, int init,
                                  int32_t *iters_out, double *residual_out, void *stream);
 
+/* ---- exact solve on the DAG (Sec. VII-B) ----
+ * The FFG has no cycles (every edge goes to a strictly better key), so
+ *   y[v] = 1 + damping * sum_{u -> v} y[u] / outdeg[u]
+ * is solved exactly in one pass over the nodes in topological order, level
+ * by level: a level is the set of nodes whose in-neighbours are all done;
+ * there are (longest improving path + 1) levels.  FP64, each in-list summed
+ * in CSR order with one rounding per operation, so y does not depend on the
+ * schedule.  Modes:
+ * - FFG_DAG_VALUES: ranks = y, damping in [0, 1];
+ * - FFG_DAG_PAGERANK: ranks = y / sum y, damping in (0, 1): the exact
+ *   PageRank, the fixed point that pagerank_solve iterates towards;
+ * - FFG_DAG_ABSORB: damping must be 1; ranks = y / n_nodes, the probability
+ *   that a walk from a uniformly random node, moving to a uniformly random
+ *   better neighbour, passes each node; at the nodes without out-edges
+ *   (minima, and failed points without a better valid neighbour) the
+ *   probability of ending there, which sum to 1.  Their C_p is
+ *   centrality_proportion with FFG_F64.
+ * Needs the out-edges as well as the in-edges.  ranks: DEVICE, n_nodes
+ * doubles.  levels_out (HOST, may be NULL): the number of levels; when
+ * non-NULL the call synchronises `stream` and reports FFG_ERR_TIMEOUT if a
+ * bounded device wait expired.  workspace: DEVICE, dag_workspace_bytes. */
+typedef enum { FFG_DAG_VALUES = 0, FFG_DAG_PAGERANK = 1, FFG_DAG_ABSORB = 2 } ffg_dag_mode;
+
+size_t dag_workspace_bytes(int64_t n_nodes);
+ffg_status dag_solve(const ffg_graph *g, double damping, ffg_dag_mode mode, double *ranks,
+                     void *workspace, size_t ws_bytes, int32_t *levels_out, void *stream);
+
 /* ---- batched PageRank: many solves in one persistent launch ----
  * A job is one PageRank solve (same definition and stopping rules as
  * pagerank_solve): graph g (host struct with DEVICE arrays), damping, tol,

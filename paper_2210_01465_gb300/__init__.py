@@ -105,7 +105,8 @@ ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
                 "ffg_build_batch_fill", "ffg_build_batch_rerun", "ffg_build_batch_query",
                 "pagerank_workspace_bytes", "pagerank_prepare", "pagerank_solve",
                 "pagerank_solve_static",
-                "pagerank_query", "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
+                "pagerank_query", "dag_workspace_bytes", "dag_solve",
+                "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
                 "pagerank_batch_plan_tuned",
                 "pagerank_batch_run", "pagerank_batch_query",
                 "centrality_workspace_bytes", "centrality_proportion",
@@ -143,6 +144,9 @@ def load(path: str | None = None):
     lib.pagerank_batch_workspace_bytes.argtypes = [P(ffg_pr_job), i32, C.c_int]
     lib.pagerank_batch_workspace_bytes.restype = sz
     lib.pagerank_batch_plan.argtypes = [P(ffg_pr_job), i32, C.c_int, vp, sz, P(ffg_pr_batch), vp]
+    lib.dag_workspace_bytes.restype = sz
+    lib.dag_workspace_bytes.argtypes = [C.c_int64]
+    lib.dag_solve.argtypes = [P(ffg_graph), C.c_double, C.c_int, vp, vp, sz, P(C.c_int32), vp]
     lib.ffg_build_batch_workspace_bytes.restype = sz
     lib.ffg_build_batch_workspace_bytes.argtypes = [P(ffg_build_job), i32]
     lib.ffg_build_batch_count.argtypes = [P(ffg_build_job), i32, vp, sz, P(ffg_build_batch), vp]
@@ -399,6 +403,35 @@ def build_graph(space: Space, fitness, nbh: int = HAMMING, fail_thr: float = 1e1
            "ffg_build_fill")
     g.nbh = nbh
     return g
+
+
+DAG_VALUES, DAG_PAGERANK, DAG_ABSORB = 0, 1, 2
+
+
+def dag_workspace_bytes(n_nodes: int) -> int:
+    return int(load().dag_workspace_bytes(int(n_nodes)))
+
+
+def dag_solve(g: "ffg_graph", damping: float, mode: int, ranks: int, ws: int, ws_bytes: int,
+              stream: int = 0):
+    """Returns (status, levels)."""
+    lv = C.c_int32(0)
+    s = load().dag_solve(C.byref(g), float(damping), int(mode), C.c_void_p(ranks),
+                         C.c_void_p(ws), int(ws_bytes), C.byref(lv), C.c_void_p(stream))
+    return int(s), int(lv.value)
+
+
+def dag(g: "Graph", damping: float = 0.85, mode: int = DAG_PAGERANK, stream=None):
+    """Exact solve on the DAG; returns (float64 tensor, levels)."""
+    torch = _torch()
+    dev = g.out_ptr.device
+    out = torch.empty(g.n_nodes, dtype=torch.float64, device=dev)
+    need = dag_workspace_bytes(g.n_nodes)
+    ws = workspace(need, dev)
+    st, lv = dag_solve(g.c, damping, mode, out.data_ptr(), ws.data_ptr(), need,
+                       _stream_handle(stream))
+    _check(st, "dag_solve")
+    return out, lv
 
 
 class BuildBatch:

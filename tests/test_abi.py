@@ -155,3 +155,17 @@ def test_batched_build_validated_on_host(lib):
                                      None) == ffg.FFG_ERR_NO_MEMORY
     assert lib.ffg_build_batch_rerun(C.byref(ffg.ffg_build_batch()), None) == \
         ffg.FFG_ERR_INVALID_ARG
+
+
+def test_dag_solve_validated_on_host(lib):
+    g = ffg.ffg_graph()
+    g.n_nodes, g.n_edges = 10, 5
+    g.in_ptr = g.out_ptr = g.in_idx = g.out_idx = g.outdeg = 256
+    need = ffg.dag_workspace_bytes(10)
+    assert need > 0
+    assert ffg.dag_solve(ffg.ffg_graph(), 0.85, ffg.DAG_PAGERANK, 256, 256, need)[0] == 1
+    for d, mode in ((1.0, ffg.DAG_PAGERANK), (0.0, ffg.DAG_PAGERANK), (0.85, ffg.DAG_ABSORB),
+                    (1.5, ffg.DAG_VALUES), (-0.1, ffg.DAG_VALUES), (0.5, 7)):
+        assert ffg.dag_solve(g, d, mode, 256, 256, need)[0] == ffg.FFG_ERR_INVALID_ARG
+    assert ffg.dag_solve(g, 0.85, ffg.DAG_PAGERANK, 256, 258, need)[0] == ffg.FFG_ERR_INVALID_ARG
+    assert ffg.dag_solve(g, 0.85, ffg.DAG_PAGERANK, 256, 256, 16)[0] == ffg.FFG_ERR_NO_MEMORY

@@ -483,3 +483,62 @@ def test_batched_build_rerun_refuses_changed_sizes():
     np.testing.assert_array_equal(_np(bb.graphs[0].out_ptr), before[0])
     np.testing.assert_array_equal(_np(bb.graphs[0].out_idx), before[1])
     assert_same_graph(bb.graphs[1], og_b)
+
+
+def _longest_path(og):
+    key = np.where(og.failed, np.inf, og.node_fit)
+    depth = np.zeros(og.n_nodes, dtype=np.int64)
+    for v in np.argsort(-key, kind="stable"):
+        a, b = og.in_ptr[v], og.in_ptr[v + 1]
+        if b > a:
+            depth[v] = 1 + depth[og.in_idx[a:b]].max()
+    return int(depth.max())
+
+
+@pytest.mark.parametrize("nbh", ["hamming", "adjacent"])
+def test_dag_solve_bit_exact(nbh):
+    """The level-by-level exact solve reproduces the sequential one bit for
+    bit (y for d < 1 and d = 1, and the absorbing walk); its PageRank mode is
+    the exact PageRank and the power iteration's limit; its level count is
+    the longest improving path + 1."""
+    cases = [(fi.single_small(), 1, 0.03), (fi.pnpoly_space(), 2, 0.7),
+             (fi.gemm_space(), 3, 0.3)]
+    cases += [(sp, 20 + k, (0.03, 0.3, 0.7)[k % 3])
+              for k, sp in enumerate(fi.tiny_spaces(8, seed0=15000, max_raw=3000))]
+    for spec, seed, fail in cases:
+        f = fi.runtimes(spec, seed, fail_frac=fail)
+        try:
+            og = oracle.build(spec, f, NBH[nbh][1])
+        except oracle.OracleError:      # a space without valid configurations
+            continue
+        g, fd = run_build(spec, f, nbh)
+        for d in (0.5, 0.85, 1.0):
+            y, lv = ffg.dag(g, d, ffg.DAG_VALUES)
+            np.testing.assert_array_equal(_np(y), oracle.dag_values(og, d))
+        assert lv == _longest_path(og) + 1
+        a, _ = ffg.dag(g, 1.0, ffg.DAG_ABSORB)
+        ae = oracle.absorption(og)
+        np.testing.assert_array_equal(_np(a), ae)
+        x, _ = ffg.dag(g, 0.85, ffg.DAG_PAGERANK)
+        assert np.abs(_np(x) - oracle.pagerank_exact(og, 0.85)).sum() <= 1e-14
+        if og.is_min.any():
+            p = [0.0, 0.05, 0.2]
+            cp = ffg.centrality(g, fd, a, p)
+            assert np.abs(cp - oracle.centrality(og, ae, p)).max() <= 1e-12
+
+
+def test_dag_solve_full_size():
+    """Both neighbourhoods of the single large space: bit-exact y, and the
+    exact PageRank agrees with the FP64 power iteration."""
+    spec = fi.single_large()
+    f = fi.runtimes(spec, 1)
+    for nbh in ("hamming", "adjacent"):
+        og = oracle.build(spec, f, NBH[nbh][1])
+        g, _ = run_build(spec, f, nbh)
+        y, lv = ffg.dag(g, 0.85, ffg.DAG_VALUES)
+        np.testing.assert_array_equal(_np(y), oracle.dag_values(og, 0.85))
+        x, _ = ffg.dag(g, 0.85, ffg.DAG_PAGERANK)
+        xp, it, res, conv = ffg.pagerank(g, 0.85, 1e-13, prec=ffg.F64)
+        assert conv and np.abs(_np(x) - _np(xp)).sum() <= 1e-11
+        a, _ = ffg.dag(g, 1.0, ffg.DAG_ABSORB)
+        np.testing.assert_array_equal(_np(a), oracle.absorption(og))
