@@ -348,9 +348,12 @@ def run_gpu(args):
         cpu = {"value": u / s, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": ORACLE_SAMPLE + f" ({s:.1f} s)"}
 
-    scale = None
+    scale = exact = None
     if not args.no_batched:
         scale = run_scale(dev, stream)
+        f64_solve = {n: (statistics.mean(ea.elapsed_time(eb) for (m, ea, eb, _) in recs64 if m == n),
+                         statistics.mean(it for (m, _, _, it) in recs64 if m == n)) for n in nbhs}
+        exact = run_exact(ffg, graphs, fd, dev, stream, f64_solve)
     batched = sweep = None
     if not args.no_batched:
         batched = run_batched(dev, stream, steps=max(3, args.steps // 10), warmup=1,
@@ -383,6 +386,7 @@ def run_gpu(args):
                          "launch_ms": statistics.mean(durs),
                          "l2_resident": True},
             "beyond_l2": scale,
+            "exact_dag": exact,
             "batched": batched,
             "sweep": sweep,
             "cpu_baseline": cpu,
@@ -397,6 +401,44 @@ def run_gpu(args):
 
 
 BATCH_P = [0.01, 0.02, 0.05, 0.10, 0.20]
+
+
+def run_exact(ffg, graphs, fd, dev, stream, f64_solve, reps=3):
+    """The exact solve on the DAG (level by level) for both FFGs of the single
+    large space: the exact FP64 PageRank next to the FP64 power iteration,
+    and the absorbing improving walk with the C_p of its arrival
+    probabilities."""
+    import torch
+    sh = stream.cuda_stream
+    out = {}
+    for name, nbh in (("hamming", ffg.HAMMING), ("adjacent", ffg.ADJACENT)):
+        g = graphs[nbh]
+        need = ffg.dag_workspace_bytes(g.n_nodes)
+        ws = ffg.workspace(need, dev)
+        x = torch.empty(g.n_nodes, dtype=torch.float64, device=dev)
+        ts = []
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, lv = ffg.dag_solve(g.c, DAMPING, ffg.DAG_PAGERANK, x.data_ptr(), ws.data_ptr(),
+                                   need, sh)
+            e1.record(stream)
+            e1.synchronize()
+            assert st == 0, st
+            ts.append(e0.elapsed_time(e1))
+        a = torch.empty_like(x)
+        st, _ = ffg.dag_solve(g.c, 1.0, ffg.DAG_ABSORB, a.data_ptr(), ws.data_ptr(), need, sh)
+        assert st == 0, st
+        cp = ffg.centrality(g, fd, a, P_LIST)
+        out[name] = {"levels": lv, "ms": statistics.median(ts[1:]),
+                     "edges_per_s": g.n_edges / (statistics.median(ts[1:]) / 1e3),
+                     "f64_power_iteration_ms": f64_solve[nbh][0],
+                     "f64_power_iterations": f64_solve[nbh][1],
+                     "absorb_cp": [round(float(v), 6) for v in cp]}
+    out["workload"] = ("single large space, exact FP64 PageRank by one level-by-level pass "
+                       "over the DAG (levels = longest improving path + 1); absorb_cp: C_p at "
+                       "1/5/10 % of the absorbing improving walk's arrival probabilities")
+    return out
 
 
 def run_scale(dev, stream, reps=3):

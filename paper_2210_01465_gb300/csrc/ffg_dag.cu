@@ -9,11 +9,14 @@
 // neighbour for the next level.  The number of levels is the longest
 // improving path + 1.
 //
-// One cooperative persistent launch: every level is a grid-stride pass over
-// the current queue, then a bounded grid barrier (FFG_ERR_TIMEOUT on
-// expiry).  One thread per queued node sums its in-list in CSR order in FP64
-// with one rounding per operation (no fused multiply-add), so y does not
-// depend on the schedule and equals the sequential solve bit for bit.
+// One cooperative persistent launch: every level is a grid-stride pass of
+// warps over the current queue, then a bounded grid barrier (FFG_ERR_TIMEOUT
+// on expiry).  One warp per queued node: the lanes gather and divide 32
+// in-neighbours at a time and the terms are added one by one in CSR order
+// (FP64, one rounding per operation, no fused multiply-add), so y does not
+// depend on the schedule and equals the sequential solve bit for bit; the
+// lanes then count down 32 out-neighbours at a time and queue, with one
+// atomic per warp, those that became ready.
 // Values written at earlier levels by other blocks are read through L2
 // (ld.cg), never from a possibly stale L1 line.
 #include "ffg_internal.cuh"
@@ -166,17 +169,37 @@ __global__ void __launch_bounds__(kDagThreads) k_dag(DagArgs a) {
         if (blockIdx.x == 0 && threadIdx.x == 0) ctl->tail[clr] = 0;  // used as `nxt` next level
         const int32_t *qc = q[level & 1];
         int32_t *qn = q[(level + 1) & 1];
-        for (int64_t i = gid; i < F; i += stride) {
+        const int lane = threadIdx.x & 31;
+        const int64_t warps = stride >> 5;
+        for (int64_t i = gid >> 5; i < F; i += warps) {
             const int32_t v = __ldcg(qc + i);
+            const int64_t e0 = a.in_ptr[v], e1 = a.in_ptr[v + 1];
             double s = 0.0;
-            for (int64_t e = a.in_ptr[v]; e < a.in_ptr[v + 1]; ++e) {
-                const int32_t u = a.in_idx[e];
-                s = __dadd_rn(s, __ddiv_rn(__ldcg(a.y + u), static_cast<double>(a.outdeg[u])));
+            for (int64_t b = e0; b < e1; b += 32) {
+                double term = 0.0;
+                if (b + lane < e1) {
+                    const int32_t u = a.in_idx[b + lane];
+                    term = __ddiv_rn(__ldcg(a.y + u), static_cast<double>(a.outdeg[u]));
+                }
+                const int m = e1 - b < 32 ? static_cast<int>(e1 - b) : 32;
+                for (int k = 0; k < m; ++k) s = __dadd_rn(s, __shfl_sync(0xffffffffu, term, k));
             }
-            a.y[v] = __dadd_rn(1.0, __dmul_rn(a.d, s));
-            for (int64_t e = a.out_ptr[v]; e < a.out_ptr[v + 1]; ++e) {
-                const int32_t t = a.out_idx[e];
-                if (atomicSub(&a.w.remaining[t], 1) == 1) qn[atomicAdd(&ctl->tail[nxt], 1u)] = t;
+            if (lane == 0) a.y[v] = __dadd_rn(1.0, __dmul_rn(a.d, s));
+            const int64_t o1 = a.out_ptr[v + 1];
+            for (int64_t b = a.out_ptr[v]; b < o1; b += 32) {
+                int32_t t = -1;
+                bool ready = false;
+                if (b + lane < o1) {
+                    t = a.out_idx[b + lane];
+                    ready = atomicSub(&a.w.remaining[t], 1) == 1;
+                }
+                const unsigned mask = __ballot_sync(0xffffffffu, ready);
+                if (mask) {
+                    unsigned pos = 0;
+                    if (lane == 0) pos = atomicAdd(&ctl->tail[nxt], static_cast<unsigned>(__popc(mask)));
+                    pos = __shfl_sync(0xffffffffu, pos, 0);
+                    if (ready) qn[pos + __popc(mask & ((1u << lane) - 1u))] = t;
+                }
             }
         }
         ++phase;
