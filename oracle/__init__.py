@@ -106,6 +106,10 @@ def _load():
                                           C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
             lib.or_absorption.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.or_splitmix64.restype = C.c_uint64
+            lib.or_splitmix64.argtypes = [C.c_uint64]
+            lib.or_walks.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
+                                     C.c_int64, C.c_void_p, C.POINTER(C.c_int64)]
             _lib = lib
     return _lib
 
@@ -264,6 +268,30 @@ def absorption_csr(in_ptr, in_idx, outdeg, key):
     if st:
         raise OracleError(st, "absorption")
     return a
+
+
+def splitmix64(x: int) -> int:
+    return int(_load().or_splitmix64(int(x) & 0xFFFFFFFFFFFFFFFF))
+
+
+def walks_csr(out_ptr, out_idx, outdeg, seed: int, n_walks: int):
+    """Simulated improving walks; returns (counts per node, total steps)."""
+    out_ptr = np.ascontiguousarray(out_ptr, dtype=np.int64)
+    out_idx = np.ascontiguousarray(out_idx if len(out_idx) else [0], dtype=np.int32)
+    outdeg = np.ascontiguousarray(outdeg, dtype=np.int32)
+    n = len(outdeg)
+    counts = np.zeros(n, dtype=np.uint64)
+    steps = C.c_int64(0)
+    st = _load().or_walks(n, _ptr(out_ptr), _ptr(out_idx), _ptr(outdeg),
+                          int(seed) & 0xFFFFFFFFFFFFFFFF, int(n_walks), _ptr(counts),
+                          C.byref(steps))
+    if st:
+        raise OracleError(st, "walks")
+    return counts, int(steps.value)
+
+
+def walks(g: Graph, seed: int, n_walks: int):
+    return walks_csr(g.out_ptr, g.out_idx, g.outdeg, seed, n_walks)
 
 
 def centrality(g: Graph, x: np.ndarray, p) -> np.ndarray:

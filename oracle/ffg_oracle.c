@@ -19,6 +19,9 @@
  *                      closed forms, and y / sum y = or_pagerank_exact.
  *   or_absorption      pinned: dense solve of (I - A) a = 1/n, chain and star
  *                      closed forms, the mass of the sinks sums to 1.
+ *   or_walks           pinned: the SplitMix64 reference outputs, a chain (every
+ *                      walk ends at its end), arrival frequencies within
+ *                      binomial bounds of or_absorption.
  *   or_centrality      pinned: hand examples, monotonicity, limits.
  */
 #include "ffg_oracle.h"
@@ -400,6 +403,51 @@ int or_absorption(int64_t n, const int64_t *in_ptr, const int32_t *in_idx,
     int st = or_dag_values(n, in_ptr, in_idx, outdeg, failed, node_fit, 1.0, a);
     if (st) return st;
     for (int64_t v = 0; v < n; ++v) a[v] = a[v] / (double)n;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* simulated improving walks (Sec. VII-B: a random walk on the FFG mimics a  */
+/* randomised first-improvement local search)                                */
+/* ------------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): output for state x, the
+ * state having been advanced by the golden gamma first. */
+static uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t or_splitmix64(uint64_t x) { return splitmix64(x); }
+
+/* index in [0, m) from a draw: the high 32 bits scaled by m */
+static uint64_t pick(uint64_t draw, uint64_t m) { return ((draw >> 32) * m) >> 32; }
+
+int or_walks(int64_t n, const int64_t *out_ptr, const int32_t *out_idx, const int32_t *outdeg,
+             uint64_t seed, int64_t n_walks, uint64_t *counts, int64_t *steps)
+{
+    if (n <= 0 || n_walks < 0) return OR_BAD_ARG;
+    for (int64_t v = 0; v < n; ++v) counts[v] = 0;
+    int64_t total = 0;
+    for (int64_t j = 0; j < n_walks; ++j) {
+        /* walk j: the k-th draw is the k-th output of the SplitMix64 stream
+         * whose state starts at splitmix64(seed ^ j) */
+        const uint64_t s0 = splitmix64(seed ^ (uint64_t)j);
+        uint64_t k = 0;
+        int64_t v = (int64_t)pick(splitmix64(s0 + k * 0x9e3779b97f4a7c15ULL), (uint64_t)n);
+        while (outdeg[v] > 0) {
+            ++k;
+            const uint64_t i = pick(splitmix64(s0 + k * 0x9e3779b97f4a7c15ULL),
+                                    (uint64_t)outdeg[v]);
+            v = out_idx[out_ptr[v] + (int64_t)i];
+            ++total;
+        }
+        counts[v] += 1;
+    }
+    if (steps) *steps = total;
     return OR_OK;
 }
 

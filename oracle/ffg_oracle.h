@@ -89,6 +89,15 @@ int or_absorption(int64_t n, const int64_t *in_ptr, const int32_t *in_idx,
                   const int32_t *outdeg, const uint8_t *failed, const double *node_fit,
                   double *a);
 
+/* SplitMix64 output for state x (the state advanced by the golden gamma). */
+uint64_t or_splitmix64(uint64_t x);
+
+/* n_walks improving walks: walk j starts at a uniformly random node and moves
+ * to a uniformly random out-neighbour until a node without out-edges;
+ * counts[v] = walks that ended at v; *steps = moves made. */
+int or_walks(int64_t n, const int64_t *out_ptr, const int32_t *out_idx, const int32_t *outdeg,
+             uint64_t seed, int64_t n_walks, uint64_t *counts, int64_t *steps);
+
 /* C_p for every threshold p[k] (fractions, e.g. 0.05). */
 int or_centrality(int64_t n, const uint8_t *is_min, const double *node_fit, const double *x,
                   double f_opt, const double *p, int32_t n_p, double *cp);

@@ -352,3 +352,42 @@ def test_absorption_closed_forms():
     key = np.array([1.0] + [2.0] * k)
     a = oracle.absorption_csr(ptr, idx, deg, key)
     assert abs(a[0] - 1.0) < 1e-15 and np.abs(a[1:] - 1.0 / (k + 1)).max() < 1e-15
+
+
+# ---------------------------------------------------------------- simulated improving walks
+
+def test_splitmix64_reference_outputs():
+    """The first outputs of SplitMix64 from state 0 (the published reference
+    sequence)."""
+    g = 0x9E3779B97F4A7C15
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert [oracle.splitmix64((k * g) & 0xFFFFFFFFFFFFFFFF) for k in range(3)] == want
+
+
+def test_walks_chain_and_mass():
+    n = 6
+    spec = _one_param(list(range(n)))
+    g = oracle.build(spec, np.arange(n, 0, -1, dtype=np.float64), oracle.ADJACENT)
+    counts, steps = oracle.walks(g, seed=3, n_walks=1000)
+    assert counts[-1] == 1000 and counts[:-1].sum() == 0
+    # a walk from node k makes n-1-k moves; starts are uniform
+    assert 0 < steps < 1000 * (n - 1)
+
+
+def test_walk_frequencies_match_absorption():
+    """Arrival frequencies of 200,000 walks against the exact arrival
+    probabilities, within 5 binomial standard deviations at every sink."""
+    spaces = [fi.single_small(), fi.conv_mi50_space()] + fi.tiny_spaces(3, seed0=9300,
+                                                                         max_raw=1500)
+    for k, spec in enumerate(spaces):
+        f = fi.runtimes(spec, seed=k + 51, fail_frac=(0.03, 0.3)[k % 2])
+        g = oracle.build(spec, f, oracle.HAMMING if k % 2 else oracle.ADJACENT)
+        W = 200_000
+        counts, _ = oracle.walks(g, seed=100 + k, n_walks=W)
+        a = oracle.absorption(g)
+        sinks = g.outdeg == 0
+        assert counts[~sinks].sum() == 0 and counts.sum() == W
+        p = a[sinks]
+        freq = counts[sinks] / W
+        sd = np.sqrt(np.clip(p * (1 - p), 0.0, None) / W)
+        assert (np.abs(freq - p) <= 5 * sd + 1e-12).all()
