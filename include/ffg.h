@@ -276,6 +276,24 @@ size_t dag_workspace_bytes(int64_t n_nodes);
 ffg_status dag_solve(const ffg_graph *g, double damping, ffg_dag_mode mode, double *ranks,
                      void *workspace, size_t ws_bytes, int32_t *levels_out, void *stream);
 
+/* ---- simulated improving walks (Sec. VII-B) ----
+ * A random walk on the FFG mimics a randomised first-improvement local
+ * search.  walk_simulate runs n_walks walks: walk j starts at a uniformly
+ * random node and moves to a uniformly random out-neighbour until it reaches
+ * a node without out-edges; counts[v] (DEVICE, n_nodes uint64, overwritten)
+ * = walks that ended at v.  Walk j's k-th draw (k = 0 for the start) is the
+ * k-th output of the SplitMix64 stream whose state starts at
+ * splitmix64(seed ^ j); a draw x picks index ((x >> 32) * m) >> 32 among m
+ * choices.  The counts are reproducible bit for bit, and their expectation
+ * is n_walks times dag_solve's FFG_DAG_ABSORB.  workspace: DEVICE, 256-byte
+ * aligned, walk_workspace_bytes().  steps_out (HOST, may be NULL): moves
+ * made; when non-NULL the call synchronises `stream` and reports
+ * FFG_ERR_INVALID_ARG if a walk made n_nodes moves (a graph with a cycle;
+ * impossible on an FFG; such a walk stops uncounted). */
+size_t walk_workspace_bytes(void);
+ffg_status walk_simulate(const ffg_graph *g, uint64_t seed, int64_t n_walks, uint64_t *counts,
+                         void *workspace, size_t ws_bytes, int64_t *steps_out, void *stream);
+
 /* ---- batched PageRank: many solves in one persistent launch ----
  * A job is one PageRank solve (same definition and stopping rules as
  * pagerank_solve): graph g (host struct with DEVICE arrays), damping, tol,

@@ -106,6 +106,7 @@ ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
                 "pagerank_workspace_bytes", "pagerank_prepare", "pagerank_solve",
                 "pagerank_solve_static",
                 "pagerank_query", "dag_workspace_bytes", "dag_solve",
+                "walk_workspace_bytes", "walk_simulate",
                 "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
                 "pagerank_batch_plan_tuned",
                 "pagerank_batch_run", "pagerank_batch_query",
@@ -144,6 +145,10 @@ def load(path: str | None = None):
     lib.pagerank_batch_workspace_bytes.argtypes = [P(ffg_pr_job), i32, C.c_int]
     lib.pagerank_batch_workspace_bytes.restype = sz
     lib.pagerank_batch_plan.argtypes = [P(ffg_pr_job), i32, C.c_int, vp, sz, P(ffg_pr_batch), vp]
+    lib.walk_workspace_bytes.restype = sz
+    lib.walk_workspace_bytes.argtypes = []
+    lib.walk_simulate.argtypes = [P(ffg_graph), C.c_uint64, C.c_int64, vp, vp, sz,
+                                  P(C.c_int64), vp]
     lib.dag_workspace_bytes.restype = sz
     lib.dag_workspace_bytes.argtypes = [C.c_int64]
     lib.dag_solve.argtypes = [P(ffg_graph), C.c_double, C.c_int, vp, vp, sz, P(C.c_int32), vp]
@@ -432,6 +437,28 @@ def dag(g: "Graph", damping: float = 0.85, mode: int = DAG_PAGERANK, stream=None
                        _stream_handle(stream))
     _check(st, "dag_solve")
     return out, lv
+
+
+def walk_simulate(g: "ffg_graph", seed: int, n_walks: int, counts: int, ws: int,
+                  ws_bytes: int, stream: int = 0):
+    """Returns (status, steps)."""
+    steps = C.c_int64(0)
+    s = load().walk_simulate(C.byref(g), int(seed) & 0xFFFFFFFFFFFFFFFF, int(n_walks),
+                             C.c_void_p(counts), C.c_void_p(ws), int(ws_bytes),
+                             C.byref(steps), C.c_void_p(stream))
+    return int(s), int(steps.value)
+
+
+def walks(g: "Graph", seed: int, n_walks: int, stream=None):
+    """Improving-walk arrival counts (int64 tensor) and the number of moves."""
+    torch = _torch()
+    dev = g.out_ptr.device
+    counts = torch.empty(g.n_nodes, dtype=torch.int64, device=dev)
+    ws = workspace(int(load().walk_workspace_bytes()), dev)
+    st, steps = walk_simulate(g.c, seed, n_walks, counts.data_ptr(), ws.data_ptr(), ws.numel(),
+                              _stream_handle(stream))
+    _check(st, "walk_simulate")
+    return counts, steps
 
 
 class BuildBatch:

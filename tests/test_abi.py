@@ -169,3 +169,15 @@ def test_dag_solve_validated_on_host(lib):
         assert ffg.dag_solve(g, d, mode, 256, 256, need)[0] == ffg.FFG_ERR_INVALID_ARG
     assert ffg.dag_solve(g, 0.85, ffg.DAG_PAGERANK, 256, 258, need)[0] == ffg.FFG_ERR_INVALID_ARG
     assert ffg.dag_solve(g, 0.85, ffg.DAG_PAGERANK, 256, 256, 16)[0] == ffg.FFG_ERR_NO_MEMORY
+
+
+def test_walk_simulate_validated_on_host(lib):
+    g = ffg.ffg_graph()
+    g.n_nodes, g.n_edges = 10, 5
+    g.in_ptr = g.out_ptr = g.in_idx = g.out_idx = g.outdeg = 256
+    assert lib.walk_workspace_bytes() == 256
+    assert ffg.walk_simulate(ffg.ffg_graph(), 1, 10, 256, 256, 256)[0] == 1
+    assert ffg.walk_simulate(g, 1, -1, 256, 256, 256)[0] == ffg.FFG_ERR_INVALID_ARG
+    assert ffg.walk_simulate(g, 1, 10, 0, 256, 256)[0] == ffg.FFG_ERR_INVALID_ARG
+    assert ffg.walk_simulate(g, 1, 10, 256, 258, 256)[0] == ffg.FFG_ERR_INVALID_ARG
+    assert ffg.walk_simulate(g, 1, 10, 256, 256, 8)[0] == ffg.FFG_ERR_NO_MEMORY

@@ -542,3 +542,29 @@ def test_dag_solve_full_size():
         assert conv and np.abs(_np(x) - _np(xp)).sum() <= 1e-11
         a, _ = ffg.dag(g, 1.0, ffg.DAG_ABSORB)
         np.testing.assert_array_equal(_np(a), oracle.absorption(og))
+
+
+def test_walks_bit_exact_and_unbiased():
+    """Simulated improving walks: counts and moves equal the oracle's (same
+    SplitMix64 draws) on paper-shaped spaces and the 1.42M-node space; the
+    arrival frequencies of 10^7 walks on that space lie within binomial
+    bounds of the exact absorbing walk."""
+    cases = [(fi.single_small(), 1, "hamming", 100_000), (fi.pnpoly_space(), 2, "adjacent", 100_000),
+             (fi.gemm_space(), 3, "hamming", 50_000), (fi.single_large(), 1, "hamming", 1_000_000)]
+    for spec, seed, nbh, W in cases:
+        f = fi.runtimes(spec, seed)
+        og = oracle.build(spec, f, NBH[nbh][1])
+        g, _ = run_build(spec, f, nbh)
+        counts, steps = ffg.walks(g, seed=77 + seed, n_walks=W)
+        ce, se = oracle.walks(og, seed=77 + seed, n_walks=W)
+        np.testing.assert_array_equal(_np(counts).astype(np.uint64), ce)
+        assert steps == se
+    W = 10_000_000
+    counts, _ = ffg.walks(g, seed=5, n_walks=W)
+    a, _ = ffg.dag(g, 1.0, ffg.DAG_ABSORB)
+    a = _np(a)
+    sinks = _np(g.outdeg) == 0
+    freq = _np(counts)[sinks] / W
+    p = a[sinks]
+    sd = np.sqrt(np.clip(p * (1 - p), 0.0, None) / W)
+    assert (np.abs(freq - p) <= 6 * sd + 1e-12).all()
