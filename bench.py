@@ -430,6 +430,34 @@ def run_exact(ffg, graphs, fd, dev, stream, f64_solve, reps=3):
         st, _ = ffg.dag_solve(g.c, 1.0, ffg.DAG_ABSORB, a.data_ptr(), ws.data_ptr(), need, sh)
         assert st == 0, st
         cp = ffg.centrality(g, fd, a, P_LIST)
+        # simulated improving walks, checked against the exact arrival probabilities
+        W = 10_000_000
+        wws = ffg.workspace(256, dev)
+        counts = torch.empty(g.n_nodes, dtype=torch.int64, device=dev)
+        tw = []
+        for r in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, moves = ffg.walk_simulate(g.c, 1000 + r, W, counts.data_ptr(), wws.data_ptr(),
+                                          256, sh)
+            e1.record(stream)
+            e1.synchronize()
+            assert st == 0, st
+            tw.append(e0.elapsed_time(e1))
+        sinks = g.outdeg == 0
+        p = a[sinks]
+        freq = counts[sinks].double() / W
+        sd = torch.sqrt(torch.clamp(p * (1 - p), min=0.0) / W)
+        z = float(((freq - p).abs() / torch.clamp(sd, min=1e-300)).max())
+        out[name + "_walks"] = {"walks": W, "moves": moves, "ms": tw[-1],
+                                "moves_per_s": moves / (tw[-1] / 1e3),
+                                "max_z_vs_exact": round(z, 2)}
+        frac, _ = ffg.minima_fraction(g, fd)
+        out[name + "_minima"] = {"n_minima": g.n_minima,
+                                 "frac_opt_quartiles": [round(float(q), 4) for q in
+                                                        torch.quantile(frac, torch.tensor(
+                                                            [0.25, 0.5, 0.75], dtype=frac.dtype,
+                                                            device=dev)).tolist()]}
         out[name] = {"levels": lv, "ms": statistics.median(ts[1:]),
                      "edges_per_s": g.n_edges / (statistics.median(ts[1:]) / 1e3),
                      "f64_power_iteration_ms": f64_solve[nbh][0],
@@ -437,7 +465,9 @@ def run_exact(ffg, graphs, fd, dev, stream, f64_solve, reps=3):
                      "absorb_cp": [round(float(v), 6) for v in cp]}
     out["workload"] = ("single large space, exact FP64 PageRank by one level-by-level pass "
                        "over the DAG (levels = longest improving path + 1); absorb_cp: C_p at "
-                       "1/5/10 % of the absorbing improving walk's arrival probabilities")
+                       "1/5/10 % of the absorbing improving walk's arrival probabilities; "
+                       "*_walks: 10^7 simulated improving walks, max z-score of their arrival "
+                       "frequencies against the exact probabilities")
     return out
 
 

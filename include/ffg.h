@@ -249,6 +249,17 @@ ffg_status pagerank_solve_static(const ffg_graph *g, double damping, double tol,
                                  int32_t max_iter, ffg_prec prec, void *ranks, int init,
                                  int32_t *iters_out, double *residual_out, void *stream);
 
+/* ---- the naive metric (Sec. VII-A) ----
+ * For every local minimum x (is_min), the fraction of optimal fitness
+ * f_opt / f(x), in ascending node order: frac (DEVICE, g->n_minima
+ * doubles) and, if node is non-NULL, the node ids (DEVICE, n_minima int64).
+ * The number of minima is g->n_minima.  FFG_ERR_EMPTY without minima.
+ * workspace: DEVICE, 256-byte aligned, minima_workspace_bytes.
+ * Asynchronous. */
+size_t minima_workspace_bytes(int64_t n_nodes);
+ffg_status minima_fraction(const ffg_graph *g, const double *fitness_raw, double *frac,
+                           int64_t *node, void *workspace, size_t ws_bytes, void *stream);
+
 /* ---- exact solve on the DAG (Sec. VII-B) ----
  * The FFG has no cycles (every edge goes to a strictly better key), so
  *   y[v] = 1 + damping * sum_{u -> v} y[u] / outdeg[u]

@@ -106,6 +106,8 @@ def _load():
                                           C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
             lib.or_absorption.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.or_minima_fraction.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_double,
+                                               C.c_void_p, C.POINTER(C.c_int64)]
             lib.or_splitmix64.restype = C.c_uint64
             lib.or_splitmix64.argtypes = [C.c_uint64]
             lib.or_walks.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
@@ -268,6 +270,18 @@ def absorption_csr(in_ptr, in_idx, outdeg, key):
     if st:
         raise OracleError(st, "absorption")
     return a
+
+
+def minima_fraction(g: Graph) -> np.ndarray:
+    """f_opt / f(x) of every local minimum (ascending node order)."""
+    out = np.zeros(max(g.n_nodes, 1), dtype=np.float64)
+    k = C.c_int64(0)
+    is_min = g.is_min.astype(np.uint8)
+    st = _load().or_minima_fraction(g.n_nodes, _ptr(is_min), _ptr(g.node_fit), g.f_opt,
+                                    _ptr(out), C.byref(k))
+    if st:
+        raise OracleError(st, "minima_fraction")
+    return out[:k.value]
 
 
 def splitmix64(x: int) -> int:

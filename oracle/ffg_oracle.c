@@ -23,6 +23,8 @@
  *                      walk ends at its end), arrival frequencies within
  *                      binomial bounds of or_absorption.
  *   or_centrality      pinned: hand examples, monotonicity, limits.
+ *   or_minima_fraction pinned: a hand example, the global minimum gives 1,
+ *                      every fraction lies in (0, 1].
  */
 #include "ffg_oracle.h"
 
@@ -476,4 +478,20 @@ int or_centrality(int64_t n, const uint8_t *is_min, const double *node_fit, cons
         cp[k] = sp / sl;
     }
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* the naive metric (Sec. VII-A): f_opt / f(x) for every local minimum x,     */
+/* in ascending node order                                                    */
+/* ------------------------------------------------------------------------ */
+
+int or_minima_fraction(int64_t n, const uint8_t *is_min, const double *node_fit, double f_opt,
+                       double *frac, int64_t *n_out)
+{
+    if (n <= 0) return OR_BAD_ARG;
+    int64_t k = 0;
+    for (int64_t v = 0; v < n; ++v)
+        if (is_min[v]) frac[k++] = f_opt / node_fit[v];
+    *n_out = k;
+    return k ? OR_OK : OR_EMPTY;
 }

@@ -98,6 +98,10 @@ uint64_t or_splitmix64(uint64_t x);
 int or_walks(int64_t n, const int64_t *out_ptr, const int32_t *out_idx, const int32_t *outdeg,
              uint64_t seed, int64_t n_walks, uint64_t *counts, int64_t *steps);
 
+/* f_opt / f(x) for every local minimum, ascending node order; *n_out = count. */
+int or_minima_fraction(int64_t n, const uint8_t *is_min, const double *node_fit, double f_opt,
+                       double *frac, int64_t *n_out);
+
 /* C_p for every threshold p[k] (fractions, e.g. 0.05). */
 int or_centrality(int64_t n, const uint8_t *is_min, const double *node_fit, const double *x,
                   double f_opt, const double *p, int32_t n_p, double *cp);

@@ -107,6 +107,7 @@ ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
                 "pagerank_solve_static",
                 "pagerank_query", "dag_workspace_bytes", "dag_solve",
                 "walk_workspace_bytes", "walk_simulate",
+                "minima_workspace_bytes", "minima_fraction",
                 "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
                 "pagerank_batch_plan_tuned",
                 "pagerank_batch_run", "pagerank_batch_query",
@@ -145,6 +146,9 @@ def load(path: str | None = None):
     lib.pagerank_batch_workspace_bytes.argtypes = [P(ffg_pr_job), i32, C.c_int]
     lib.pagerank_batch_workspace_bytes.restype = sz
     lib.pagerank_batch_plan.argtypes = [P(ffg_pr_job), i32, C.c_int, vp, sz, P(ffg_pr_batch), vp]
+    lib.minima_workspace_bytes.restype = sz
+    lib.minima_workspace_bytes.argtypes = [C.c_int64]
+    lib.minima_fraction.argtypes = [P(ffg_graph), vp, vp, vp, vp, sz, vp]
     lib.walk_workspace_bytes.restype = sz
     lib.walk_workspace_bytes.argtypes = []
     lib.walk_simulate.argtypes = [P(ffg_graph), C.c_uint64, C.c_int64, vp, vp, sz,
@@ -437,6 +441,21 @@ def dag(g: "Graph", damping: float = 0.85, mode: int = DAG_PAGERANK, stream=None
                        _stream_handle(stream))
     _check(st, "dag_solve")
     return out, lv
+
+
+def minima_fraction(g: "Graph", fitness, stream=None):
+    """(f_opt / f(x) of every local minimum, node ids), ascending node order."""
+    torch = _torch()
+    dev = g.out_ptr.device
+    frac = torch.empty(max(g.n_minima, 1), dtype=torch.float64, device=dev)
+    node = torch.empty(max(g.n_minima, 1), dtype=torch.int64, device=dev)
+    need = int(load().minima_workspace_bytes(g.n_nodes))
+    ws = workspace(need, dev)
+    _check(int(load().minima_fraction(C.byref(g.c), C.c_void_p(fitness.data_ptr()),
+                                      C.c_void_p(frac.data_ptr()), C.c_void_p(node.data_ptr()),
+                                      C.c_void_p(ws.data_ptr()), need,
+                                      C.c_void_p(_stream_handle(stream)))), "minima_fraction")
+    return frac[:g.n_minima], node[:g.n_minima]
 
 
 def walk_simulate(g: "ffg_graph", seed: int, n_walks: int, counts: int, ws: int,

@@ -378,3 +378,73 @@ extern "C" ffg_status centrality_batch(const ffg_cp_job *jobs, int32_t n_jobs, f
     if (empty) return set_error("a job's graph has no local minimum (its C_p is NaN)"), FFG_ERR_EMPTY;
     return FFG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// the naive metric (Sec. VII-A): fraction of optimal fitness f_opt / f(x) of
+// every local minimum, in ascending node order (flags, one scan, scatter)
+// ---------------------------------------------------------------------------
+namespace ffg {
+namespace {
+
+__global__ void k_min_flags(const uint8_t *__restrict__ is_min, int64_t n, int32_t *flag) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
+         v += int64_t(gridDim.x) * blockDim.x)
+        flag[v] = is_min[v] ? 1 : 0;
+}
+
+__global__ void k_min_emit(const uint8_t *__restrict__ is_min,
+                           const int64_t *__restrict__ node_raw,
+                           const double *__restrict__ fit, const int64_t *__restrict__ pos,
+                           int64_t n, double f_opt, double *frac, int64_t *node) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
+         v += int64_t(gridDim.x) * blockDim.x) {
+        if (!is_min[v]) continue;
+        const int64_t k = pos[v];
+        frac[k] = f_opt / fit[node_raw[v]];
+        if (node) node[k] = v;
+    }
+}
+
+unsigned min_grid(int64_t n) {
+    const int64_t g = (n + 255) / 256;
+    return static_cast<unsigned>(g < 1 ? 1 : (g > 65535 ? 65535 : g));
+}
+
+}  // namespace
+}  // namespace ffg
+
+extern "C" size_t minima_workspace_bytes(int64_t n_nodes) {
+    if (n_nodes < 0) return 0;
+    Carver c(nullptr);
+    c.take<int32_t>(size_t(n_nodes));
+    c.take<int64_t>(size_t(n_nodes) + 1);
+    c.take<int64_t>(size_t(scan_scratch_elems(n_nodes)));
+    return c.off;
+}
+
+extern "C" ffg_status minima_fraction(const ffg_graph *g, const double *fitness_raw,
+                                      double *frac, int64_t *node, void *workspace,
+                                      size_t ws_bytes, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!g || g->n_nodes <= 0 || !g->is_min || !g->node_raw || !fitness_raw || !frac)
+        return set_error("graph incomplete, or fitness / frac NULL"), FFG_ERR_INVALID_ARG;
+    if (g->n_minima <= 0) return set_error("the graph has no local minimum"), FFG_ERR_EMPTY;
+    if (!workspace || !aligned256(workspace))
+        return set_error("workspace NULL or not 256-byte aligned"), FFG_ERR_INVALID_ARG;
+    const int64_t n = g->n_nodes;
+    Carver c(workspace);
+    int32_t *flag = c.take<int32_t>(size_t(n));
+    int64_t *pos = c.take<int64_t>(size_t(n) + 1);
+    int64_t *scratch = c.take<int64_t>(size_t(scan_scratch_elems(n)));
+    if (ws_bytes < c.off)
+        return set_error("workspace %zu bytes, need %zu", ws_bytes, c.off), FFG_ERR_NO_MEMORY;
+    k_min_flags<<<min_grid(n), 256, 0, stream>>>(g->is_min, n, flag);
+    count_launch();
+    FFG_TRY(check_launch("k_min_flags"));
+    FFG_TRY(scan_exclusive(flag, pos, n, scratch, stream));
+    k_min_emit<<<min_grid(n), 256, 0, stream>>>(g->is_min, g->node_raw, fitness_raw, pos, n,
+                                                g->f_opt, frac, node);
+    count_launch();
+    return check_launch("k_min_emit");
+}

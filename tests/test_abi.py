@@ -181,3 +181,17 @@ def test_walk_simulate_validated_on_host(lib):
     assert ffg.walk_simulate(g, 1, 10, 0, 256, 256)[0] == ffg.FFG_ERR_INVALID_ARG
     assert ffg.walk_simulate(g, 1, 10, 256, 258, 256)[0] == ffg.FFG_ERR_INVALID_ARG
     assert ffg.walk_simulate(g, 1, 10, 256, 256, 8)[0] == ffg.FFG_ERR_NO_MEMORY
+
+
+def test_minima_fraction_validated_on_host(lib):
+    g = ffg.ffg_graph()
+    g.n_nodes, g.is_min, g.node_raw, g.n_minima = 10, 256, 256, 0
+    need = lib.minima_workspace_bytes(10)
+    assert need > 0
+    args = (C.c_void_p(256), C.c_void_p(256), None, C.c_void_p(256), need, None)
+    assert lib.minima_fraction(C.byref(g), *args) == ffg.FFG_ERR_EMPTY
+    g.n_minima = 2
+    assert lib.minima_fraction(C.byref(g), C.c_void_p(256), C.c_void_p(256), None,
+                               C.c_void_p(258), need, None) == ffg.FFG_ERR_INVALID_ARG
+    assert lib.minima_fraction(C.byref(g), C.c_void_p(256), C.c_void_p(256), None,
+                               C.c_void_p(256), 8, None) == ffg.FFG_ERR_NO_MEMORY

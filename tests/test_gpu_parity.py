@@ -568,3 +568,14 @@ def test_walks_bit_exact_and_unbiased():
     p = a[sinks]
     sd = np.sqrt(np.clip(p * (1 - p), 0.0, None) / W)
     assert (np.abs(freq - p) <= 6 * sd + 1e-12).all()
+
+
+def test_minima_fraction_bit_exact():
+    for spec, seed, nbh in [(fi.single_small(), 1, "hamming"), (fi.gemm_space(), 2, "adjacent"),
+                            (fi.single_large(), 1, "hamming")]:
+        f = fi.runtimes(spec, seed)
+        og = oracle.build(spec, f, NBH[nbh][1])
+        g, fd = run_build(spec, f, nbh)
+        frac, node = ffg.minima_fraction(g, fd)
+        np.testing.assert_array_equal(_np(frac), oracle.minima_fraction(og))
+        np.testing.assert_array_equal(_np(node), np.flatnonzero(og.is_min))

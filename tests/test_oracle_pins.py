@@ -391,3 +391,17 @@ def test_walk_frequencies_match_absorption():
         freq = counts[sinks] / W
         sd = np.sqrt(np.clip(p * (1 - p), 0.0, None) / W)
         assert (np.abs(freq - p) <= 5 * sd + 1e-12).all()
+
+
+def test_minima_fraction():
+    """Hand example: fitness 4 (min), 6, 2 (min, optimum), 5 on an adjacent
+    line: minima 0 and 2 give 2/4 and 2/2."""
+    spec = _one_param([1, 2, 3, 4])
+    g = oracle.build(spec, np.array([4.0, 6.0, 2.0, 5.0]), oracle.ADJACENT)
+    assert list(g.is_min) == [True, False, True, False]
+    assert list(oracle.minima_fraction(g)) == [0.5, 1.0]
+    for seed in (1, 2):
+        g = oracle.build(fi.single_small(), fi.runtimes(fi.single_small(), seed), oracle.HAMMING)
+        fr = oracle.minima_fraction(g)
+        assert len(fr) == g.is_min.sum() and (fr > 0).all() and (fr <= 1).all()
+        assert (fr == 1.0).any()
