@@ -24,6 +24,7 @@ CANDIDATES = (
     (0.5, 0.1, 0, 24, 0),
     (0.25, 0.05, 0, 24, 0),
     (0.1, 0.02, 0, 24, 0),
+    (0.05, 0.005, 0, 24, 0),
     (0.5, 0.5, 0, 24, 1),
 )
 
