@@ -3,14 +3,17 @@
 //
 // One thread per raw point r, warps over 32 consecutive raw points:
 //   k_valid  decodes r into mixed-radix digits, evaluates the clauses and
-//            writes one 32-bit word of the validity bitmap per warp (ballot);
-//            also reduces the node count and f_opt (best non-failed fitness).
+//            writes one 32-bit word of the validity bitmap per warp (ballot)
+//            and the point's key (fitness, +inf if failed, NaN if invalid:
+//            every comparison with NaN is false, so an invalid neighbour
+//            needs no separate check); also reduces the node count and f_opt
+//            (best non-failed fitness).
 //   scan     of the per-word popcounts gives the rank directory: the node id
 //            of a valid raw point is prefix[r/32] + popc(word & lanes below).
 //   k_count  enumerates the neighbours of every valid point -- Hamming: every
 //            other value of one parameter (Eq. 2); adjacent: the list
-//            neighbours d-1 and d+1 -- keeps the valid ones (bitmap) and
-//            counts those with strictly lower (out) and higher (in) key.
+//            neighbours d-1 and d+1 -- and counts those with strictly lower
+//            (out) and higher (in) key; it also records each point's node id.
 //   scans    of the degrees give out_ptr / in_ptr.
 //   k_emit   enumerates again in ascending raw order and writes node ids.
 //
@@ -21,8 +24,10 @@
 // so the lists come out sorted by node id.
 //
 // For a warp of 32 consecutive raw points, the candidates for one (i, j)
-// are 32 shifted consecutive raw points, so the fitness and bitmap loads of
-// the enumeration are coalesced.
+// are 32 shifted consecutive raw points, so the key and node-id loads of the
+// enumeration are coalesced.  Digits come from divisions by the radices done
+// as one multiply-high each (Lemire, Kaser and Kurz 2019: for 32-bit n and
+// d >= 2, floor(n / d) = (n * ceil(2^64 / d)) >> 64).
 #include <vector>
 
 #include "ffg_internal.cuh"
@@ -43,6 +48,8 @@ struct BuildCtl {
 
 struct BuildWs {
     BuildCtl *ctl;
+    double *key;       // per raw point: fitness key, NaN if invalid
+    int32_t *node_of;  // per valid raw point: node id
     uint32_t *bitmap;
     int32_t *wcount;
     int64_t *wprefix;
@@ -57,6 +64,8 @@ BuildWs carve(void *base, int64_t R) {
     Carver c(base);
     BuildWs w;
     w.ctl = c.take<BuildCtl>(1);
+    w.key = c.take<double>(R);
+    w.node_of = c.take<int32_t>(R);
     w.bitmap = c.take<uint32_t>(W);
     w.wcount = c.take<int32_t>(W);
     w.wprefix = c.take<int64_t>(W + 1);
@@ -73,8 +82,16 @@ struct SmemSpace {
     int32_t radix[FFG_MAX_PARAMS];
     int32_t voff[FFG_MAX_PARAMS];
     uint32_t stride[FFG_MAX_PARAMS];
+    unsigned long long magic[FFG_MAX_PARAMS];  // ceil(2^64 / radix), radix >= 2
     DevClause clause[FFG_MAX_CONSTRAINTS];
 };
+
+// n / radix_i for n < 2^31
+__device__ __forceinline__ uint32_t div_radix(const SmemSpace &s, int i, uint32_t n) {
+    return s.radix[i] == 1 ? n : static_cast<uint32_t>(__umul64hi(n, s.magic[i]));
+}
+
+__device__ __forceinline__ double invalid_key() { return __longlong_as_double(0x7ff8000000000000LL); }
 
 __device__ __forceinline__ void stage_space(const DevSpace &sp, SmemSpace &s, int64_t *vals,
                                             bool with_values) {
@@ -84,18 +101,16 @@ __device__ __forceinline__ void stage_space(const DevSpace &sp, SmemSpace &s, in
         s.nc = sp.n_clauses;
     }
     if (t < FFG_MAX_PARAMS) {
-        s.radix[t] = sp.radix[t];
+        const int32_t r = sp.radix[t];
+        s.radix[t] = r;
         s.voff[t] = sp.voff[t];
         s.stride[t] = static_cast<uint32_t>(sp.stride[t]);
+        s.magic[t] = r >= 2 ? ~0ULL / static_cast<unsigned long long>(r) + 1ULL : 0ULL;
     }
     if (t < FFG_MAX_CONSTRAINTS) s.clause[t] = sp.clause[t];
     if (with_values)
         for (int i = t; i < sp.n_values; i += blockDim.x) vals[i] = sp.values[i];
     __syncthreads();
-}
-
-__device__ __forceinline__ bool bit_of(const uint32_t *__restrict__ bm, uint32_t r) {
-    return (__ldg(bm + (r >> 5)) >> (r & 31)) & 1u;
 }
 
 // node id of valid raw point r; wprefix may be a slice of a longer scan
@@ -158,7 +173,8 @@ __device__ __forceinline__ int64_t mask_product(const SmemSpace &s, const int64_
 __device__ __forceinline__ void valid_body(const SmemSpace &s, const int64_t *vals, int64_t R,
                                            int64_t r, const double *__restrict__ fit,
                                            double fail_thr, uint32_t *__restrict__ bitmap,
-                                           int32_t *__restrict__ wcount, BuildCtl *ctl) {
+                                           int32_t *__restrict__ wcount, double *__restrict__ key,
+                                           BuildCtl *ctl) {
     const int64_t W = (R + 31) >> 5;
     bool ok = false;
     unsigned long long fbits = ~0ULL;
@@ -166,7 +182,7 @@ __device__ __forceinline__ void valid_body(const SmemSpace &s, const int64_t *va
         int32_t digit[FFG_MAX_PARAMS];
         uint32_t rem = static_cast<uint32_t>(r);
         for (int i = s.n - 1; i >= 0; --i) {
-            const uint32_t q = rem / static_cast<uint32_t>(s.radix[i]);
+            const uint32_t q = div_radix(s, i, rem);
             digit[i] = static_cast<int32_t>(rem - q * static_cast<uint32_t>(s.radix[i]));
             rem = q;
         }
@@ -184,10 +200,13 @@ __device__ __forceinline__ void valid_body(const SmemSpace &s, const int64_t *va
             }
             ok = ok && h;
         }
+        double k = invalid_key();
         if (ok) {
             const double f = fit[r];
             if (f < fail_thr) fbits = ordered_bits(f);
+            k = fit_key(f, fail_thr);
         }
+        key[r] = k;
     }
     const unsigned m = __ballot_sync(0xffffffffu, ok);
     if ((threadIdx.x & 31) == 0 && (r >> 5) < W) {
@@ -205,12 +224,13 @@ __device__ __forceinline__ void valid_body(const SmemSpace &s, const int64_t *va
 __global__ void __launch_bounds__(kThreads) k_valid(const DevSpace sp,
                                                     const double *__restrict__ fit,
                                                     double fail_thr, uint32_t *__restrict__ bitmap,
-                                                    int32_t *__restrict__ wcount, BuildCtl *ctl) {
+                                                    int32_t *__restrict__ wcount,
+                                                    double *__restrict__ key, BuildCtl *ctl) {
     __shared__ SmemSpace s;
     __shared__ int64_t vals[FFG_MAX_VALUES];
     stage_space(sp, s, vals, true);
     valid_body(s, vals, sp.n_raw, int64_t(blockIdx.x) * kThreads + threadIdx.x, fit, fail_thr,
-               bitmap, wcount, ctl);
+               bitmap, wcount, key, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -218,20 +238,21 @@ __global__ void __launch_bounds__(kThreads) k_valid(const DevSpace sp,
 // ---------------------------------------------------------------------------
 template <int NBH>
 __device__ __forceinline__ void count_body(const SmemSpace &s, int64_t R, int64_t r64,
-                                           const double *__restrict__ fit, double fail_thr,
+                                           const double *__restrict__ key, double fail_thr,
                                            const uint32_t *__restrict__ bitmap,
                                            const int64_t *__restrict__ wprefix, int64_t wbase,
                                            int32_t *__restrict__ outdeg,
-                                           int32_t *__restrict__ indeg, BuildCtl *ctl) {
+                                           int32_t *__restrict__ indeg,
+                                           int32_t *__restrict__ node_of, BuildCtl *ctl) {
     unsigned long long n_out = 0, n_in = 0, n_min = 0;
-    if (r64 < R && bit_of(bitmap, static_cast<uint32_t>(r64))) {
+    const double k0 = r64 < R ? __ldg(key + r64) : invalid_key();
+    if (k0 == k0) {  // a valid point
         const uint32_t r = static_cast<uint32_t>(r64);
-        const double k0 = fit_key(__ldg(fit + r), fail_thr);
         int32_t out = 0, in = 0;
         uint32_t rem = r;
         for (int i = s.n - 1; i >= 0; --i) {
             const uint32_t rad = static_cast<uint32_t>(s.radix[i]);
-            const uint32_t q = rem / rad;
+            const uint32_t q = div_radix(s, i, rem);
             const uint32_t d = rem - q * rad;
             rem = q;
             const uint32_t st = s.stride[i];
@@ -240,14 +261,13 @@ __device__ __forceinline__ void count_body(const SmemSpace &s, int64_t R, int64_
             const uint32_t jhi = NBH == FFG_HAMMING ? rad - 1 : (d + 1 < rad ? d + 1 : d);
             for (uint32_t j = jlo; j <= jhi; ++j) {
                 if (j == d) continue;
-                const uint32_t rr = base + j * st;
-                if (!bit_of(bitmap, rr)) continue;
-                const double kk = fit_key(__ldg(fit + rr), fail_thr);
+                const double kk = __ldg(key + base + j * st);  // NaN if invalid
                 out += kk < k0;
                 in += kk > k0;
             }
         }
         const int32_t node = rank_of(bitmap, wprefix, wbase, r);
+        node_of[r] = node;
         outdeg[node] = out;
         indeg[node] = in;
         n_out = out;
@@ -266,16 +286,17 @@ __device__ __forceinline__ void count_body(const SmemSpace &s, int64_t R, int64_
 
 template <int NBH>
 __global__ void __launch_bounds__(kThreads) k_count(const DevSpace sp,
-                                                    const double *__restrict__ fit,
+                                                    const double *__restrict__ key,
                                                     double fail_thr,
                                                     const uint32_t *__restrict__ bitmap,
                                                     const int64_t *__restrict__ wprefix,
                                                     int32_t *__restrict__ outdeg,
-                                                    int32_t *__restrict__ indeg, BuildCtl *ctl) {
+                                                    int32_t *__restrict__ indeg,
+                                                    int32_t *__restrict__ node_of, BuildCtl *ctl) {
     __shared__ SmemSpace s;
     stage_space(sp, s, nullptr, false);
-    count_body<NBH>(s, sp.n_raw, int64_t(blockIdx.x) * kThreads + threadIdx.x, fit, fail_thr,
-                    bitmap, wprefix, 0, outdeg, indeg, ctl);
+    count_body<NBH>(s, sp.n_raw, int64_t(blockIdx.x) * kThreads + threadIdx.x, key, fail_thr,
+                    bitmap, wprefix, 0, outdeg, indeg, node_of, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -283,15 +304,16 @@ __global__ void __launch_bounds__(kThreads) k_count(const DevSpace sp,
 // ---------------------------------------------------------------------------
 template <int NBH>
 __device__ __forceinline__ void emit_body(
-    const SmemSpace &s, int64_t R, int64_t r64, const double *__restrict__ fit, double fail_thr,
-    const uint32_t *__restrict__ bitmap, const int64_t *__restrict__ wprefix, int64_t wbase,
-    const int64_t *__restrict__ out_ptr, const int64_t *__restrict__ in_ptr,
-    int32_t *__restrict__ out_idx, int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg,
-    int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min) {
-    if (r64 >= R || !bit_of(bitmap, static_cast<uint32_t>(r64))) return;
+    const SmemSpace &s, int64_t R, int64_t r64, const double *__restrict__ key, double fail_thr,
+    const int32_t *__restrict__ node_of, const int64_t *__restrict__ out_ptr,
+    const int64_t *__restrict__ in_ptr, int32_t *__restrict__ out_idx,
+    int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg, int64_t *__restrict__ node_raw,
+    uint8_t *__restrict__ is_min) {
+    if (r64 >= R) return;
+    const double k0 = __ldg(key + r64);
+    if (!(k0 == k0)) return;  // not a valid point
     const uint32_t r = static_cast<uint32_t>(r64);
-    const double k0 = fit_key(__ldg(fit + r), fail_thr);
-    const int32_t node = rank_of(bitmap, wprefix, wbase, r);
+    const int32_t node = __ldg(node_of + r);
     const int64_t o0 = out_ptr[node];
     int64_t o = o0, q = in_ptr[node];
 
@@ -302,17 +324,16 @@ __device__ __forceinline__ void emit_body(
         for (int i = FFG_MAX_PARAMS - 1; i >= 0; --i) {
             if (i < s.n) {
                 const uint32_t rad = static_cast<uint32_t>(s.radix[i]);
-                const uint32_t qq = rem / rad;
+                const uint32_t qq = div_radix(s, i, rem);
                 digit[i] = rem - qq * rad;
                 rem = qq;
             }
         }
     }
     auto visit = [&](uint32_t rr) {
-        if (!bit_of(bitmap, rr)) return;
-        const double kk = fit_key(__ldg(fit + rr), fail_thr);
-        if (kk < k0) out_idx[o++] = rank_of(bitmap, wprefix, wbase, rr);
-        else if (kk > k0) in_idx[q++] = rank_of(bitmap, wprefix, wbase, rr);
+        const double kk = __ldg(key + rr);  // NaN if invalid: both tests false
+        if (kk < k0) out_idx[o++] = __ldg(node_of + rr);
+        else if (kk > k0) in_idx[q++] = __ldg(node_of + rr);
     };
     // negative offsets: slowest parameter first, values ascending
 #pragma unroll
@@ -341,15 +362,15 @@ __device__ __forceinline__ void emit_body(
 
 template <int NBH>
 __global__ void __launch_bounds__(kThreads) k_emit(
-    const DevSpace sp, const double *__restrict__ fit, double fail_thr,
-    const uint32_t *__restrict__ bitmap, const int64_t *__restrict__ wprefix,
-    const int64_t *__restrict__ out_ptr, const int64_t *__restrict__ in_ptr,
-    int32_t *__restrict__ out_idx, int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg,
-    int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min) {
+    const DevSpace sp, const double *__restrict__ key, double fail_thr,
+    const int32_t *__restrict__ node_of, const int64_t *__restrict__ out_ptr,
+    const int64_t *__restrict__ in_ptr, int32_t *__restrict__ out_idx,
+    int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg, int64_t *__restrict__ node_raw,
+    uint8_t *__restrict__ is_min) {
     __shared__ SmemSpace s;
     stage_space(sp, s, nullptr, false);
-    emit_body<NBH>(s, sp.n_raw, int64_t(blockIdx.x) * kThreads + threadIdx.x, fit, fail_thr,
-                   bitmap, wprefix, 0, out_ptr, in_ptr, out_idx, in_idx, outdeg, node_raw, is_min);
+    emit_body<NBH>(s, sp.n_raw, int64_t(blockIdx.x) * kThreads + threadIdx.x, key, fail_thr,
+                   node_of, out_ptr, in_ptr, out_idx, in_idx, outdeg, node_raw, is_min);
 }
 
 ffg_status check_common(const ffg_space *space, const double *fitness_raw, ffg_nbh nbh,
@@ -395,16 +416,19 @@ extern "C" ffg_status ffg_build_count(const ffg_space *space, const double *fitn
     const unsigned grid = static_cast<unsigned>((R + kThreads - 1) / kThreads);
     FFG_TRY(check_cuda(cudaMemsetAsync(w.ctl, 0, sizeof(BuildCtl), stream), "memset"));
     FFG_TRY(check_cuda(cudaMemsetAsync(&w.ctl->fopt_bits, 0xff, 8, stream), "memset"));
-    k_valid<<<grid, kThreads, 0, stream>>>(d, fitness_raw, fail_thr, w.bitmap, w.wcount, w.ctl);
+    k_valid<<<grid, kThreads, 0, stream>>>(d, fitness_raw, fail_thr, w.bitmap, w.wcount, w.key,
+                                           w.ctl);
     count_launch();
     FFG_TRY(check_launch("k_valid"));
     FFG_TRY(scan_exclusive(w.wcount, w.wprefix, W, w.scratch, stream));
     if (nbh == FFG_HAMMING)
-        k_count<FFG_HAMMING><<<grid, kThreads, 0, stream>>>(d, fitness_raw, fail_thr, w.bitmap,
-                                                            w.wprefix, w.outdeg, w.indeg, w.ctl);
+        k_count<FFG_HAMMING><<<grid, kThreads, 0, stream>>>(d, w.key, fail_thr, w.bitmap,
+                                                            w.wprefix, w.outdeg, w.indeg,
+                                                            w.node_of, w.ctl);
     else
-        k_count<FFG_ADJACENT><<<grid, kThreads, 0, stream>>>(d, fitness_raw, fail_thr, w.bitmap,
-                                                             w.wprefix, w.outdeg, w.indeg, w.ctl);
+        k_count<FFG_ADJACENT><<<grid, kThreads, 0, stream>>>(d, w.key, fail_thr, w.bitmap,
+                                                             w.wprefix, w.outdeg, w.indeg,
+                                                             w.node_of, w.ctl);
     count_launch();
     FFG_TRY(check_launch("k_count"));
     BuildCtl h;
@@ -445,12 +469,12 @@ extern "C" ffg_status ffg_build_fill(const ffg_space *space, const double *fitne
     FFG_TRY(scan_exclusive(w.indeg, g->in_ptr, N, w.scratch, stream));
     if (nbh == FFG_HAMMING)
         k_emit<FFG_HAMMING><<<grid, kThreads, 0, stream>>>(
-            d, fitness_raw, fail_thr, w.bitmap, w.wprefix, g->out_ptr, g->in_ptr, g->out_idx,
-            g->in_idx, g->outdeg, g->node_raw, g->is_min);
+            d, w.key, fail_thr, w.node_of, g->out_ptr, g->in_ptr, g->out_idx, g->in_idx,
+            g->outdeg, g->node_raw, g->is_min);
     else
         k_emit<FFG_ADJACENT><<<grid, kThreads, 0, stream>>>(
-            d, fitness_raw, fail_thr, w.bitmap, w.wprefix, g->out_ptr, g->in_ptr, g->out_idx,
-            g->in_idx, g->outdeg, g->node_raw, g->is_min);
+            d, w.key, fail_thr, w.node_of, g->out_ptr, g->in_ptr, g->out_idx, g->in_idx,
+            g->outdeg, g->node_raw, g->is_min);
     count_launch();
     return check_launch("k_emit");
 }
@@ -493,6 +517,8 @@ struct BatchBuildWs {
     int32_t *odeg, *ideg;
     int64_t *opre, *ipre;
     int64_t *scratch;
+    double *key;       // per raw point of every job
+    int32_t *node_of;  // per raw point of every job
     size_t bytes;
 };
 
@@ -514,6 +540,8 @@ BatchBuildWs carve_bb(void *base, int n, int64_t total_raw, int64_t total_words)
     w.ipre = c.take<int64_t>(total_raw + 1);
     w.scratch = c.take<int64_t>(scan_scratch_elems(total_raw > total_words ? total_raw
                                                                            : total_words));
+    w.key = c.take<double>(total_raw);
+    w.node_of = c.take<int32_t>(total_raw);
     w.bytes = c.off;
     return w;
 }
@@ -546,22 +574,24 @@ __global__ void k_bctl_init(BuildCtl *ctl, int32_t *status, int n) {
 __global__ void __launch_bounds__(kThreads) k_valid_batch(const BJob *__restrict__ jobs,
                                                           const int64_t *__restrict__ blk0, int n,
                                                           uint32_t *bitmap, int32_t *wcount,
-                                                          BuildCtl *ctl) {
+                                                          double *key, BuildCtl *ctl) {
     __shared__ SmemSpace s;
     __shared__ int64_t vals[FFG_MAX_VALUES];
     const int j = job_of_block(blk0, n);
     const BJob &J = jobs[j];
     stage_space(*J.sp, s, vals, true);
     const int64_t r = (int64_t(blockIdx.x) - blk0[j]) * kThreads + threadIdx.x;
-    valid_body(s, vals, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff, wcount + J.woff, ctl + j);
+    valid_body(s, vals, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff, wcount + J.woff,
+               key + J.roff, ctl + j);
 }
 
 __global__ void __launch_bounds__(kThreads) k_count_batch(const BJob *__restrict__ jobs,
                                                           const int64_t *__restrict__ blk0, int n,
+                                                          const double *__restrict__ key,
                                                           const uint32_t *__restrict__ bitmap,
                                                           const int64_t *__restrict__ wpre,
                                                           int32_t *odeg, int32_t *ideg,
-                                                          BuildCtl *ctl) {
+                                                          int32_t *node_of, BuildCtl *ctl) {
     __shared__ SmemSpace s;
     const int j = job_of_block(blk0, n);
     const BJob &J = jobs[j];
@@ -569,11 +599,13 @@ __global__ void __launch_bounds__(kThreads) k_count_batch(const BJob *__restrict
     const int64_t r = (int64_t(blockIdx.x) - blk0[j]) * kThreads + threadIdx.x;
     const int64_t wb = wpre[J.woff];
     if (J.nbh == FFG_HAMMING)
-        count_body<FFG_HAMMING>(s, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff, wpre + J.woff,
-                                wb, odeg + J.roff, ideg + J.roff, ctl + j);
+        count_body<FFG_HAMMING>(s, J.n_raw, r, key + J.roff, J.fail_thr, bitmap + J.woff,
+                                wpre + J.woff, wb, odeg + J.roff, ideg + J.roff,
+                                node_of + J.roff, ctl + j);
     else
-        count_body<FFG_ADJACENT>(s, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff,
-                                 wpre + J.woff, wb, odeg + J.roff, ideg + J.roff, ctl + j);
+        count_body<FFG_ADJACENT>(s, J.n_raw, r, key + J.roff, J.fail_thr, bitmap + J.woff,
+                                 wpre + J.woff, wb, odeg + J.roff, ideg + J.roff,
+                                 node_of + J.roff, ctl + j);
 }
 
 // the device counts of job j equal the sizes its graph arrays were made for
@@ -608,8 +640,8 @@ __global__ void k_rebase(const BJob *__restrict__ jobs, const int64_t *__restric
 
 __global__ void __launch_bounds__(kThreads) k_emit_batch(const BJob *__restrict__ jobs,
                                                          const int64_t *__restrict__ blk0, int n,
-                                                         const uint32_t *__restrict__ bitmap,
-                                                         const int64_t *__restrict__ wpre,
+                                                         const double *__restrict__ key,
+                                                         const int32_t *__restrict__ node_of,
                                                          const BuildCtl *__restrict__ ctl) {
     __shared__ SmemSpace s;
     const int j = job_of_block(blk0, n);
@@ -617,15 +649,14 @@ __global__ void __launch_bounds__(kThreads) k_emit_batch(const BJob *__restrict_
     if (!sizes_match(J, ctl[j])) return;  // uniform over the block
     stage_space(*J.sp, s, nullptr, false);
     const int64_t r = (int64_t(blockIdx.x) - blk0[j]) * kThreads + threadIdx.x;
-    const int64_t wb = wpre[J.woff];
     if (J.nbh == FFG_HAMMING)
-        emit_body<FFG_HAMMING>(s, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff, wpre + J.woff,
-                               wb, J.out_ptr, J.in_ptr, J.out_idx, J.in_idx, J.outdeg,
-                               J.node_raw, J.is_min);
+        emit_body<FFG_HAMMING>(s, J.n_raw, r, key + J.roff, J.fail_thr, node_of + J.roff,
+                               J.out_ptr, J.in_ptr, J.out_idx, J.in_idx, J.outdeg, J.node_raw,
+                               J.is_min);
     else
-        emit_body<FFG_ADJACENT>(s, J.n_raw, r, J.fit, J.fail_thr, bitmap + J.woff,
-                                wpre + J.woff, wb, J.out_ptr, J.in_ptr, J.out_idx, J.in_idx,
-                                J.outdeg, J.node_raw, J.is_min);
+        emit_body<FFG_ADJACENT>(s, J.n_raw, r, key + J.roff, J.fail_thr, node_of + J.roff,
+                                J.out_ptr, J.in_ptr, J.out_idx, J.in_idx, J.outdeg, J.node_raw,
+                                J.is_min);
 }
 
 struct BatchSizes {
@@ -670,12 +701,12 @@ ffg_status launch_count_phase(const BatchBuildWs &w, int n, int64_t total_raw,
     FFG_TRY(check_cuda(cudaMemsetAsync(w.odeg, 0, sizeof(int32_t) * total_raw, stream), "memset"));
     FFG_TRY(check_cuda(cudaMemsetAsync(w.ideg, 0, sizeof(int32_t) * total_raw, stream), "memset"));
     k_valid_batch<<<static_cast<unsigned>(total_blocks), kThreads, 0, stream>>>(
-        w.jobs, w.blk0, n, w.bitmap, w.wcount, w.ctl);
+        w.jobs, w.blk0, n, w.bitmap, w.wcount, w.key, w.ctl);
     count_launch();
     FFG_TRY(check_launch("k_valid_batch"));
     FFG_TRY(scan_exclusive(w.wcount, w.wpre, total_words, w.scratch, stream));
     k_count_batch<<<static_cast<unsigned>(total_blocks), kThreads, 0, stream>>>(
-        w.jobs, w.blk0, n, w.bitmap, w.wpre, w.odeg, w.ideg, w.ctl);
+        w.jobs, w.blk0, n, w.key, w.bitmap, w.wpre, w.odeg, w.ideg, w.node_of, w.ctl);
     count_launch();
     return check_launch("k_count_batch");
 }
@@ -690,7 +721,7 @@ ffg_status launch_fill_phase(const BatchBuildWs &w, int n, int64_t total_raw, in
     count_launch();
     FFG_TRY(check_launch("k_rebase"));
     k_emit_batch<<<static_cast<unsigned>(total_blocks), kThreads, 0, stream>>>(
-        w.jobs, w.blk0, n, w.bitmap, w.wpre, w.ctl);
+        w.jobs, w.blk0, n, w.key, w.node_of, w.ctl);
     count_launch();
     return check_launch("k_emit_batch");
 }
@@ -711,6 +742,8 @@ BatchBuildWs ws_of(const ffg_build_batch *plan) {
     w.opre = static_cast<int64_t *>(plan->tables[11]);
     w.ipre = static_cast<int64_t *>(plan->tables[12]);
     w.scratch = static_cast<int64_t *>(plan->tables[13]);
+    w.key = static_cast<double *>(plan->tables[14]);
+    w.node_of = static_cast<int32_t *>(plan->tables[15]);
     return w;
 }
 
@@ -787,10 +820,9 @@ extern "C" ffg_status ffg_build_batch_count(const ffg_build_job *jobs, int32_t n
     plan->total_words = z.total_words;
     plan->total_blocks = z.total_blocks;
     plan->total_rows = 0;
-    void *t[] = {w.dsp, w.jobs, w.blk0, w.row0, w.ctl, w.status, w.bitmap, w.wcount,
-                 w.wpre, w.odeg, w.ideg, w.opre, w.ipre, w.scratch};
-    for (int k = 0; k < 14; ++k) plan->tables[k] = t[k];
-    plan->tables[14] = plan->tables[15] = nullptr;
+    void *t[] = {w.dsp,  w.jobs, w.blk0, w.row0, w.ctl,  w.status,  w.bitmap, w.wcount,
+                 w.wpre, w.odeg, w.ideg, w.opre, w.ipre, w.scratch, w.key,    w.node_of};
+    for (int k = 0; k < 16; ++k) plan->tables[k] = t[k];
     if (empty) return set_error("a job has no valid configuration"), FFG_ERR_EMPTY;
     return FFG_OK;
 }
