@@ -57,6 +57,10 @@ namespace {
 #define FFG_PR_WARPS 24
 #endif
 constexpr int kWarpsSingle = FFG_PR_WARPS;
+#ifndef FFG_PR_WARPS64
+#define FFG_PR_WARPS64 32
+#endif
+constexpr int kWarpsSingle64 = FFG_PR_WARPS64;  // single FP64 solves
 constexpr int kWarpsBatch = 8;
 constexpr int kMaxBlocks = 4096;
 constexpr uint64_t kTimeoutNs = 2000000000ULL;
@@ -1244,7 +1248,9 @@ ffg_status launch_pr(const JobDev *jobs, const int2 *items, const int *first, in
 template <typename T>
 ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, int init,
                   void *ranks, PrWs &w, cudaStream_t stream) {
-    constexpr int W = kWarpsSingle;
+    // the FP64 forms hide their longer (16-byte or converted) gathers with
+    // more warps; FP32 is faster with more registers per warp
+    constexpr int W = sizeof(typename Rows<T>::Real) == 8 ? kWarpsSingle64 : kWarpsSingle;
     int per_sm = 0, sms = 0;
     FFG_TRY((kernel_config<T, W>(&per_sm, &sms)));
     const int64_t tiles = (g->n_nodes + 31) / 32;
