@@ -79,9 +79,6 @@ constexpr uint64_t kTimeoutNs = 2000000000ULL;
 constexpr int kSegD = FFG_PR_SEG;       // descriptors per TMA segment
 constexpr int kU = FFG_PR_UNROLL;       // descriptor padding unit
 static_assert(kU % 2 == 0 && kSegD % kU == 0 && kU <= 32, "descriptor padding");
-// Descriptors per step of the gather loop (gathers in flight per lane): a
-// multiple of kU, the remainder of a segment is done in steps of kU.  FP64
-// stays at kU: its in-sums are bound by the FP64 pipe, where padding costs.
 // The FP64 form whose w is stored as 128-bit fixed point (see Rows below);
 // `double` is the FP64 form with w stored as double.
 struct F64x {};
@@ -90,9 +87,13 @@ struct F64x {};
 // store w as double and convert each gathered value instead
 constexpr int64_t kFxMaxNodes = int64_t(1) << 21;
 
-template <typename T> struct Step { static constexpr int value = kU; };
+// Descriptors per step of the gather loop (gathers in flight per lane): a
+// multiple of kU; the remainder of a segment is done in steps of kU.  The
+// FP64 forms take 8 (their wider gathers need the registers).
+template <typename T> struct Step { static constexpr int value = 8; };
 template <> struct Step<float> { static constexpr int value = FFG_PR_STEP32; };
-static_assert(FFG_PR_STEP32 % kU == 0 && kSegD % FFG_PR_STEP32 == 0, "gather step");
+static_assert(FFG_PR_STEP32 % kU == 0 && kSegD % FFG_PR_STEP32 == 0 && 8 % kU == 0,
+              "gather step");
 constexpr int kLayoutThreads = 64;
 constexpr int64_t kRowCost = 20;        // per-row cost in in-edge units (batch plan)
 constexpr int64_t kTileCost = 19;       // per-tile cost in descriptor units (block split)
