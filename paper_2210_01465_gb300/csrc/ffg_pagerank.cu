@@ -320,10 +320,6 @@ __device__ __forceinline__ Fix3 block_sum_fix(Fix3 v) {
     return t;
 }
 
-struct Tot {
-    double r, d, s;
-};
-
 // thread 0: add the block's sums into buffer `buf`; rank 0 also clears the
 // buffer of the next phase
 __device__ __forceinline__ void publish(PrCtl *ctl, int buf, const Fix3 &b, int rank) {
