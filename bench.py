@@ -71,15 +71,71 @@ ORACLE_SAMPLE = ("oracle (plain C, 1 thread) on the same space, Hamming FFG: ful
                  "20 FP64 power iterations + C_p")
 
 
-def oracle_sample(spec, f, iters=20):
-    """One bounded sample of the workload on the CPU oracle; returns (units, seconds)."""
+def oracle_sample(spec, f, iters=20, phases=None):
+    """One bounded sample of the workload on the CPU oracle; returns (units,
+    seconds).  ``phases`` (a dict) receives the seconds of build, PageRank
+    and C_p."""
     import oracle
     t0 = time.perf_counter()
     og = oracle.build(spec, f, oracle.HAMMING)
+    t1 = time.perf_counter()
     x, it, res, conv = oracle.pagerank_power(og, DAMPING, TOL, max_iter=iters)
+    t2 = time.perf_counter()
     oracle.centrality(og, x / x.sum(), P_LIST)
-    dt = time.perf_counter() - t0
-    return og.n_edges * it, dt
+    t3 = time.perf_counter()
+    if phases is not None:
+        phases.update(build_s=t1 - t0, pagerank_s=t2 - t1, cp_s=t3 - t2)
+    return og.n_edges * it, t3 - t0
+
+
+def host_cpu():
+    """The host's CPU model (lscpu) and its logical core count."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
+_ALL_CORES_BARRIER = None
+
+
+def _all_cores_init(barrier):
+    global _ALL_CORES_BARRIER
+    _ALL_CORES_BARRIER = barrier
+
+
+def _all_cores_worker(_):
+    """One copy of the oracle sample; every copy starts once all have their
+    inputs, so they run side by side."""
+    import ffg_inputs as fi
+    spec = fi.single_large()
+    f = fi.runtimes(spec, seed=1)
+    _ALL_CORES_BARRIER.wait(timeout=600)
+    return oracle_sample(spec, f)
+
+
+def oracle_all_cores(n=None):
+    """The unmodified oracle on every host core at once: one independent copy
+    of the same sample per core (spawned processes), throughput = their
+    summed rates."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    n = n or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(n)
+    with cf.ProcessPoolExecutor(n, mp_context=ctx, initializer=_all_cores_init,
+                                initargs=(barrier,)) as ex:
+        res = list(ex.map(_all_cores_worker, range(n)))
+    return {"value": sum(u / s for u, s in res), "unit": UNIT, "cores": n,
+            "kind": "oracle copies, one per core",
+            "sample": ORACLE_SAMPLE + f" on each core at once (slowest copy "
+                      f"{max(s for _, s in res):.1f} s)"}
 
 
 def run_reference(args):
@@ -163,6 +219,9 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # roofline helpers
 # --------------------------------------------------------------------------
+
+HBM_NOMINAL_GBS = 7900.0  # the part's nominal HBM3e bandwidth (context; peak is measured)
+
 
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -342,11 +401,17 @@ def run_gpu(args):
     ach64 = pagerank_bytes(gH.n_nodes, gH.n_edges, statistics.mean(its64), 8) / \
         (statistics.mean(durs64) / 1e3) / 1e9
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        u, s = oracle_sample(spec, f_host)
+        ph = {}
+        u, s = oracle_sample(spec, f_host, phases=ph)
         cpu = {"value": u / s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": ORACLE_SAMPLE + f" ({s:.1f} s)"}
+               "sample": ORACLE_SAMPLE + f" ({s:.1f} s)",
+               "phases_s": {k: round(v, 3) for k, v in ph.items()}, "host": host_cpu()}
+        try:
+            cpu_all = oracle_all_cores()
+        except Exception as e:  # reported, never fatal: the bench line stands without it
+            cpu_all = {"unavailable": f"{type(e).__name__}: {e}"}
 
     scale = exact = None
     if not args.no_batched:
@@ -382,6 +447,7 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "kernel": "k_pagerank<float> (Hamming FFG)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
+                         "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
                          "traffic": traffic, "algorithmic_bytes": bytes_launch,
                          "launch_ms": statistics.mean(durs),
                          "l2_resident": True},
@@ -390,6 +456,7 @@ def run_gpu(args):
             "batched": batched,
             "sweep": sweep,
             "cpu_baseline": cpu,
+            "cpu_all_cores": cpu_all,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
@@ -521,7 +588,8 @@ def run_scale(dev, stream, reps=3):
         "value": g.n_edges * it / (ms / 1e3), "unit": UNIT,
         "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak,
-                     "peak_kind": peak_kind, "algorithmic_bytes": alg, "l2_resident": False},
+                     "peak_kind": peak_kind,
+                     "frac_of_nominal": alg / (ms / 1e3) / 1e9 / HBM_NOMINAL_GBS, "algorithmic_bytes": alg, "l2_resident": False},
         "pagerank_f64_ms": ms64, "iters_f64": it64, "us_per_iter_f64": 1e3 * ms64 / it64,
         "f32_vs_f64_rank_l1": float((x32.double() - x64).abs().sum()),
         "f32_vs_f64_cp_max_abs": float(np.abs(cp32 - cp64).max()),
@@ -609,8 +677,18 @@ def run_batched(dev, stream, steps, warmup, rank=0, world=1):
             "plain_f64_edges_iters_per_s": units64 / (ms64 / 1e3),
             "batched_f32_vs_plain_f64_speedup": (units / (pr_ms / 1e3)) / (units64 / (ms64 / 1e3)),
             "blocks": int(batch.plan.n_blocks),
-            "autotune": {"chosen (split/grain/max_blocks/block_warps/claim)": "/".join(map(str, best)),
-                         "ms_per_candidate": tried}}
+            "autotune": autotune_summary(batch, best, tried)}
+
+
+def autotune_summary(batch, best, tried):
+    """The chosen schedule, the time of every candidate, and the balance of the
+    last run: the sum of the jobs' block-seconds over the blocks is the time
+    a perfectly balanced schedule of the same per-job work would take."""
+    busy = batch.times()
+    return {"chosen (split/grain/max_blocks/block_warps/claim)":
+            "/".join(map(str, best)) + ("+measured" if batch.job_cost is not None else ""),
+            "ms_per_candidate": tried,
+            "balanced_ms": 1e3 * float(busy.sum()) / batch.plan.n_blocks}
 
 
 def run_sweep(dev, stream, steps, warmup):
@@ -670,8 +748,7 @@ def run_sweep(dev, stream, steps, warmup):
             "solves": len(E), "cuda_graph": captured, "ms_per_step": m,
             "solves_per_s": len(E) / (m / 1e3), "value": units / (m / 1e3), "unit": UNIT,
             "blocks": int(batch.plan.n_blocks),
-            "autotune": {"chosen (split/grain/max_blocks/block_warps/claim)": "/".join(map(str, best)),
-                         "ms_per_candidate": tried}}
+            "autotune": autotune_summary(batch, best, tried)}
 
 
 def main():

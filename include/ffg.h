@@ -354,12 +354,17 @@ ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec 
  * or 24 (one 768-thread block per SM), 0 = 24; `claim` 1 selects the claim
  * order, 0 the per-block lists; `fp64_form` (FFG_F64 only) keeps w as exact
  * 128-bit fixed point (1) or as double (2), 0 = fixed point when every
- * graph has at most 2^21 nodes.  pagerank_batch_plan uses 1.0, 1.0, 0, 8,
- * 0, 0.
+ * graph has at most 2^21 nodes.  `job_cost` (HOST, n_jobs positive finite
+ * values in any one unit, or NULL) replaces the cost model (edges + 20 x
+ * nodes, times an iteration estimate from the damping) that sizes the groups
+ * and balances the blocks, e.g. with the block-seconds that
+ * pagerank_batch_times measured on an earlier run; it is read during the
+ * call only.  pagerank_batch_plan uses 1.0, 1.0, 0, 8, 0, 0, NULL.
  * They change only the schedule, never results or the workspace size. */
 typedef struct {
     double split, grain;
     int32_t max_blocks, block_warps, claim, fp64_form;
+    const double *job_cost;
 } ffg_pr_tuning;
 
 ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec,
@@ -379,6 +384,15 @@ ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream);
  * first). */
 ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *iters_out,
                                 double *residual_out, int32_t *status_out, void *stream);
+
+/* Per-job busy time of the last run: block_seconds_out (HOST, n_jobs)
+ * receives, for every job, the sum over its blocks of the time each spent
+ * on it, from the moment all of them had started it to the block's end of
+ * it (device global timer).  The total over the jobs, divided by the
+ * plan's n_blocks, is the time an ideally balanced schedule would take.
+ * Synchronises `stream`. */
+ffg_status pagerank_batch_times(const ffg_pr_batch *plan, double *block_seconds_out,
+                                void *stream);
 
 /* Reads the outcome of the last pagerank_solve run in `workspace`
  * (synchronises `stream`).  Returns that run's status. */
@@ -417,6 +431,48 @@ size_t centrality_batch_workspace_bytes(int32_t n_jobs, int32_t n_p);
 ffg_status centrality_batch(const ffg_cp_job *jobs, int32_t n_jobs, ffg_prec prec,
                             const double *p, int32_t n_p, double *cp_out, void *workspace,
                             size_t ws_bytes, void *stream);
+
+/* ---- a whole batch in one call (Sec. VII-B over many search spaces) ----
+ * ffg_batch_run re-runs a batch planned with the calls above, in order on
+ * `stream`:
+ *   1. every FFG (ffg_build_batch_rerun of `build`; skipped when NULL,
+ *      e.g. when the graphs are built once and only the dampings vary);
+ *   2. every PageRank solve (pagerank_batch_run of `pagerank`);
+ *   3. when out->cp is non-NULL, C_p of every cp job at every p
+ *      (centrality_batch in the PageRank plan's precision; cp_jobs normally
+ *      pair each PageRank job's graph and ranks with the graph's fitness).
+ * With out == NULL only steps 1-2 are enqueued: no host work beyond argument
+ * checks, no synchronisation, so the call can be captured in a CUDA graph.
+ * Otherwise the call synchronises `stream` and fills every non-NULL field of
+ * `out` (HOST arrays): build_status (one per build job; FFG_ERR_INVALID_ARG
+ * marks a job whose recomputed sizes no longer fit its arrays, which keeps
+ * its previous graph), iters / residual / pr_status (one per PageRank job)
+ * and cp (n_cp_jobs x n_p, row-major).  The plans, the workspaces and every
+ * buffer they name belong to the caller and must stay valid.
+ * Returns the worst status: FFG_ERR_CUDA or FFG_ERR_TIMEOUT first (C_p is
+ * then not computed), else the first of the build, PageRank
+ * (FFG_ERR_NOT_CONVERGED) and C_p (FFG_ERR_EMPTY: a graph without a local
+ * minimum, its row NaN) statuses; FFG_ERR_INVALID_ARG for a missing plan or
+ * incomplete C_p arguments (nothing launched). */
+typedef struct {
+    const ffg_build_batch *build;  /* from ffg_build_batch_count + _fill, or NULL */
+    const ffg_pr_batch *pagerank;  /* from pagerank_batch_plan(_tuned); required */
+    const ffg_cp_job *cp_jobs;     /* HOST, n_cp_jobs (used when out->cp != NULL) */
+    int32_t n_cp_jobs, n_p;
+    const double *p;               /* HOST, n_p fractions (e.g. 0.05) */
+    void *cp_workspace;            /* DEVICE, centrality_batch_workspace_bytes(n_cp_jobs, n_p) */
+    size_t cp_ws_bytes;
+} ffg_batch_desc;
+
+typedef struct {
+    int32_t *build_status;         /* HOST, one per build job, or NULL */
+    int32_t *iters;                /* HOST, one per PageRank job, or NULL */
+    double *residual;              /* HOST, one per PageRank job, or NULL */
+    int32_t *pr_status;            /* HOST, one per PageRank job, or NULL */
+    double *cp;                    /* HOST, n_cp_jobs x n_p, or NULL (no C_p) */
+} ffg_batch_out;
+
+ffg_status ffg_batch_run(const ffg_batch_desc *desc, ffg_batch_out *out, void *stream);
 
 /* ---- diagnostics ---- */
 const char *ffg_status_str(ffg_status s);

@@ -92,11 +92,24 @@ class ffg_build_batch(C.Structure):
 
 class ffg_pr_tuning(C.Structure):
     _fields_ = [("split", C.c_double), ("grain", C.c_double), ("max_blocks", C.c_int32),
-                ("block_warps", C.c_int32), ("claim", C.c_int32), ("fp64_form", C.c_int32)]
+                ("block_warps", C.c_int32), ("claim", C.c_int32), ("fp64_form", C.c_int32),
+                ("job_cost", C.POINTER(C.c_double))]
 
 
 class ffg_cp_job(C.Structure):
     _fields_ = [("g", C.POINTER(ffg_graph)), ("fitness_raw", C.c_void_p), ("ranks", C.c_void_p)]
+
+
+class ffg_batch_desc(C.Structure):
+    _fields_ = [("build", C.POINTER(ffg_build_batch)), ("pagerank", C.POINTER(ffg_pr_batch)),
+                ("cp_jobs", C.POINTER(ffg_cp_job)), ("n_cp_jobs", C.c_int32),
+                ("n_p", C.c_int32), ("p", C.POINTER(C.c_double)), ("cp_workspace", C.c_void_p),
+                ("cp_ws_bytes", C.c_size_t)]
+
+
+class ffg_batch_out(C.Structure):
+    _fields_ = [("build_status", C.c_void_p), ("iters", C.c_void_p), ("residual", C.c_void_p),
+                ("pr_status", C.c_void_p), ("cp", C.c_void_p)]
 
 
 # names of include/ffg.h's entry points (the ABI test checks the header)
@@ -110,9 +123,10 @@ ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
                 "minima_workspace_bytes", "minima_fraction",
                 "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
                 "pagerank_batch_plan_tuned",
-                "pagerank_batch_run", "pagerank_batch_query",
+                "pagerank_batch_run", "pagerank_batch_query", "pagerank_batch_times",
                 "centrality_workspace_bytes", "centrality_proportion",
-                "centrality_batch_workspace_bytes", "centrality_batch", "ffg_status_str",
+                "centrality_batch_workspace_bytes", "centrality_batch", "ffg_batch_run",
+                "ffg_status_str",
                 "ffg_last_error", "ffg_launch_count")
 
 _lib = None
@@ -166,12 +180,14 @@ def load(path: str | None = None):
                                               sz, P(ffg_pr_batch), vp]
     lib.pagerank_batch_run.argtypes = [P(ffg_pr_batch), vp]
     lib.pagerank_batch_query.argtypes = [P(ffg_pr_batch), vp, vp, vp, vp]
+    lib.pagerank_batch_times.argtypes = [P(ffg_pr_batch), vp, vp]
     lib.centrality_workspace_bytes.argtypes = [i32]
     lib.centrality_workspace_bytes.restype = sz
     lib.centrality_proportion.argtypes = [P(ffg_graph), vp, vp, C.c_int, vp, i32, vp, vp, sz, vp]
     lib.centrality_batch_workspace_bytes.argtypes = [i32, i32]
     lib.centrality_batch_workspace_bytes.restype = sz
     lib.centrality_batch.argtypes = [P(ffg_cp_job), i32, C.c_int, vp, i32, vp, vp, sz, vp]
+    lib.ffg_batch_run.argtypes = [P(ffg_batch_desc), P(ffg_batch_out), vp]
     lib.ffg_status_str.argtypes = [C.c_int]
     lib.ffg_status_str.restype = C.c_char_p
     lib.ffg_last_error.argtypes = []
@@ -259,12 +275,19 @@ def pagerank_batch_plan(jobs, prec: int, ws: int, ws_bytes: int, plan: "ffg_pr_b
 
 
 def pagerank_batch_plan_tuned(jobs, prec: int, tuning, ws: int, ws_bytes: int,
-                              plan: "ffg_pr_batch", stream: int = 0) -> int:
-    """``tuning``: (split, grain, max_blocks[, block_warps[, claim[, fp64_form]]])."""
+                              plan: "ffg_pr_batch", stream: int = 0, job_cost=None) -> int:
+    """``tuning``: (split, grain, max_blocks[, block_warps[, claim[, fp64_form]]]);
+    ``job_cost``: per-job costs replacing the cost model (or None)."""
     t = ffg_pr_tuning(float(tuning[0]), float(tuning[1]), int(tuning[2]),
                       int(tuning[3]) if len(tuning) > 3 else 0,
                       int(tuning[4]) if len(tuning) > 4 else 0,
                       int(tuning[5]) if len(tuning) > 5 else 0)
+    cost = None
+    if job_cost is not None:
+        cost = np.ascontiguousarray(job_cost, dtype=np.float64)
+        if cost.shape != (len(jobs),):
+            raise ValueError("job_cost needs one value per job")
+        t.job_cost = cost.ctypes.data_as(C.POINTER(C.c_double))
     return int(load().pagerank_batch_plan_tuned(jobs, len(jobs), int(prec), C.byref(t),
                                                 C.c_void_p(ws), int(ws_bytes), C.byref(plan),
                                                 C.c_void_p(stream)))
@@ -284,6 +307,14 @@ def pagerank_batch_query(plan: "ffg_pr_batch", stream: int = 0):
                                     C.c_void_p(res.ctypes.data), C.c_void_p(st.ctypes.data),
                                     C.c_void_p(stream))
     return int(s), it, res, st
+
+
+def pagerank_batch_times(plan: "ffg_pr_batch", stream: int = 0):
+    """Returns (status, block-seconds[n_jobs]) of the last run."""
+    out = np.zeros(plan.n_jobs, dtype=np.float64)
+    s = load().pagerank_batch_times(C.byref(plan), C.c_void_p(out.ctypes.data),
+                                    C.c_void_p(stream))
+    return int(s), out
 
 
 def pagerank_query(ws: int, stream: int = 0):
@@ -564,6 +595,11 @@ def centrality_batch(jobs, prec: int, p, cp_out, ws: int, ws_bytes: int, stream:
                                        int(ws_bytes), C.c_void_p(stream)))
 
 
+def ffg_batch_run(desc: "ffg_batch_desc", out: "ffg_batch_out | None", stream: int = 0) -> int:
+    return int(load().ffg_batch_run(C.byref(desc), C.byref(out) if out is not None else None,
+                                    C.c_void_p(stream)))
+
+
 def centrality_many(specs, p, stream=None) -> np.ndarray:
     """C_p of many graphs at once; ``specs``: list of (Graph, fitness, ranks)."""
     torch = _torch()
@@ -611,15 +647,19 @@ class PageRankBatch:
         self.need = need
         self.plan = ffg_pr_batch()
         self.tuning = (1.0, 1.0, 0, 8, 0)
+        self.job_cost = None
         _check(pagerank_batch_plan(self.jobs, prec, self.ws.data_ptr(), need, self.plan,
                                    _stream_handle(stream)), "pagerank_batch_plan")
 
-    def replan(self, tuning, stream=None):
-        """Re-plan into the same workspace with (split, grain, max_blocks)."""
+    def replan(self, tuning, stream=None, job_cost=None):
+        """Re-plan into the same workspace with (split, grain, max_blocks[, block_warps[,
+        claim[, fp64_form]]]), and per-job costs in place of the model if given."""
         _check(pagerank_batch_plan_tuned(self.jobs, self.prec, tuning, self.ws.data_ptr(),
-                                         self.need, self.plan, _stream_handle(stream)),
+                                         self.need, self.plan, _stream_handle(stream),
+                                         job_cost=job_cost),
                "pagerank_batch_plan_tuned")
         self.tuning = tuple(tuning)
+        self.job_cost = None if job_cost is None else np.array(job_cost, dtype=np.float64)
 
     def run(self, stream=None):
         _check(pagerank_batch_run(self.plan, _stream_handle(stream)), "pagerank_batch_run")
@@ -628,6 +668,12 @@ class PageRankBatch:
         st, it, res, sts = pagerank_batch_query(self.plan, _stream_handle(stream))
         _check(st, "pagerank_batch_query", ok=(FFG_OK, FFG_ERR_NOT_CONVERGED))
         return it, res, sts
+
+    def times(self, stream=None):
+        """Per-job block-seconds of the last run (``pagerank_batch_times``)."""
+        st, t = pagerank_batch_times(self.plan, _stream_handle(stream))
+        _check(st, "pagerank_batch_times")
+        return t
 
 
 def centrality(g: Graph, fitness, ranks, p, ws=None, stream=None) -> np.ndarray:
@@ -641,3 +687,61 @@ def centrality(g: Graph, fitness, ranks, p, ws=None, stream=None) -> np.ndarray:
                                  ws.data_ptr(), need, _stream_handle(stream)),
            "centrality_proportion")
     return out
+
+
+class SpaceBatch:
+    """A whole batch per call (``ffg_batch_run``): ``solves`` is a
+    PageRankBatch; ``builds`` the BuildBatch of its graphs (rebuilt on every
+    run) or None; ``cp_specs`` a list of (Graph, fitness, ranks) whose C_p at
+    the fractions ``p`` every synchronising run returns (or None).
+
+    ``run(sync=False)`` only enqueues kernels (capturable in a CUDA graph);
+    ``run()`` synchronises and returns (status, outputs)."""
+
+    def __init__(self, solves, builds=None, cp_specs=None, p=None):
+        self.solves, self.builds = solves, builds
+        self.desc = ffg_batch_desc()
+        self.desc.pagerank = C.pointer(solves.plan)
+        if builds is not None:
+            self.desc.build = C.pointer(builds.plan)
+        self.n_cp = 0
+        self.p = None
+        if cp_specs:
+            if p is None or len(p) == 0:
+                raise ValueError("C_p needs the fractions p")
+            self.cp_jobs = (ffg_cp_job * len(cp_specs))()
+            for k, (g, fit, x) in enumerate(cp_specs):
+                self.cp_jobs[k].g = C.pointer(g.c)
+                self.cp_jobs[k].fitness_raw = fit.data_ptr()
+                self.cp_jobs[k].ranks = x.data_ptr()
+            self.p = np.ascontiguousarray(p, dtype=np.float64)
+            self.n_cp = len(cp_specs)
+            need = centrality_batch_workspace_bytes(self.n_cp, len(self.p))
+            self.cp_ws = workspace(need, cp_specs[0][2].device)
+            self.desc.cp_jobs = self.cp_jobs
+            self.desc.n_cp_jobs = self.n_cp
+            self.desc.n_p = len(self.p)
+            self.desc.p = self.p.ctypes.data_as(C.POINTER(C.c_double))
+            self.desc.cp_workspace = self.cp_ws.data_ptr()
+            self.desc.cp_ws_bytes = need
+
+    def run(self, sync: bool = True, stream=None):
+        sh = _stream_handle(stream)
+        if not sync:
+            _check(ffg_batch_run(self.desc, None, sh), "ffg_batch_run")
+            return None
+        n = self.solves.plan.n_jobs
+        res = {"iters": np.zeros(n, np.int32), "residual": np.zeros(n, np.float64),
+               "pr_status": np.zeros(n, np.int32)}
+        out = ffg_batch_out()
+        out.iters = res["iters"].ctypes.data
+        out.residual = res["residual"].ctypes.data
+        out.pr_status = res["pr_status"].ctypes.data
+        if self.builds is not None:
+            res["build_status"] = np.zeros(self.builds.plan.n_jobs, np.int32)
+            out.build_status = res["build_status"].ctypes.data
+        if self.n_cp:
+            res["cp"] = np.full((self.n_cp, len(self.p)), np.nan)
+            out.cp = res["cp"].ctypes.data
+        st = ffg_batch_run(self.desc, out, sh)
+        return st, res

@@ -8,13 +8,22 @@ wide its blocks are (`block_warps`: 8 warps, several blocks per SM, or 24,
 one block per SM) and whether blocks follow fixed per-block lists or claim
 jobs as they free up (`claim`).  ``tune`` runs the
 batch once per candidate (same workspace, re-planned), times it with CUDA
-events and leaves the fastest plan in place.  Results never depend on the
-tuning, only the time does.
+events and leaves the fastest plan in place.
+
+The plan balances the blocks with a cost model per job (edges + 20 x nodes,
+times an iteration estimate); what a job really costs also depends on how
+its edges pack into tile descriptors and on where its FP32 iteration stops.
+So ``tune`` also re-plans its fastest candidates with the per-job
+block-seconds each of them measured (``pagerank_batch_times``) in place of
+the model, and keeps such a plan when it is faster.  Results never depend
+on the tuning, only the time does.
 """
 from __future__ import annotations
 
 import json
 import os
+
+import numpy as np
 
 # (split, grain, max_blocks, block_warps, claim)
 CANDIDATES = (
@@ -25,30 +34,44 @@ CANDIDATES = (
     (0.25, 0.05, 0, 24, 0),
     (0.1, 0.02, 0, 24, 0),
     (0.05, 0.005, 0, 24, 0),
+    (0.02, 0.002, 0, 24, 0),
     (0.5, 0.5, 0, 24, 1),
 )
+MEASURED = 3  # candidates re-planned with measured job costs
 
 
-def tune(batch, candidates=CANDIDATES, reps: int = 1, table_path: str | None = None):
-    """Pick the fastest schedule for ``batch`` (a PageRankBatch); returns
-    (best (split, grain, max_blocks, block_warps, claim), {candidate: ms})."""
+def _time(batch, reps):
     import torch
-    times = {}
+    batch.run()
+    batch.query()                      # warm-up run of this plan
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.run()
+        e1.record()
+        batch.query()
+        ms.append(e0.elapsed_time(e1))
+    return min(ms)
+
+
+def tune(batch, candidates=CANDIDATES, reps: int = 1, table_path: str | None = None,
+         measured: int = MEASURED):
+    """Pick the fastest schedule for ``batch`` (a PageRankBatch); returns
+    (best (split, grain, max_blocks, block_warps, claim), {candidate: ms}).
+    Candidates re-planned with measured job costs are keyed with a
+    ``+measured`` suffix; the chosen plan's costs stay in ``batch.job_cost``."""
+    times, costs = {}, {}
     for cand in candidates:
         batch.replan(cand)
-        batch.run()
-        batch.query()                      # warm-up run of this plan
-        ms = []
-        for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            batch.run()
-            e1.record()
-            batch.query()
-            ms.append(e0.elapsed_time(e1))
-        times[cand] = min(ms)
-    best = min(times, key=times.get)
-    batch.replan(best)
+        times[(cand, False)] = _time(batch, reps)
+        costs[cand] = np.maximum(batch.times(), 1e-9)  # a cost must be positive
+    for cand in sorted(candidates, key=lambda c: times[(c, False)])[:measured]:
+        batch.replan(cand, job_cost=costs[cand])
+        times[(cand, True)] = _time(batch, reps)
+    best_key = min(times, key=times.get)
+    best, use_cost = best_key
+    batch.replan(best, job_cost=costs[best] if use_cost else None)
     if table_path:
         key = f"jobs={batch.plan.n_jobs},graphs={batch.plan.n_graphs}," \
               f"edges={sum(g.n_edges for g in batch.graphs)},prec={batch.prec}"
@@ -57,7 +80,9 @@ def tune(batch, candidates=CANDIDATES, reps: int = 1, table_path: str | None = N
             with open(table_path) as fh:
                 table = json.load(fh)
         table[key] = {"split": best[0], "grain": best[1], "max_blocks": best[2],
-                      "block_warps": best[3], "claim": best[4], "ms": times[best]}
+                      "block_warps": best[3], "claim": best[4], "measured_costs": use_cost,
+                      "ms": times[best_key]}
         with open(table_path, "w") as fh:
             json.dump(table, fh, indent=1)
-    return best, {"/".join(map(str, c)): round(t, 3) for c, t in times.items()}
+    return best, {"/".join(map(str, c)) + ("+measured" if m else ""): round(t, 3)
+                  for (c, m), t in times.items()}

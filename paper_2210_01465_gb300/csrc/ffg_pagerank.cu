@@ -112,6 +112,7 @@ struct PrCtl {
     int nblocks;
     int pad;
     unsigned long long acc[3][4];
+    unsigned long long busy_ns;  // sum over the job's blocks of their time on it
 };
 
 struct PrWs {
@@ -832,6 +833,7 @@ struct JobDev {
 struct LoopState {
     double res, prev_res, xs;
     int it, stop, converged, pad;
+    uint64_t t0;  // when all ranks had started (for the job's busy time)
 };
 
 // thread 0, after the barrier of an iteration: read the job's sums, decide
@@ -912,7 +914,10 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     unsigned phase = 1;
     int buf = 0;
     if (!group_barrier(ctl, phase * nb, nb)) return false;
-    if (threadIdx.x == 0) advance<R>(J, s_ls, ctl, buf, &s_c, false);
+    if (threadIdx.x == 0) {
+        s_ls.t0 = global_ns();
+        advance<R>(J, s_ls, ctl, buf, &s_c, false);
+    }
     __syncthreads();
     WS *wc = w0, *wn = w1;
     const R a = static_cast<R>(J.alpha);
@@ -1039,11 +1044,14 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
         const int32_t od = __ldg(outdeg + v);
         ranks[v] = static_cast<R>(Rows<T>::x_of(wc[v], od) * inv_s);
     }
-    if (rank == 0 && threadIdx.x == 0) {
-        ctl->iters = s_ls.it;
-        ctl->residual = s_ls.res;
-        ctl->converged = s_ls.converged;
-        ctl->nblocks = nb;
+    if (threadIdx.x == 0) {
+        atomicAdd(&ctl->busy_ns, static_cast<unsigned long long>(global_ns() - s_ls.t0));
+        if (rank == 0) {
+            ctl->iters = s_ls.it;
+            ctl->residual = s_ls.res;
+            ctl->converged = s_ls.converged;
+            ctl->nblocks = nb;
+        }
     }
     return failed == 0;
 }
@@ -1433,7 +1441,9 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, int warps,
                    FFG_ERR_INVALID_ARG;
         }
         P.graph_of_job[j] = it->second;
-        cost[j] = double(g->n_edges + kRowCost * g->n_nodes) * est_iters(jobs[j].damping);
+        cost[j] = tu.job_cost ? tu.job_cost[j]
+                              : double(g->n_edges + kRowCost * g->n_nodes) *
+                                    est_iters(jobs[j].damping);
         const int64_t tiles = (g->n_nodes + 31) / 32;
         useful += std::max<int64_t>(1, (tiles + 4 * warps - 1) / (4 * warps));
     }
@@ -1648,7 +1658,7 @@ ffg_status batch_cap(ffg_prec prec, int *cap) {
 }  // namespace ffg
 
 // per-block lists of 8-warp blocks: the fastest on the 234-space batch
-const ffg_pr_tuning kDefaultTuning = {1.0, 1.0, 0, kWarpsBatch, 0, 0};
+const ffg_pr_tuning kDefaultTuning = {1.0, 1.0, 0, kWarpsBatch, 0, 0, nullptr};
 
 extern "C" size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs,
                                                  ffg_prec prec) {
@@ -1692,6 +1702,11 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
                          "0, %d or %d, claim 0 or 1, fp64_form 0, 1 or 2",
                          kWarpsBatch, kWarpsSingle),
                FFG_ERR_INVALID_ARG;
+    if (tu.job_cost)
+        for (int j = 0; j < n_jobs; ++j)
+            if (!(tu.job_cost[j] > 0.0 && tu.job_cost[j] < HUGE_VAL))
+                return set_error("tuning: job_cost[%d] must be positive and finite", j),
+                       FFG_ERR_INVALID_ARG;
     int cap = 0, nb_max = 0;
     FFG_TRY(batch_cap(prec, &cap));
     FFG_TRY(batch_blocks(prec, warps, &nb_max));
@@ -1825,4 +1840,18 @@ extern "C" ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *it
     }
     if (worst == FFG_ERR_TIMEOUT) set_error("pagerank batch: a bounded device wait timed out");
     return worst;
+}
+
+extern "C" ffg_status pagerank_batch_times(const ffg_pr_batch *plan, double *block_seconds_out,
+                                           void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (!plan || plan->n_jobs < 1 || !plan->ctl || !block_seconds_out)
+        return set_error("plan is empty or block_seconds_out NULL"), FFG_ERR_INVALID_ARG;
+    std::vector<PrCtl> h(plan->n_jobs);
+    FFG_TRY(check_cuda(cudaMemcpyAsync(h.data(), plan->ctl, sizeof(PrCtl) * h.size(),
+                                       cudaMemcpyDeviceToHost, stream), "read batch times"));
+    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync batch times"));
+    for (int j = 0; j < plan->n_jobs; ++j) block_seconds_out[j] = 1e-9 * double(h[j].busy_ns);
+    return FFG_OK;
 }

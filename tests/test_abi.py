@@ -125,6 +125,39 @@ def test_batch_tuning_validated_on_host(lib):
         assert ffg.pagerank_batch_plan_tuned(jobs, ffg.F32, tuning, 256, 1 << 20, plan) == \
             ffg.FFG_ERR_INVALID_ARG
         assert "tuning" in ffg.ffg_last_error()
+    # measured job costs: positive and finite, checked before any planning
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        assert ffg.pagerank_batch_plan_tuned(jobs, ffg.F32, (1.0, 1.0, 0), 256, 1 << 20, plan,
+                                             job_cost=[bad]) == ffg.FFG_ERR_INVALID_ARG
+        assert "job_cost" in ffg.ffg_last_error()
+    with pytest.raises(ValueError):
+        ffg.pagerank_batch_plan_tuned(jobs, ffg.F32, (1.0, 1.0, 0), 256, 1 << 20, plan,
+                                      job_cost=[1.0, 2.0])
+    assert ffg.pagerank_batch_times(ffg.ffg_pr_batch())[0] == ffg.FFG_ERR_INVALID_ARG
+    assert lib.pagerank_batch_times(None, None, None) == ffg.FFG_ERR_INVALID_ARG
+
+
+def test_batch_run_validated_on_host(lib):
+    """ffg_batch_run refuses a missing plan or incomplete C_p arguments
+    before it launches anything."""
+    before = lib.ffg_launch_count()
+    assert lib.ffg_batch_run(None, None, None) == ffg.FFG_ERR_INVALID_ARG
+    desc = ffg.ffg_batch_desc()
+    assert ffg.ffg_batch_run(desc, None) == ffg.FFG_ERR_INVALID_ARG     # no PageRank plan
+    plan = ffg.ffg_pr_batch()
+    desc.pagerank = C.pointer(plan)
+    assert ffg.ffg_batch_run(desc, None) == ffg.FFG_ERR_INVALID_ARG     # plan with no jobs
+    plan.n_jobs = 1
+    bplan = ffg.ffg_build_batch()
+    desc.build = C.pointer(bplan)
+    assert ffg.ffg_batch_run(desc, None) == ffg.FFG_ERR_INVALID_ARG     # empty build plan
+    desc.build = None
+    cp = np.zeros(4)
+    out = ffg.ffg_batch_out()
+    out.cp = cp.ctypes.data
+    assert ffg.ffg_batch_run(desc, out) == ffg.FFG_ERR_INVALID_ARG      # C_p without jobs
+    assert "cp_jobs" in ffg.ffg_last_error()
+    assert lib.ffg_launch_count() == before
 
 
 def test_batched_build_validated_on_host(lib):

@@ -419,6 +419,110 @@ def test_batch_tuning_changes_schedule_not_results():
                 np.testing.assert_array_equal(x, x0)
 
 
+def test_batch_measured_costs_change_schedule_not_results():
+    """The per-job block-seconds of a run, fed back as job costs, give
+    another schedule and the same bits (FP32 and FP64); no block is busy
+    with two jobs at once, so the busy times add up to at most the grid's
+    time."""
+    specs = []
+    for k, spec in enumerate([fi.single_small(), fi.pnpoly_space(), fi.conv_mi50_space(),
+                              fi.gemm_space()]):
+        f = fi.runtimes(spec, 30 + k, fail_frac=0.7 if spec.name == "gemm" else 0.05)
+        g, _ = run_build(spec, f, "hamming" if k % 2 == 0 else "adjacent")
+        for alpha in (0.6, 0.85):
+            specs.append((g, alpha))
+    for prec in (ffg.F32, ffg.F64):
+        batch = ffg.PageRankBatch(specs, prec=prec, tol=1e-12)
+        batch.replan((0.1, 0.1, 0, 24))
+        batch.run()
+        batch.query()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.run()
+        e1.record()
+        it0, _, st = batch.query()
+        assert (st == 0).all()
+        xs0 = [_np(x) for x in batch.ranks]
+        busy = batch.times()
+        assert busy.shape == (len(specs),) and (busy > 0).all()
+        wall = e0.elapsed_time(e1) / 1e3
+        assert busy.sum() <= batch.plan.n_blocks * wall * 1.01 + 1e-4
+        n_blocks0 = batch.plan.n_blocks
+        for cost in (busy, busy[::-1].copy(), np.linspace(1.0, 50.0, len(specs))):
+            batch.replan((0.1, 0.1, 0, 24), job_cost=cost)
+            batch.run()
+            it, _, st = batch.query()
+            assert (st == 0).all()
+            np.testing.assert_array_equal(it, it0)
+            for x, x0 in zip(batch.ranks, xs0):
+                np.testing.assert_array_equal(_np(x), x0)
+        assert batch.plan.n_blocks == n_blocks0
+
+
+def test_batch_run_one_call_matches_separate_calls():
+    """ffg_batch_run -- every FFG, every solve, every C_p in one call -- is
+    bit-exact against the oracle's graphs, within the FP64 bars of its
+    ranks and C_p, and gives the bits of the separate calls; its
+    launches-only form replays from a CUDA graph."""
+    cases = [(fi.single_small(), 1, 0.03), (fi.pnpoly_space(), 2, 0.7),
+             (fi.conv_mi50_space(), 3, 0.3)]
+    cases += [(sp, 40 + k, 0.03) for k, sp in
+              enumerate(fi.tiny_spaces(5, seed0=15000, max_raw=3000))]
+    p = [0.0, 0.01, 0.05, 0.1]
+    specs, refs = [], []
+    for k, (spec, seed, fail) in enumerate(cases):
+        f = fi.runtimes(spec, seed, fail_frac=fail)
+        nbh = "hamming" if k % 2 == 0 else "adjacent"
+        og = oracle.build(spec, f, NBH[nbh][1])
+        if og.n_nodes == 0 or not og.is_min.any():
+            continue
+        fd = torch.from_numpy(f).cuda()
+        specs.append((ffg.Space.from_spec(spec), fd, NBH[nbh][0]))
+        xe = oracle.pagerank_exact(og, 0.85)
+        refs.append((og, xe, oracle.centrality(og, xe, p)))
+    bb = ffg.BuildBatch(specs)
+    batch = ffg.PageRankBatch([(g, 0.85) for g in bb.graphs], prec=ffg.F64, tol=1e-12)
+    cp_specs = [(g, fd, x) for g, (_, fd, _), x in zip(bb.graphs, specs, batch.ranks)]
+    sb = ffg.SpaceBatch(batch, builds=bb, cp_specs=cp_specs, p=p)
+    for g in bb.graphs:
+        g.out_idx.fill_(-1)
+        g.in_ptr.fill_(-1)
+    st, out = sb.run()
+    assert st == ffg.FFG_OK, ffg.ffg_last_error()
+    assert (out["build_status"] == 0).all() and (out["pr_status"] == 0).all()
+    for g, x, (og, xe, cpe) in zip(bb.graphs, batch.ranks, refs):
+        assert_same_graph(g, og)
+        assert np.abs(_np(x) - xe).sum() <= F64_L1
+    for row, (_, _, cpe) in zip(out["cp"], refs):
+        assert np.abs(row - cpe).max() <= F64_CP
+    xs = [_np(x) for x in batch.ranks]
+    # the separate calls: the same bits
+    bb.rerun()
+    batch.run()
+    it, res, sts = batch.query()
+    np.testing.assert_array_equal(it, out["iters"])
+    np.testing.assert_array_equal(res, out["residual"])
+    for x, x0 in zip(batch.ranks, xs):
+        np.testing.assert_array_equal(_np(x), x0)
+    np.testing.assert_array_equal(ffg.centrality_many(cp_specs, p), out["cp"])
+    # launches only, captured and replayed
+    cg = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(cg, stream=side):
+            sb.run(sync=False, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    for g, x in zip(bb.graphs, batch.ranks):
+        g.in_idx.fill_(-1)
+        x.fill_(0)
+    cg.replay()
+    torch.cuda.synchronize()
+    for g, x, x0, (og, _, _) in zip(bb.graphs, batch.ranks, xs, refs):
+        assert_same_graph(g, og)
+        np.testing.assert_array_equal(_np(x), x0)
+
+
 def test_batched_build_matches_per_space_builds():
     """All FFGs of many spaces at once (both neighbourhoods, ragged sizes,
     failures and ties): bit-exact against the oracle; a re-run from the
