@@ -350,8 +350,9 @@ ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec 
 /* Planning options.  A job whose cost exceeds `split` times the per-block
  * share of the batch gets its own blocks, about one per `grain` shares (the
  * others run on one block each); `max_blocks` caps the grid (0 = every
- * co-resident block); `block_warps` is 8 (256-thread blocks, several per SM)
- * or 24 (one 768-thread block per SM), 0 = 24; `claim` 1 selects the claim
+ * co-resident block); `block_warps` is 8 (256-thread blocks, several per SM),
+ * 16 (one 512-thread block per SM, 128 registers per thread) or 24 (one
+ * 768-thread block per SM), 0 = 24; `claim` 1 selects the claim
  * order, 0 the per-block lists; `fp64_form` (FFG_F64 only) keeps w as exact
  * 128-bit fixed point (1) or as double (2), 0 = fixed point when every
  * graph has at most 2^21 nodes.  `job_cost` (HOST, n_jobs positive finite

@@ -4,8 +4,9 @@ The tile shape is fixed (32 rows, one per lane; the gather step was chosen
 by a build-time sweep on the single large space); what varies with the
 workload is the schedule of a batch: which jobs get dedicated blocks
 (`split`), how many (`grain`), how large the grid is (`max_blocks`) and how
-wide its blocks are (`block_warps`: 8 warps, several blocks per SM, or 24,
-one block per SM) and whether blocks follow fixed per-block lists or claim
+wide its blocks are (`block_warps`: 8 warps, several blocks per SM; 16, one
+block per SM with room for every job pointer in registers; or 24, one block
+per SM) and whether blocks follow fixed per-block lists or claim
 jobs as they free up (`claim`).  ``tune`` runs the
 batch once per candidate (same workspace, re-planned), times it with CUDA
 events and leaves the fastest plan in place.
@@ -29,12 +30,14 @@ import numpy as np
 CANDIDATES = (
     (1.0, 1.0, 0, 8, 0),
     (0.5, 0.25, 0, 8, 0),
-    (0.5, 0.5, 0, 24, 0),
+    (1.0, 1.0, 0, 16, 0),
+    (0.5, 0.1, 0, 16, 0),
+    (0.1, 0.02, 0, 16, 0),
+    (0.05, 0.005, 0, 16, 0),
+    (0.02, 0.002, 0, 16, 0),
     (0.5, 0.1, 0, 24, 0),
-    (0.25, 0.05, 0, 24, 0),
     (0.1, 0.02, 0, 24, 0),
     (0.05, 0.005, 0, 24, 0),
-    (0.02, 0.002, 0, 24, 0),
     (0.5, 0.5, 0, 24, 1),
 )
 MEASURED = 3  # candidates re-planned with measured job costs

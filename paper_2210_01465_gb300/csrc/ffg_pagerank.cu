@@ -51,8 +51,13 @@ namespace {
 // Warps per block: a single solve runs one block of kWarpsSingle warps per
 // SM, so that all warps of an SM share one tile counter (warps of one SM are
 // not served equally: with several blocks per SM the youngest block finishes
-// last); a batch runs blocks of kWarpsBatch warps, several per SM, one job
-// (or one rank of a job) per block at a time.
+// last).  A batch runs one job (or one rank of a job) per block at a time, in
+// blocks of kWarpsBatch warps (several per SM), kWarpsBatchWide warps (one
+// per SM, 128 registers per thread) or kWarpsSingle warps (one per SM).  The
+// batch kernel holds each job's pointers in registers, where the single
+// kernel reads them from its parameters; at 80 registers per thread that
+// spills in the tile loop, so the 16-warp form, which has room for them,
+// runs the large jobs of a batch faster than the 24-warp one.
 #ifndef FFG_PR_WARPS
 #define FFG_PR_WARPS 24
 #endif
@@ -62,6 +67,7 @@ constexpr int kWarpsSingle = FFG_PR_WARPS;
 #endif
 constexpr int kWarpsSingle64 = FFG_PR_WARPS64;  // single FP64 solves
 constexpr int kWarpsBatch = 8;
+constexpr int kWarpsBatchWide = 16;
 constexpr int kMaxBlocks = 4096;
 constexpr uint64_t kTimeoutNs = 2000000000ULL;
 #ifndef FFG_PR_SEG
@@ -1089,7 +1095,7 @@ __device__ __forceinline__ Stream make_stream(unsigned char *s_dyn) {
 
 // One solve on the whole grid.
 template <typename T, int W>
-__global__ void __launch_bounds__(32 * W, W > kWarpsBatch ? 1 : FFG_PR_MINBLOCKS)
+__global__ void __launch_bounds__(32 * W, W == kWarpsBatch ? FFG_PR_MINBLOCKS : 1)
     k_pagerank(JobDev single) {
     extern __shared__ __align__(128) unsigned char s_dyn[];
     Stream st = make_stream<W>(s_dyn);
@@ -1097,7 +1103,7 @@ __global__ void __launch_bounds__(32 * W, W > kWarpsBatch ? 1 : FFG_PR_MINBLOCKS
 }
 
 template <typename T, int W>
-__global__ void __launch_bounds__(32 * W, W > kWarpsBatch ? 1 : FFG_PR_MINBLOCKS)
+__global__ void __launch_bounds__(32 * W, W == kWarpsBatch ? FFG_PR_MINBLOCKS : 1)
     k_pagerank_batch(const JobDev *__restrict__ jobs, const int2 *__restrict__ items,
                      const int *__restrict__ first, int *__restrict__ queue, int n_items) {
     extern __shared__ __align__(128) unsigned char s_dyn[];
@@ -1619,45 +1625,58 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, ffg_prec pre
     return w;
 }
 
+bool batch_width_ok(int warps) {
+    return warps == kWarpsBatch || warps == kWarpsBatchWide || warps == kWarpsSingle;
+}
+
+template <int W>
+ffg_status batch_blocks_w(ffg_prec prec, int *per_sm, int *sms) {
+    if (prec == FFG_F64) {
+        int a = 0, b = 0;
+        FFG_TRY((kernel_config<double, W>(&a, sms, true)));
+        FFG_TRY((kernel_config<F64x, W>(&b, sms, true)));
+        *per_sm = std::min(a, b);
+        return FFG_OK;
+    }
+    return kernel_config<float, W>(per_sm, sms, true);
+}
+
 // co-resident blocks of the batch kernel with `warps` warps per block
 ffg_status batch_blocks(ffg_prec prec, int warps, int *nb_max) {
     int per_sm = 0, sms = 0;
-    int a = 0, b = 0;
-    if (warps == kWarpsBatch) {
-        if (prec == FFG_F64) {
-            FFG_TRY((kernel_config<double, kWarpsBatch>(&a, &sms, true)));
-            FFG_TRY((kernel_config<F64x, kWarpsBatch>(&b, &sms, true)));
-            per_sm = std::min(a, b);
-        } else {
-            FFG_TRY((kernel_config<float, kWarpsBatch>(&per_sm, &sms, true)));
-        }
-    } else {
-        if (prec == FFG_F64) {
-            FFG_TRY((kernel_config<double, kWarpsSingle>(&a, &sms, true)));
-            FFG_TRY((kernel_config<F64x, kWarpsSingle>(&b, &sms, true)));
-            per_sm = std::min(a, b);
-        } else {
-            FFG_TRY((kernel_config<float, kWarpsSingle>(&per_sm, &sms, true)));
-        }
-    }
+    if (warps == kWarpsBatch) FFG_TRY(batch_blocks_w<kWarpsBatch>(prec, &per_sm, &sms));
+    else if (warps == kWarpsBatchWide) FFG_TRY(batch_blocks_w<kWarpsBatchWide>(prec, &per_sm, &sms));
+    else FFG_TRY(batch_blocks_w<kWarpsSingle>(prec, &per_sm, &sms));
     *nb_max = std::min(kMaxBlocks, sms * per_sm);
     return FFG_OK;
 }
 
-// plan tables are sized for the larger of the two grids, so that the
+// plan tables are sized for the largest of the grids, so that the
 // workspace does not depend on the tuning
 ffg_status batch_cap(ffg_prec prec, int *cap) {
-    int a = 0, b = 0;
+    int a = 0, b = 0, c = 0;
     FFG_TRY(batch_blocks(prec, kWarpsBatch, &a));
-    FFG_TRY(batch_blocks(prec, kWarpsSingle, &b));
-    *cap = std::max(a, b);
+    FFG_TRY(batch_blocks(prec, kWarpsBatchWide, &b));
+    FFG_TRY(batch_blocks(prec, kWarpsSingle, &c));
+    *cap = std::max(a, std::max(b, c));
     return FFG_OK;
+}
+
+// the batch kernel for the plan's precision and storage form of w
+template <int W>
+ffg_status launch_batch(ffg_prec prec, bool fx, const JobDev *jobs, const int2 *items,
+                        const int *first, int *queue, int ni, int nb, cudaStream_t stream) {
+    const JobDev none{};
+    if (prec == FFG_F32) return launch_pr<float, W>(jobs, items, first, queue, ni, nb, none, stream);
+    if (fx) return launch_pr<F64x, W>(jobs, items, first, queue, ni, nb, none, stream);
+    return launch_pr<double, W>(jobs, items, first, queue, ni, nb, none, stream);
 }
 
 }  // namespace
 }  // namespace ffg
 
-// per-block lists of 8-warp blocks: the fastest on the 234-space batch
+// per-block lists of 8-warp blocks, one job per block unless a job alone
+// outweighs a block's share
 const ffg_pr_tuning kDefaultTuning = {1.0, 1.0, 0, kWarpsBatch, 0, 0, nullptr};
 
 extern "C" size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs,
@@ -1695,12 +1714,11 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
         return set_error("workspace not 256-byte aligned"), FFG_ERR_INVALID_ARG;
     const ffg_pr_tuning tu = tuning ? *tuning : kDefaultTuning;
     const int warps = tu.block_warps ? tu.block_warps : kWarpsSingle;
-    if (!(tu.split > 0.0) || !(tu.grain > 0.0) || tu.max_blocks < 0 ||
-        (warps != kWarpsBatch && warps != kWarpsSingle) || (tu.claim != 0 && tu.claim != 1) ||
-        tu.fp64_form < 0 || tu.fp64_form > 2)
+    if (!(tu.split > 0.0) || !(tu.grain > 0.0) || tu.max_blocks < 0 || !batch_width_ok(warps) ||
+        (tu.claim != 0 && tu.claim != 1) || tu.fp64_form < 0 || tu.fp64_form > 2)
         return set_error("tuning: split and grain must be > 0, max_blocks >= 0, block_warps "
-                         "0, %d or %d, claim 0 or 1, fp64_form 0, 1 or 2",
-                         kWarpsBatch, kWarpsSingle),
+                         "0, %d, %d or %d, claim 0 or 1, fp64_form 0, 1 or 2",
+                         kWarpsBatch, kWarpsBatchWide, kWarpsSingle),
                FFG_ERR_INVALID_ARG;
     if (tu.job_cost)
         for (int j = 0; j < n_jobs; ++j)
@@ -1768,7 +1786,7 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
     if (!plan || plan->n_jobs < 1 || !plan->jobs || !plan->ctl || plan->n_blocks < 1)
         return set_error("plan is empty"), FFG_ERR_INVALID_ARG;
     const ffg_prec prec = static_cast<ffg_prec>(plan->prec);
-    if (plan->warps != kWarpsBatch && plan->warps != kWarpsSingle)
+    if (!batch_width_ok(plan->warps))
         return set_error("plan has %d warps per block", plan->warps), FFG_ERR_INVALID_ARG;
     int nb_max = 0;
     FFG_TRY(batch_blocks(prec, plan->warps, &nb_max));
@@ -1798,25 +1816,17 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
     FFG_TRY(scan_exclusive(static_cast<const int32_t *>(plan->tables[0]),
                            static_cast<int64_t *>(plan->tables[1]), plan->total_tiles,
                            static_cast<int64_t *>(plan->tables[2]), stream));
-    JobDev none{};
     const JobDev *jobs = static_cast<const JobDev *>(plan->jobs);
     const int2 *items = static_cast<const int2 *>(plan->items);
     const int *first = static_cast<const int *>(plan->first);
     int *queue = plan->claim ? static_cast<int *>(plan->queue) : nullptr;
     const int ni = plan->n_items, nb = plan->n_blocks;
     const bool fx = plan->w_form != 0;  // FP64 w stored in fixed point
-    if (plan->warps == kWarpsBatch) {
-        if (prec == FFG_F32)
-            return launch_pr<float, kWarpsBatch>(jobs, items, first, queue, ni, nb, none, stream);
-        if (fx)
-            return launch_pr<F64x, kWarpsBatch>(jobs, items, first, queue, ni, nb, none, stream);
-        return launch_pr<double, kWarpsBatch>(jobs, items, first, queue, ni, nb, none, stream);
-    }
-    if (prec == FFG_F32)
-        return launch_pr<float, kWarpsSingle>(jobs, items, first, queue, ni, nb, none, stream);
-    if (fx)
-        return launch_pr<F64x, kWarpsSingle>(jobs, items, first, queue, ni, nb, none, stream);
-    return launch_pr<double, kWarpsSingle>(jobs, items, first, queue, ni, nb, none, stream);
+    if (plan->warps == kWarpsBatch)
+        return launch_batch<kWarpsBatch>(prec, fx, jobs, items, first, queue, ni, nb, stream);
+    if (plan->warps == kWarpsBatchWide)
+        return launch_batch<kWarpsBatchWide>(prec, fx, jobs, items, first, queue, ni, nb, stream);
+    return launch_batch<kWarpsSingle>(prec, fx, jobs, items, first, queue, ni, nb, stream);
 }
 
 extern "C" ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *iters_out,

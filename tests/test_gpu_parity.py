@@ -400,7 +400,8 @@ def test_batch_tuning_changes_schedule_not_results():
     first = {}
     for tuning in ((1.0, 1.0, 0), (0.1, 0.1, 0), (5.0, 1.0, 3), (1.0, 1.0, 0, 8),
                    (0.1, 0.1, 0, 8), (0.1, 0.1, 0, 8, 1), (0.5, 0.5, 0, 24, 1),
-                   (1.0, 1.0, 0, 8, 0, 2), (0.1, 0.02, 0, 24, 0, 2)):
+                   (1.0, 1.0, 0, 16), (0.1, 0.02, 0, 16, 0), (0.5, 0.5, 0, 16, 1),
+                   (1.0, 1.0, 0, 8, 0, 2), (0.1, 0.02, 0, 24, 0, 2), (0.1, 0.02, 0, 16, 0, 2)):
         batch.replan(tuning)
         batch.run()
         it, res, st = batch.query()
@@ -433,7 +434,7 @@ def test_batch_measured_costs_change_schedule_not_results():
             specs.append((g, alpha))
     for prec in (ffg.F32, ffg.F64):
         batch = ffg.PageRankBatch(specs, prec=prec, tol=1e-12)
-        batch.replan((0.1, 0.1, 0, 24))
+        batch.replan((0.1, 0.1, 0, 16))
         batch.run()
         batch.query()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -449,7 +450,7 @@ def test_batch_measured_costs_change_schedule_not_results():
         assert busy.sum() <= batch.plan.n_blocks * wall * 1.01 + 1e-4
         n_blocks0 = batch.plan.n_blocks
         for cost in (busy, busy[::-1].copy(), np.linspace(1.0, 50.0, len(specs))):
-            batch.replan((0.1, 0.1, 0, 24), job_cost=cost)
+            batch.replan((0.1, 0.1, 0, 16), job_cost=cost)
             batch.run()
             it, _, st = batch.query()
             assert (st == 0).all()
