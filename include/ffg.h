@@ -320,7 +320,10 @@ typedef struct {
 } ffg_pr_job;
 
 /* Filled by pagerank_batch_plan; plain data owned by the caller (device
- * pointers point into the plan's workspace). */
+ * pointers point into the plan's workspace).  A batch of at most
+ * FFG_PR_PARAM_JOBS jobs also carries its job table in `params`, which
+ * pagerank_batch_run passes to the kernel as its parameters (30 KB). */
+#define FFG_PR_PARAM_JOBS 240
 typedef struct {
     int32_t prec, n_jobs, n_graphs, n_blocks, warps, n_items, claim;
     int32_t w_form;  /* FP64: 1 = w kept as exact fixed point, 0 = as double */
@@ -328,6 +331,8 @@ typedef struct {
     void *jobs, *graphs, *items, *first, *queue, *ctl;
     int64_t total_rows;
     void *tables[8];  /* per-row and per-tile tables of all graphs (internal) */
+    int32_t param_jobs, reserved; /* jobs in `params` (n_jobs or 0) */
+    uint64_t params[FFG_PR_PARAM_JOBS * 16]; /* the job table (internal) */
 } ffg_pr_batch;
 
 size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec);

@@ -68,6 +68,9 @@ class ffg_pr_job(C.Structure):
                 ("max_iter", C.c_int32), ("init", C.c_int32), ("ranks", C.c_void_p)]
 
 
+PARAM_JOBS = 240  # FFG_PR_PARAM_JOBS: batches up to this size pass their job table as parameters
+
+
 class ffg_pr_batch(C.Structure):
     _fields_ = [("prec", C.c_int32), ("n_jobs", C.c_int32), ("n_graphs", C.c_int32),
                 ("n_blocks", C.c_int32), ("warps", C.c_int32), ("n_items", C.c_int32),
@@ -75,7 +78,9 @@ class ffg_pr_batch(C.Structure):
                 ("total_tiles", C.c_int64), ("jobs", C.c_void_p),
                 ("graphs", C.c_void_p), ("items", C.c_void_p), ("first", C.c_void_p),
                 ("queue", C.c_void_p),
-                ("ctl", C.c_void_p), ("total_rows", C.c_int64), ("tables", C.c_void_p * 8)]
+                ("ctl", C.c_void_p), ("total_rows", C.c_int64), ("tables", C.c_void_p * 8),
+                ("param_jobs", C.c_int32), ("reserved", C.c_int32),
+                ("params", C.c_uint64 * (PARAM_JOBS * 16))]
 
 
 class ffg_build_job(C.Structure):

@@ -1129,6 +1129,48 @@ __global__ void __launch_bounds__(32 * W, W == kWarpsBatch ? FFG_PR_MINBLOCKS : 
     }
 }
 
+// The same with the job table in the kernel's parameters, for batches of at
+// most kParamJobs jobs.  A job's pointers are then read from the constant
+// bank where they are used, as in k_pagerank, instead of being held in
+// registers for the whole job: at 80 registers per thread those spilled in
+// the tile loop (the 24-warp kernel ran the 234-space batch 20 % slower).
+constexpr int kParamJobs = FFG_PR_PARAM_JOBS;
+static_assert(sizeof(JobDev) == 128 && sizeof(JobDev) * kParamJobs ==
+                                           sizeof(((ffg_pr_batch *)nullptr)->params),
+              "the plan holds the parameter job table");
+struct BatchParams {
+    const int2 *items;
+    const int *first;
+    int *queue;
+    int n_items, pad;
+    JobDev jobs[kParamJobs];
+};
+static_assert(sizeof(BatchParams) <= 32764, "kernel parameter limit");
+
+template <typename T, int W>
+__global__ void __launch_bounds__(32 * W, W == kWarpsBatch ? FFG_PR_MINBLOCKS : 1)
+    k_pagerank_batch_p(const __grid_constant__ BatchParams P) {
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    Stream st = make_stream<W>(s_dyn);
+    if (P.queue == nullptr) {
+        for (int i = P.first[blockIdx.x]; i < P.first[blockIdx.x + 1]; ++i) {
+            const int2 item = P.items[i];
+            if (!run_job<T, W>(P.jobs[item.x], item.y, st)) return;
+        }
+        return;
+    }
+    __shared__ int s_item;
+    while (true) {
+        __syncthreads();  // every thread has read the previous item
+        if (threadIdx.x == 0) s_item = atomicAdd(P.queue, 1);
+        __syncthreads();
+        const int i = s_item;
+        if (i >= P.n_items) return;
+        const int2 item = P.items[i];
+        if (!run_job<T, W>(P.jobs[item.x], item.y, st)) return;
+    }
+}
+
 // Layout kernels over every distinct graph of a batch: a global row or tile
 // index -> graph by binary search over the graphs' first rows or tiles.
 struct GraphDev {
@@ -1216,14 +1258,14 @@ ffg_status launch_layout(const ffg_graph *g, PrWs &w, cudaStream_t stream) {
     return scan_exclusive(w.cnt, w.tpre, tiles, w.scan, stream);
 }
 
-template <typename T, int W>
-ffg_status kernel_config(int *blocks_per_sm, int *sms, bool batch = false) {
+// co-resident blocks per SM of kernel `kern` (W warps per block); sets its
+// dynamic shared memory limit
+template <int W>
+ffg_status kernel_config(const void *kern, int *blocks_per_sm, int *sms) {
     int dev = 0;
     FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
     FFG_TRY(check_cuda(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev), "attr"));
     const size_t smem = pr_smem_bytes<W>();
-    const void *kern = batch ? reinterpret_cast<const void *>(k_pagerank_batch<T, W>)
-                             : reinterpret_cast<const void *>(k_pagerank<T, W>);
     FFG_TRY(check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             static_cast<int>(smem)),
                        "smem attribute"));
@@ -1235,23 +1277,37 @@ ffg_status kernel_config(int *blocks_per_sm, int *sms, bool batch = false) {
 }
 
 template <typename T, int W>
-ffg_status launch_pr(const JobDev *jobs, const int2 *items, const int *first, int *queue,
-                     int n_items, int nb, const JobDev &single, cudaStream_t stream) {
+ffg_status launch_single(const JobDev &single, int nb, cudaStream_t stream) {
     const size_t smem = pr_smem_bytes<W>();
-    if (jobs == nullptr) {
-        JobDev s = single;
-        void *args[] = {(void *)&s};
-        FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)k_pagerank<T, W>, dim3(nb),
-                                                       dim3(32 * W), args, smem, stream),
-                           "k_pagerank"));
-    } else {
-        void *args[] = {(void *)&jobs, (void *)&items, (void *)&first, (void *)&queue,
-                        (void *)&n_items};
-        FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)k_pagerank_batch<T, W>,
-                                                       dim3(nb), dim3(32 * W), args, smem,
-                                                       stream),
-                           "k_pagerank_batch"));
-    }
+    JobDev s = single;
+    void *args[] = {(void *)&s};
+    FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)k_pagerank<T, W>, dim3(nb),
+                                                   dim3(32 * W), args, smem, stream),
+                       "k_pagerank"));
+    count_launch();
+    return FFG_OK;
+}
+
+template <typename T, int W>
+ffg_status launch_pr(const JobDev *jobs, const int2 *items, const int *first, int *queue,
+                     int n_items, int nb, cudaStream_t stream) {
+    const size_t smem = pr_smem_bytes<W>();
+    void *args[] = {(void *)&jobs, (void *)&items, (void *)&first, (void *)&queue,
+                    (void *)&n_items};
+    FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)k_pagerank_batch<T, W>,
+                                                   dim3(nb), dim3(32 * W), args, smem, stream),
+                       "k_pagerank_batch"));
+    count_launch();
+    return FFG_OK;
+}
+
+template <typename T, int W>
+ffg_status launch_pr_param(const BatchParams &P, int nb, cudaStream_t stream) {
+    const size_t smem = pr_smem_bytes<W>();
+    void *args[] = {(void *)&P};
+    FFG_TRY(check_cuda(cudaLaunchCooperativeKernel((const void *)k_pagerank_batch_p<T, W>,
+                                                   dim3(nb), dim3(32 * W), args, smem, stream),
+                       "k_pagerank_batch_p"));
     count_launch();
     return FFG_OK;
 }
@@ -1263,7 +1319,7 @@ ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, in
     // more warps; FP32 is faster with more registers per warp
     constexpr int W = sizeof(typename Rows<T>::Real) == 8 ? kWarpsSingle64 : kWarpsSingle;
     int per_sm = 0, sms = 0;
-    FFG_TRY((kernel_config<T, W>(&per_sm, &sms)));
+    FFG_TRY((kernel_config<W>((const void *)k_pagerank<T, W>, &per_sm, &sms)));
     const int64_t tiles = (g->n_nodes + 31) / 32;
     int64_t max_res = int64_t(sms) * per_sm;
     if (max_res > kMaxBlocks) max_res = kMaxBlocks;
@@ -1288,7 +1344,7 @@ ffg_status launch(const ffg_graph *g, double alpha, double tol, int max_iter, in
     J.init = init;
     J.group = nb;
     J.pad = 0;
-    return launch_pr<T, W>(nullptr, nullptr, nullptr, nullptr, 0, nb, J, stream);
+    return launch_single<T, W>(J, nb, stream);
 }
 
 ffg_status read_result(const PrCtl *dctl, int32_t *iters_out, double *residual_out,
@@ -1387,8 +1443,11 @@ extern "C" ffg_status pagerank_query(const void *workspace, int32_t *iters_out,
 // item on every one of them), the others run on one block each, placed by
 // longest-processing-time-first on the least loaded block.
 // ---------------------------------------------------------------------------
+#include <string.h>
+
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <numeric>
 #include <queue>
 #include <unordered_map>
@@ -1629,16 +1688,26 @@ bool batch_width_ok(int warps) {
     return warps == kWarpsBatch || warps == kWarpsBatchWide || warps == kWarpsSingle;
 }
 
+// co-resident blocks per SM of both forms of the batch kernel
+template <typename T, int W>
+ffg_status batch_per_sm(int *per_sm, int *sms) {
+    int a = 0, b = 0;
+    FFG_TRY((kernel_config<W>((const void *)k_pagerank_batch<T, W>, &a, sms)));
+    FFG_TRY((kernel_config<W>((const void *)k_pagerank_batch_p<T, W>, &b, sms)));
+    *per_sm = std::min(a, b);
+    return FFG_OK;
+}
+
 template <int W>
 ffg_status batch_blocks_w(ffg_prec prec, int *per_sm, int *sms) {
     if (prec == FFG_F64) {
         int a = 0, b = 0;
-        FFG_TRY((kernel_config<double, W>(&a, sms, true)));
-        FFG_TRY((kernel_config<F64x, W>(&b, sms, true)));
+        FFG_TRY((batch_per_sm<double, W>(&a, sms)));
+        FFG_TRY((batch_per_sm<F64x, W>(&b, sms)));
         *per_sm = std::min(a, b);
         return FFG_OK;
     }
-    return kernel_config<float, W>(per_sm, sms, true);
+    return batch_per_sm<float, W>(per_sm, sms);
 }
 
 // co-resident blocks of the batch kernel with `warps` warps per block
@@ -1662,14 +1731,20 @@ ffg_status batch_cap(ffg_prec prec, int *cap) {
     return FFG_OK;
 }
 
-// the batch kernel for the plan's precision and storage form of w
+// the batch kernel for the plan's precision and storage form of w; with the
+// job table in its parameters when the plan carries it
 template <int W>
-ffg_status launch_batch(ffg_prec prec, bool fx, const JobDev *jobs, const int2 *items,
-                        const int *first, int *queue, int ni, int nb, cudaStream_t stream) {
-    const JobDev none{};
-    if (prec == FFG_F32) return launch_pr<float, W>(jobs, items, first, queue, ni, nb, none, stream);
-    if (fx) return launch_pr<F64x, W>(jobs, items, first, queue, ni, nb, none, stream);
-    return launch_pr<double, W>(jobs, items, first, queue, ni, nb, none, stream);
+ffg_status launch_batch(ffg_prec prec, bool fx, const BatchParams *P, const JobDev *jobs,
+                        const int2 *items, const int *first, int *queue, int ni, int nb,
+                        cudaStream_t stream) {
+    if (P) {
+        if (prec == FFG_F32) return launch_pr_param<float, W>(*P, nb, stream);
+        if (fx) return launch_pr_param<F64x, W>(*P, nb, stream);
+        return launch_pr_param<double, W>(*P, nb, stream);
+    }
+    if (prec == FFG_F32) return launch_pr<float, W>(jobs, items, first, queue, ni, nb, stream);
+    if (fx) return launch_pr<F64x, W>(jobs, items, first, queue, ni, nb, stream);
+    return launch_pr<double, W>(jobs, items, first, queue, ni, nb, stream);
 }
 
 }  // namespace
@@ -1777,6 +1852,9 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     plan->tables[3] = w.aflag;
     plan->tables[4] = w.apre;
     plan->tables[5] = w.ascan;
+    plan->param_jobs = n_jobs <= kParamJobs ? n_jobs : 0;
+    memset(plan->params, 0, sizeof(plan->params));
+    if (plan->param_jobs) memcpy(plan->params, jd.data(), sizeof(JobDev) * jd.size());
     return FFG_OK;
 }
 
@@ -1822,11 +1900,26 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
     int *queue = plan->claim ? static_cast<int *>(plan->queue) : nullptr;
     const int ni = plan->n_items, nb = plan->n_blocks;
     const bool fx = plan->w_form != 0;  // FP64 w stored in fixed point
+    // batches of at most kParamJobs jobs pass their job table as parameters
+    std::unique_ptr<BatchParams> params;
+    if (plan->param_jobs > 0) {
+        if (plan->param_jobs != plan->n_jobs || plan->param_jobs > kParamJobs)
+            return set_error("plan's parameter table does not match its jobs"),
+                   FFG_ERR_INVALID_ARG;
+        params.reset(new BatchParams());
+        params->items = items;
+        params->first = first;
+        params->queue = queue;
+        params->n_items = ni;
+        memcpy(params->jobs, plan->params, sizeof(JobDev) * size_t(plan->param_jobs));
+    }
+    const BatchParams *P = params.get();
     if (plan->warps == kWarpsBatch)
-        return launch_batch<kWarpsBatch>(prec, fx, jobs, items, first, queue, ni, nb, stream);
+        return launch_batch<kWarpsBatch>(prec, fx, P, jobs, items, first, queue, ni, nb, stream);
     if (plan->warps == kWarpsBatchWide)
-        return launch_batch<kWarpsBatchWide>(prec, fx, jobs, items, first, queue, ni, nb, stream);
-    return launch_batch<kWarpsSingle>(prec, fx, jobs, items, first, queue, ni, nb, stream);
+        return launch_batch<kWarpsBatchWide>(prec, fx, P, jobs, items, first, queue, ni, nb,
+                                             stream);
+    return launch_batch<kWarpsSingle>(prec, fx, P, jobs, items, first, queue, ni, nb, stream);
 }
 
 extern "C" ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *iters_out,

@@ -460,6 +460,41 @@ def test_batch_measured_costs_change_schedule_not_results():
         assert batch.plan.n_blocks == n_blocks0
 
 
+def test_batch_job_table_forms_agree():
+    """A batch of up to FFG_PR_PARAM_JOBS jobs passes its job table to the
+    kernel as parameters, a larger one reads it from device memory: the same
+    jobs give the same bits either way, in every block width and order."""
+    cases = [(fi.single_small(), 5, "hamming"), (fi.pnpoly_space(), 6, "adjacent"),
+             (fi.conv_mi50_space(), 7, "hamming")]
+    graphs, refs = [], []
+    for spec, seed, nbh in cases:
+        f = fi.runtimes(spec, seed)
+        og = oracle.build(spec, f, NBH[nbh][1])
+        g, _ = run_build(spec, f, nbh)
+        graphs.append(g)
+        refs.append(og)
+    dampings = np.linspace(0.5, 0.95, 81)
+    jobs = [(g, float(a)) for g in graphs for a in dampings]
+    assert len(jobs) > ffg.PARAM_JOBS
+    big = ffg.PageRankBatch(jobs, prec=ffg.F32, tol=1e-12)
+    small = ffg.PageRankBatch(jobs[:ffg.PARAM_JOBS], prec=ffg.F32, tol=1e-12)
+    assert big.plan.param_jobs == 0 and small.plan.param_jobs == ffg.PARAM_JOBS
+    for tuning in ((1.0, 1.0, 0, 8, 0), (0.1, 0.02, 0, 24, 0), (0.5, 0.5, 0, 16, 1)):
+        out = []
+        for b in (big, small):
+            b.replan(tuning)
+            b.run()
+            it, _, st = b.query()
+            assert (st == 0).all()
+            out.append((it, [_np(x) for x in b.ranks]))
+        np.testing.assert_array_equal(out[0][0][:ffg.PARAM_JOBS], out[1][0])
+        for x0, x1 in zip(out[0][1], out[1][1]):
+            np.testing.assert_array_equal(x0, x1)
+    for k in (0, 80, 81 + 40, 2 * 81 + 80):    # against the exact solve
+        xe = oracle.pagerank_exact(refs[k // 81], float(dampings[k % 81]))
+        assert np.abs(_np(big.ranks[k]).astype(np.float64) - xe).sum() <= 1e-5
+
+
 def test_batch_run_one_call_matches_separate_calls():
     """ffg_batch_run -- every FFG, every solve, every C_p in one call -- is
     bit-exact against the oracle's graphs, within the FP64 bars of its
