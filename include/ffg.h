@@ -357,15 +357,16 @@ ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec 
  * others run on one block each); `max_blocks` caps the grid (0 = every
  * co-resident block); `block_warps` is 8 (256-thread blocks, several per SM),
  * 16 (one 512-thread block per SM, 128 registers per thread) or 24 (one
- * 768-thread block per SM), 0 = 24; `claim` 1 selects the claim
- * order, 0 the per-block lists; `fp64_form` (FFG_F64 only) keeps w as exact
- * 128-bit fixed point (1) or as double (2), 0 = fixed point when every
- * graph has at most 2^21 nodes.  `job_cost` (HOST, n_jobs positive finite
+ * 768-thread block per SM), 0 = 24 for a batch of at most FFG_PR_PARAM_JOBS
+ * jobs (its job table then travels in the kernel's parameters), else 16;
+ * `claim` 1 selects the claim order, 0 the per-block lists; `fp64_form`
+ * (FFG_F64 only) keeps w as exact 128-bit fixed point (1) or as double (2),
+ * 0 = fixed point when every graph has at most 2^21 nodes.  `job_cost` (HOST, n_jobs positive finite
  * values in any one unit, or NULL) replaces the cost model (edges + 20 x
  * nodes, times an iteration estimate from the damping) that sizes the groups
  * and balances the blocks, e.g. with the block-seconds that
  * pagerank_batch_times measured on an earlier run; it is read during the
- * call only.  pagerank_batch_plan uses 1.0, 1.0, 0, 8, 0, 0, NULL.
+ * call only.  pagerank_batch_plan uses 0.05, 0.005, 0, 0, 0, 0, NULL.
  * They change only the schedule, never results or the workspace size. */
 typedef struct {
     double split, grain;

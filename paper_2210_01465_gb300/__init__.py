@@ -651,7 +651,7 @@ class PageRankBatch:
         self.ws = workspace(need, self.graphs[0].out_ptr.device)
         self.need = need
         self.plan = ffg_pr_batch()
-        self.tuning = (1.0, 1.0, 0, 8, 0)
+        self.tuning = (0.05, 0.005, 0, 0, 0)   # pagerank_batch_plan's defaults
         self.job_cost = None
         _check(pagerank_batch_plan(self.jobs, prec, self.ws.data_ptr(), need, self.plan,
                                    _stream_handle(stream)), "pagerank_batch_plan")

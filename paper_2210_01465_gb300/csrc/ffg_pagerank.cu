@@ -1750,9 +1750,11 @@ ffg_status launch_batch(ffg_prec prec, bool fx, const BatchParams *P, const JobD
 }  // namespace
 }  // namespace ffg
 
-// per-block lists of 8-warp blocks, one job per block unless a job alone
-// outweighs a block's share
-const ffg_pr_tuning kDefaultTuning = {1.0, 1.0, 0, kWarpsBatch, 0, 0, nullptr};
+// per-block lists; a job above 5 % of a block's share gets about one block per
+// 0.5 % of a share; the block width follows the size of the job table
+// (0.05 / 0.005 was the best or close to it on both the 234-space batch and
+// the 512-solve sweep)
+const ffg_pr_tuning kDefaultTuning = {0.05, 0.005, 0, 0, 0, 0, nullptr};
 
 extern "C" size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs,
                                                  ffg_prec prec) {
@@ -1788,7 +1790,11 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     if (!aligned256(workspace))
         return set_error("workspace not 256-byte aligned"), FFG_ERR_INVALID_ARG;
     const ffg_pr_tuning tu = tuning ? *tuning : kDefaultTuning;
-    const int warps = tu.block_warps ? tu.block_warps : kWarpsSingle;
+    // width 0: 24 warps when the job table travels in the kernel's parameters
+    // (no spills), else the 16-warp form with room for the job's pointers
+    const int warps = tu.block_warps          ? tu.block_warps
+                      : n_jobs <= kParamJobs ? kWarpsSingle
+                                             : kWarpsBatchWide;
     if (!(tu.split > 0.0) || !(tu.grain > 0.0) || tu.max_blocks < 0 || !batch_width_ok(warps) ||
         (tu.claim != 0 && tu.claim != 1) || tu.fp64_form < 0 || tu.fp64_form > 2)
         return set_error("tuning: split and grain must be > 0, max_blocks >= 0, block_warps "
