@@ -648,11 +648,15 @@ def run_batched(dev, stream, steps, warmup, rank=0, world=1):
     build_ms = float(np.mean([r[1] for r in recs]))
     iters = recs[-1][3].astype(np.float64)
     units = float((E * iters).sum())
+    pr_bytes = float(sum(pagerank_bytes(n, e, k, 4) for n, e, k in zip(N, E, iters)))
     from paper_2210_01465_gb300.multi import reduce_time_work
     n_spaces = len(graphs)
     ms, units_all = reduce_time_work(ms, units, device=dev)
     pr_ms, _ = reduce_time_work(pr_ms, 0.0, device=dev)
     _, n_spaces = reduce_time_work(0.0, n_spaces, device=dev)
+    _, pr_bytes = reduce_time_work(0.0, pr_bytes, device=dev)
+    peak, peak_kind = hbm_peak()
+    pr_gbs = pr_bytes / (pr_ms / 1e3) / 1e9
     # plain FP64, one solve per space
     t64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     units64 = 0.0
@@ -677,6 +681,12 @@ def run_batched(dev, stream, steps, warmup, rank=0, world=1):
             "plain_f64_edges_iters_per_s": units64 / (ms64 / 1e3),
             "batched_f32_vs_plain_f64_speedup": (units / (pr_ms / 1e3)) / (units64 / (ms64 / 1e3)),
             "blocks": int(batch.plan.n_blocks),
+            "roofline": {"bound": "hbm", "kernel": "k_pagerank_batch (one launch, every job)",
+                         "achieved": pr_gbs, "peak": peak, "unit": "GB/s",
+                         "frac": pr_gbs / peak, "peak_kind": peak_kind,
+                         "frac_of_nominal": pr_gbs / HBM_NOMINAL_GBS,
+                         "algorithmic_bytes": pr_bytes,
+                         "l2_resident": "mixed: most jobs fit in L2 one at a time"},
             "autotune": autotune_summary(batch, best, tried)}
 
 
@@ -706,6 +716,7 @@ def run_sweep(dev, stream, steps, warmup):
     dampings = (0.5, 0.7, 0.85, 0.95)
     batch = ffg.PageRankBatch([(g, a) for g in graphs for a in dampings], prec=ffg.F32, tol=TOL)
     E = np.array([g.n_edges for g in graphs for _ in dampings], dtype=np.float64)
+    N = np.array([g.n_nodes for g in graphs for _ in dampings], dtype=np.float64)
     from paper_2210_01465_gb300.autotune import tune
     best, tried = tune(batch)
     captured = True
@@ -742,10 +753,18 @@ def run_sweep(dev, stream, steps, warmup):
         ms.append(e0.elapsed_time(e1))
     m = float(np.mean(ms))
     units = float((E * it).sum())
+    pr_bytes = float(sum(pagerank_bytes(n, e, k, 4) for n, e, k in zip(N, E, it)))
+    peak, peak_kind = hbm_peak()
+    gbs = pr_bytes / (m / 1e3) / 1e9
     return {"workload": "64 spaces x 2 neighbourhoods x damping {0.5,0.7,0.85,0.95}: 128 FFG "
                         "builds + 512 FP32 PageRank solves per step, replayed from one CUDA "
                         "graph",
             "solves": len(E), "cuda_graph": captured, "ms_per_step": m,
+            "roofline": {"bound": "hbm", "scope": "the PageRank bytes over the whole replayed "
+                         "step (128 FFG builds included), so a lower bound for the solve",
+                         "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_kind": peak_kind, "frac_of_nominal": gbs / HBM_NOMINAL_GBS,
+                         "algorithmic_bytes": pr_bytes},
             "solves_per_s": len(E) / (m / 1e3), "value": units / (m / 1e3), "unit": UNIT,
             "blocks": int(batch.plan.n_blocks),
             "autotune": autotune_summary(batch, best, tried)}
