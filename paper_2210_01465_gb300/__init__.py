@@ -416,6 +416,39 @@ class Graph:
     n_minima = property(lambda self: int(self.c.n_minima))
     f_opt = property(lambda self: float(self.c.f_opt))
 
+    _ARRAYS = ("out_ptr", "in_ptr", "out_idx", "in_idx", "outdeg", "node_raw", "is_min")
+
+    def save(self, path):
+        """Checkpoint the graph as a CSR ``.npz`` (host copies of every array and
+        the sizes); ``load_graph`` restores it."""
+        e = self.n_edges
+        arrays = {}
+        for name in self._ARRAYS:
+            t = getattr(self, name)
+            arrays[name] = (t[:e] if name in ("out_idx", "in_idx") else t).cpu().numpy()
+        np.savez(path, n_raw=self.n_raw, n_nodes=self.n_nodes, n_edges=e,
+                 n_minima=self.n_minima, f_opt=self.f_opt, nbh=getattr(self, "nbh", -1),
+                 **arrays)
+
+
+def load_graph(path, device="cuda") -> Graph:
+    """A graph saved by ``Graph.save``, in new tensors on ``device``."""
+    torch = _torch()
+    with np.load(path) as z:
+        g = Graph(int(z["n_raw"]), int(z["n_nodes"]), int(z["n_edges"]), int(z["n_minima"]),
+                  float(z["f_opt"]), device)
+        for name in Graph._ARRAYS:
+            src = torch.from_numpy(np.ascontiguousarray(z[name]))
+            dst = getattr(g, name)
+            if name in ("out_idx", "in_idx"):
+                dst = dst[:src.numel()]
+            if dst.shape != src.shape or dst.dtype != src.dtype:
+                raise ValueError(f"{path}: array {name} has the wrong shape or type")
+            dst.copy_(src)
+        if int(z["nbh"]) >= 0:
+            g.nbh = int(z["nbh"])
+    return g
+
 
 def _check(st, where, ok=(FFG_OK,)):
     if st not in ok:

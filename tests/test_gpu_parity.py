@@ -722,3 +722,26 @@ def test_minima_fraction_bit_exact():
         frac, node = ffg.minima_fraction(g, fd)
         np.testing.assert_array_equal(_np(frac), oracle.minima_fraction(og))
         np.testing.assert_array_equal(_np(node), np.flatnonzero(og.is_min))
+
+
+def test_graph_checkpoint_resumes_on_gpu(tmp_path):
+    """An FFG saved as a CSR .npz and loaded back onto the GPU is the same
+    graph and gives the same ranks bit for bit; a solve resumed from saved
+    ranks converges at once."""
+    spec = fi.pnpoly_space()
+    f = fi.runtimes(spec, 9, fail_frac=0.3)
+    og = oracle.build(spec, f, oracle.HAMMING)
+    g, _ = run_build(spec, f, "hamming")
+    x, it, res, conv = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64)
+    path = tmp_path / "ffg.npz"
+    g.save(path)
+    np.save(tmp_path / "ranks.npy", _np(x))
+    h = ffg.load_graph(path, device="cuda")
+    assert_same_graph(h, og)
+    y, it2, res2, conv2 = ffg.pagerank(h, 0.85, 1e-12, prec=ffg.F64)
+    assert conv and conv2 and it2 == it
+    np.testing.assert_array_equal(_np(y), _np(x))
+    x0 = torch.from_numpy(np.load(tmp_path / "ranks.npy")).cuda()
+    z, it3, res3, conv3 = ffg.pagerank(h, 0.85, 1e-12, prec=ffg.F64, init=x0)
+    assert conv3 and it3 <= 2
+    assert np.abs(_np(z) - oracle.pagerank_exact(og, 0.85)).sum() <= F64_L1
