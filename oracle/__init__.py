@@ -35,6 +35,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ffg_oracle.c")
 _HDR = os.path.join(_HERE, "ffg_oracle.h")
 LIB_PATH = os.path.join(_HERE, "libffg_oracle.so")
+_TEST_SRC = os.path.join(_HERE, "test_oracle.c")
+TEST_EXE = os.path.join(_HERE, "test_oracle")
 
 HAMMING, ADJACENT = 0, 1
 _KIND = {"prod_le": 0, "prod_ge": 1, "divides": 2, "prod_le_prod": 3}
@@ -49,15 +51,35 @@ class OracleError(RuntimeError):
 
 
 def compile_oracle(force: bool = False) -> str:
-    """Compile ffg_oracle.c with gcc into a shared library next to it."""
+    """Compile ffg_oracle.c with gcc into a shared library next to it, and the
+    C self-test (``test_oracle.c``) into an executable beside it."""
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
-        return LIB_PATH
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
-                    "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"], check=True)
-    os.replace(tmp, LIB_PATH)
+    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
+                        "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, LIB_PATH)
+    compile_self_test(force)
     return LIB_PATH
+
+
+def compile_self_test(force: bool = False) -> str:
+    """Compile the oracle's C self-test (test_oracle.c + ffg_oracle.c)."""
+    newest = max(os.path.getmtime(p) for p in (_SRC, _HDR, _TEST_SRC))
+    if not force and os.path.exists(TEST_EXE) and os.path.getmtime(TEST_EXE) >= newest:
+        return TEST_EXE
+    tmp = TEST_EXE + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
+                    "-I", _HERE, "-o", tmp, _TEST_SRC, _SRC, "-lm"], check=True)
+    os.replace(tmp, TEST_EXE)
+    return TEST_EXE
+
+
+def run_self_test() -> tuple[int, str]:
+    """Run the C self-test; returns (exit status, its output)."""
+    exe = compile_self_test()
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    return r.returncode, r.stdout + r.stderr
 
 
 class _Clause(C.Structure):
