@@ -413,12 +413,13 @@ def run_gpu(args):
         except Exception as e:  # reported, never fatal: the bench line stands without it
             cpu_all = {"unavailable": f"{type(e).__name__}: {e}"}
 
-    scale = exact = None
+    scale = exact = rows = None
     if not args.no_batched:
         scale = run_scale(dev, stream)
         f64_solve = {n: (statistics.mean(ea.elapsed_time(eb) for (m, ea, eb, _) in recs64 if m == n),
                          statistics.mean(it for (m, _, _, it) in recs64 if m == n)) for n in nbhs}
         exact = run_exact(ffg, graphs, fd, dev, stream, f64_solve)
+        rows = run_rows(ffg, graphs[ffg.HAMMING], dev, f64_solve[ffg.HAMMING])
     batched = sweep = None
     if not args.no_batched:
         batched = run_batched(dev, stream, steps=max(3, args.steps // 10), warmup=1,
@@ -453,6 +454,7 @@ def run_gpu(args):
                          "l2_resident": True},
             "beyond_l2": scale,
             "exact_dag": exact,
+            "row_partitioned": rows,
             "batched": batched,
             "sweep": sweep,
             "cpu_baseline": cpu,
@@ -468,6 +470,37 @@ def run_gpu(args):
 
 
 BATCH_P = [0.01, 0.02, 0.05, 0.10, 0.20]
+
+
+def run_rows(ffg, g, dev, f64_single, parts=4, reps=3):
+    """The row-partitioned solve of the single large space's Hamming FFG in
+    one process: ``parts`` row ranges standing for ranks (laid out once; one
+    launch per range and iteration, a host read of the sums per iteration, no
+    exchange needed), FP64, host-timed, next to the persistent single-launch
+    solve, which it equals bit for bit."""
+    import torch
+    from paper_2210_01465_gb300.multi import RowRange, solve_rows, split_rows
+    try:
+        bounds = split_rows(g.in_ptr.cpu().numpy(), parts)
+        ranges = [RowRange(g, a, b, ffg.F64) for a, b in bounds]   # laid out once
+        x_ref, it_ref, _, _ = ffg.pagerank(g, DAMPING, TOL, prec=ffg.F64)
+        ts = []
+        for k in range(reps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            y, it, res, conv = solve_rows(g, ranges, DAMPING, TOL, prec=ffg.F64)
+            torch.cuda.synchronize(dev)
+            if k:
+                ts.append(time.perf_counter() - t0)
+        ms = 1e3 * statistics.median(ts)
+        return {"workload": f"single large space, Hamming FFG, FP64, {parts} row ranges in one "
+                            "process (host-driven iterations)",
+                "ranges": bounds, "iters": it, "ms": ms, "us_per_iter": 1e3 * ms / it,
+                "single_launch_ms": f64_single[0],
+                "single_launch_us_per_iter": 1e3 * f64_single[0] / f64_single[1],
+                "bit_exact_vs_single": bool(torch.equal(y, x_ref)) and it == it_ref}
+    except Exception as e:   # reported; the bench line stands without it
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def run_exact(ffg, graphs, fd, dev, stream, f64_solve, reps=3):

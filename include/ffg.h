@@ -305,6 +305,60 @@ size_t walk_workspace_bytes(void);
 ffg_status walk_simulate(const ffg_graph *g, uint64_t seed, int64_t n_walks, uint64_t *counts,
                          void *workspace, size_t ws_bytes, int64_t *steps_out, void *stream);
 
+/* ---- PageRank over a range of rows: the row-partitioned solve ----
+ * The iteration of pagerank_solve (Sec. VII-B) split by rows, for a graph
+ * shared by several ranks: a rank owns rows [row0, row1) and, per iteration,
+ * forms w' of its rows from w of every row, where w = x / outdeg per row (x
+ * for rows without out-edges).  Between iterations the ranks exchange their
+ * rows of w' (an all-gather) and add their sums (an all-reduce); that host
+ * side is paper_2210_01465_gb300.multi.  w is stored per row in
+ * pagerank_rows_w_bytes(prec) opaque bytes (FFG_F32: a float; FFG_F64: an
+ * exact 128-bit fixed-point value, so that a row-partitioned FP64 solve
+ * equals pagerank_solve's bit for bit).
+ *
+ * pagerank_rows_workspace_bytes reads in_ptr[row0] and in_ptr[row1] from
+ * the device (synchronously) and returns the range's workspace size (0 on
+ * bad arguments).  pagerank_rows_prepare lays out the range's in-edges
+ * (the same tiles and descriptors as pagerank_prepare, their offsets taken
+ * from the global row); it also reads those two values.
+ *
+ * pagerank_rows_run enqueues one operation on the range (no host read, no
+ * synchronisation).  `sums` (DEVICE, 4 uint64, added to, never cleared):
+ * [0] residual sum |x' - x|, [1] dangling mass, [2] sum of x, each fixed
+ * point with quantum 2^-60, and [3] the number of bounded waits that
+ * expired (then report FFG_ERR_TIMEOUT; results are undefined).  w_in,
+ * w_out: DEVICE, n_nodes w elements each (every row; w_out's rows of the
+ * range are written).  ranks: DEVICE, n_nodes reals of the precision.
+ *   FFG_ROWS_INIT:  w_out from x0 = ranks (or 1/n_nodes when NULL); sums[1].
+ *   FFG_ROWS_STEP:  w_out = one iteration on w_in with `damping` and the
+ *                   previous dangling mass `dangling` (sums[1] of every
+ *                   rank, fixed point); sums[0], sums[1], sums[3].
+ *   FFG_ROWS_SUM:   sums[2] from w_in.
+ *   FFG_ROWS_WRITE: ranks = x * scale from w_in (scale = 1 / sum of x).
+ * Stop as pagerank_solve does: residual < tol, or (FFG_F32) a residual that
+ * stops decreasing, or max_iter. */
+typedef enum { FFG_ROWS_INIT = 0, FFG_ROWS_STEP = 1, FFG_ROWS_SUM = 2, FFG_ROWS_WRITE = 3 } ffg_rows_kind;
+
+typedef struct {
+    int32_t op, reserved;  /* ffg_rows_kind */
+    double damping;        /* STEP */
+    uint64_t dangling;     /* STEP */
+    double scale;          /* WRITE */
+    const void *w_in;
+    void *w_out;
+    void *ranks;
+    uint64_t *sums;
+} ffg_rows_op;
+
+size_t pagerank_rows_w_bytes(ffg_prec prec);
+size_t pagerank_rows_workspace_bytes(const ffg_graph *g, int64_t row0, int64_t row1,
+                                     ffg_prec prec);
+ffg_status pagerank_rows_prepare(const ffg_graph *g, int64_t row0, int64_t row1, ffg_prec prec,
+                                 void *workspace, size_t ws_bytes, void *stream);
+ffg_status pagerank_rows_run(const ffg_graph *g, int64_t row0, int64_t row1, ffg_prec prec,
+                             const ffg_rows_op *op, void *workspace, size_t ws_bytes,
+                             void *stream);
+
 /* ---- batched PageRank: many solves in one persistent launch ----
  * A job is one PageRank solve (same definition and stopping rules as
  * pagerank_solve): graph g (host struct with DEVICE arrays), damping, tol,

@@ -105,6 +105,15 @@ class ffg_cp_job(C.Structure):
     _fields_ = [("g", C.POINTER(ffg_graph)), ("fitness_raw", C.c_void_p), ("ranks", C.c_void_p)]
 
 
+class ffg_rows_op(C.Structure):
+    _fields_ = [("op", C.c_int32), ("reserved", C.c_int32), ("damping", C.c_double),
+                ("dangling", C.c_uint64), ("scale", C.c_double), ("w_in", C.c_void_p),
+                ("w_out", C.c_void_p), ("ranks", C.c_void_p), ("sums", C.c_void_p)]
+
+
+ROWS_INIT, ROWS_STEP, ROWS_SUM, ROWS_WRITE = 0, 1, 2, 3
+
+
 class ffg_batch_desc(C.Structure):
     _fields_ = [("build", C.POINTER(ffg_build_batch)), ("pagerank", C.POINTER(ffg_pr_batch)),
                 ("cp_jobs", C.POINTER(ffg_cp_job)), ("n_cp_jobs", C.c_int32),
@@ -129,6 +138,8 @@ ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
                 "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
                 "pagerank_batch_plan_tuned",
                 "pagerank_batch_run", "pagerank_batch_query", "pagerank_batch_times",
+                "pagerank_rows_w_bytes", "pagerank_rows_workspace_bytes",
+                "pagerank_rows_prepare", "pagerank_rows_run",
                 "centrality_workspace_bytes", "centrality_proportion",
                 "centrality_batch_workspace_bytes", "centrality_batch", "ffg_batch_run",
                 "ffg_status_str",
@@ -186,6 +197,13 @@ def load(path: str | None = None):
     lib.pagerank_batch_run.argtypes = [P(ffg_pr_batch), vp]
     lib.pagerank_batch_query.argtypes = [P(ffg_pr_batch), vp, vp, vp, vp]
     lib.pagerank_batch_times.argtypes = [P(ffg_pr_batch), vp, vp]
+    lib.pagerank_rows_w_bytes.argtypes = [C.c_int]
+    lib.pagerank_rows_w_bytes.restype = sz
+    lib.pagerank_rows_workspace_bytes.argtypes = [P(ffg_graph), i64, i64, C.c_int]
+    lib.pagerank_rows_workspace_bytes.restype = sz
+    lib.pagerank_rows_prepare.argtypes = [P(ffg_graph), i64, i64, C.c_int, vp, sz, vp]
+    lib.pagerank_rows_run.argtypes = [P(ffg_graph), i64, i64, C.c_int, P(ffg_rows_op), vp, sz,
+                                      vp]
     lib.centrality_workspace_bytes.argtypes = [i32]
     lib.centrality_workspace_bytes.restype = sz
     lib.centrality_proportion.argtypes = [P(ffg_graph), vp, vp, C.c_int, vp, i32, vp, vp, sz, vp]
@@ -320,6 +338,27 @@ def pagerank_batch_times(plan: "ffg_pr_batch", stream: int = 0):
     s = load().pagerank_batch_times(C.byref(plan), C.c_void_p(out.ctypes.data),
                                     C.c_void_p(stream))
     return int(s), out
+
+
+def pagerank_rows_w_bytes(prec: int) -> int:
+    return int(load().pagerank_rows_w_bytes(int(prec)))
+
+
+def pagerank_rows_workspace_bytes(g: "ffg_graph", row0: int, row1: int, prec: int) -> int:
+    return int(load().pagerank_rows_workspace_bytes(C.byref(g), int(row0), int(row1), int(prec)))
+
+
+def pagerank_rows_prepare(g: "ffg_graph", row0: int, row1: int, prec: int, ws: int,
+                          ws_bytes: int, stream: int = 0) -> int:
+    return int(load().pagerank_rows_prepare(C.byref(g), int(row0), int(row1), int(prec),
+                                            C.c_void_p(ws), int(ws_bytes), C.c_void_p(stream)))
+
+
+def pagerank_rows_run(g: "ffg_graph", row0: int, row1: int, prec: int, op: "ffg_rows_op",
+                      ws: int, ws_bytes: int, stream: int = 0) -> int:
+    return int(load().pagerank_rows_run(C.byref(g), int(row0), int(row1), int(prec),
+                                        C.byref(op), C.c_void_p(ws), int(ws_bytes),
+                                        C.c_void_p(stream)))
 
 
 def pagerank_query(ws: int, stream: int = 0):

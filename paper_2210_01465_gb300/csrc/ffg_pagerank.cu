@@ -379,11 +379,15 @@ __global__ void k_perm(const int64_t *__restrict__ apre, int64_t n, int32_t *__r
 // holds the lanes that have it.  Offsets fit int32 (n < 2^31); INT32_MAX
 // marks an exhausted list.  The in-edges of the slots before this tile
 // number in_ptr[perm[32t]] when that row has in-edges (all earlier slots
-// hold smaller rows with in-edges), else all e of them.
+// hold smaller rows with in-edges), else all of them (e).
+// A range of rows of a larger graph is laid out the same way: in_ptr then
+// starts at the range's first row (its first in-edge is number ebase), e is
+// the range's end, and offsets are taken from the global row (row0 + local
+// row), so that they index the w of every row.
 __device__ void layout_tile(const int64_t *__restrict__ in_ptr,
                             const int32_t *__restrict__ in_idx,
-                            const int32_t *__restrict__ perm, int64_t n, int64_t e,
-                            uint2 *__restrict__ desc, int32_t *__restrict__ cnt,
+                            const int32_t *__restrict__ perm, int64_t n, int64_t e, int64_t ebase,
+                            int64_t row0, uint2 *__restrict__ desc, int32_t *__restrict__ cnt,
                             uint2 *__restrict__ tinfo, int64_t t, int lane) {
     const int64_t slot = (t << 5) + lane;
     int32_t vi = 0;
@@ -395,9 +399,10 @@ __device__ void layout_tile(const int64_t *__restrict__ in_ptr,
     }
     const int64_t c0 = __shfl_sync(0xffffffffu, cur, 0);  // slot 32t exists
     const int64_t z0 = __shfl_sync(0xffffffffu, end, 0);
-    const int64_t dbeg = desc_begin(z0 > c0 ? c0 : e, t);
+    const int64_t dbeg = desc_begin((z0 > c0 ? c0 : e) - ebase, t);
     uint2 *out = desc + dbeg;
-    int32_t head = cur < end ? __ldg(in_idx + cur) - vi : INT32_MAX;
+    const int32_t row = static_cast<int32_t>(row0 + vi);  // global row, < 2^31
+    int32_t head = cur < end ? __ldg(in_idx + cur) - row : INT32_MAX;
     int k = 0;
     while (true) {
         const int32_t m = __reduce_min_sync(0xffffffffu, head);
@@ -408,7 +413,7 @@ __device__ void layout_tile(const int64_t *__restrict__ in_ptr,
         ++k;
         if (hit) {
             ++cur;
-            head = cur < end ? __ldg(in_idx + cur) - vi : INT32_MAX;
+            head = cur < end ? __ldg(in_idx + cur) - row : INT32_MAX;
         }
     }
     const int padded = (k + kU - 1) / kU * kU;
@@ -421,13 +426,13 @@ __device__ void layout_tile(const int64_t *__restrict__ in_ptr,
 
 __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout(
     const int64_t *__restrict__ in_ptr, const int32_t *__restrict__ in_idx,
-    const int32_t *__restrict__ perm, int64_t n, int64_t e, uint2 *__restrict__ desc,
-    int32_t *__restrict__ cnt, uint2 *__restrict__ tinfo) {
+    const int32_t *__restrict__ perm, int64_t n, int64_t e, int64_t ebase, int64_t row0,
+    uint2 *__restrict__ desc, int32_t *__restrict__ cnt, uint2 *__restrict__ tinfo) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t ntiles = (n + 31) >> 5;
     const int64_t step = int64_t(gridDim.x) * (kLayoutThreads / 32);
     for (int64_t t = int64_t(blockIdx.x) * (kLayoutThreads / 32) + warp; t < ntiles; t += step)
-        layout_tile(in_ptr, in_idx, perm, n, e, desc, cnt, tinfo, t, lane);
+        layout_tile(in_ptr, in_idx, perm, n, e, ebase, row0, desc, cnt, tinfo, t, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -842,14 +847,21 @@ struct LoopState {
     uint64_t t0;  // when all ranks had started (for the job's busy time)
 };
 
+// the teleport term (alpha * D + 1 - alpha) / n from the fixed-point dangling
+// mass D, one rounding per operation (also in the row-range form, so that
+// both give the same bits)
+__device__ __forceinline__ double teleport(double alpha, unsigned long long d_fix, int64_t n) {
+    const double d = static_cast<double>(d_fix) / kFix;
+    return __dsub_rn(__dadd_rn(__dmul_rn(alpha, d), 1.0), alpha) / static_cast<double>(n);
+}
+
 // thread 0, after the barrier of an iteration: read the job's sums, decide
 // whether to stop, and publish the next teleport term
 template <typename T>
 __device__ __forceinline__ void advance(const JobDev &J, LoopState &ls, const PrCtl *ctl, int buf,
                                         T *s_c, bool count_iter) {
     const double r = static_cast<double>(__ldcg(&ctl->acc[buf][0])) / kFix;
-    const double d = static_cast<double>(__ldcg(&ctl->acc[buf][1])) / kFix;
-    *s_c = static_cast<T>((J.alpha * d + 1.0 - J.alpha) / static_cast<double>(J.n));
+    *s_c = static_cast<T>(teleport(J.alpha, __ldcg(&ctl->acc[buf][1]), J.n));
     if (!count_iter) return;  // the prologue: no iteration yet
     ls.prev_res = ls.res;
     ls.res = r;
@@ -1221,8 +1233,8 @@ __global__ void __launch_bounds__(kLayoutThreads) k_pr_layout_batch(const GraphD
     for (int64_t gt = int64_t(blockIdx.x) * (kLayoutThreads / 32) + warp; gt < total_tiles;
          gt += step) {
         const GraphDev g = gr[graph_of(gr, n_graphs, gt, true)];
-        layout_tile(g.in_ptr, g.in_idx, g.perm, g.n, g.e, g.desc, g.cnt, g.tinfo, gt - g.tile0,
-                    lane);
+        layout_tile(g.in_ptr, g.in_idx, g.perm, g.n, g.e, 0, 0, g.desc, g.cnt, g.tinfo,
+                    gt - g.tile0, lane);
     }
 }
 
@@ -1252,7 +1264,7 @@ ffg_status launch_layout(const ffg_graph *g, PrWs &w, cudaStream_t stream) {
     count_launch();
     FFG_TRY(check_launch("k_perm"));
     k_pr_layout<<<grid_for(tiles, kLayoutThreads / 32, sms), kLayoutThreads, 0, stream>>>(
-        g->in_ptr, g->in_idx, w.perm, n, g->n_edges, w.desc, w.cnt, w.tinfo);
+        g->in_ptr, g->in_idx, w.perm, n, g->n_edges, 0, 0, w.desc, w.cnt, w.tinfo);
     count_launch();
     FFG_TRY(check_launch("k_pr_layout"));
     return scan_exclusive(w.cnt, w.tpre, tiles, w.scan, stream);
@@ -1434,6 +1446,334 @@ extern "C" ffg_status pagerank_query(const void *workspace, int32_t *iters_out,
         return set_error("workspace NULL or misaligned"), FFG_ERR_INVALID_ARG;
     const PrCtl *ctl = static_cast<const PrCtl *>(workspace);
     return read_result(ctl, iters_out, residual_out, static_cast<cudaStream_t>(stream_));
+}
+
+// ---------------------------------------------------------------------------
+// PageRank over a range of rows: the row-partitioned form of the solve.  A
+// rank owns rows [row0, row1); per iteration it forms w' of its rows from w
+// of every row, and the ranks exchange their rows of w' and their
+// fixed-point sums between iterations (host side).  One launch per
+// iteration, no grid barrier: the exchange is the synchronisation.
+// ---------------------------------------------------------------------------
+namespace ffg {
+namespace {
+
+struct RowsWs {
+    double *rinv;   // FP64: 1 / outdeg per row of the range
+    uint2 *desc;
+    int32_t *cnt;
+    uint2 *tinfo;
+    int64_t *tpre;
+    int64_t *scan;
+    int32_t *perm;
+    int32_t *aflag;
+    int64_t *apre;
+    int64_t *ascan;
+    size_t bytes;
+};
+
+// The descriptors come last, so that every table's place depends on the
+// number of rows only: an iteration finds them without knowing the range's
+// in-edges (which would take a device read).
+RowsWs carve_rows(void *base, int64_t n, int64_t e) {
+    Carver c(base);
+    RowsWs w;
+    const int64_t tiles = (n + 31) / 32;
+    w.rinv = c.take<double>(size_t(n));
+    w.cnt = c.take<int32_t>(size_t(tiles));
+    w.tinfo = c.take<uint2>(size_t(tiles));
+    w.tpre = c.take<int64_t>(size_t(tiles) + 1);
+    w.scan = c.take<int64_t>(size_t(scan_scratch_elems(tiles)));
+    w.perm = c.take<int32_t>(size_t(n));
+    w.aflag = c.take<int32_t>(size_t(n));
+    w.apre = c.take<int64_t>(size_t(n) + 1);
+    w.ascan = c.take<int64_t>(size_t(scan_scratch_elems(n)));
+    w.desc = c.take<uint2>(size_t(desc_capacity(n, e)));
+    w.bytes = c.off;
+    return w;
+}
+
+// One range's view: rows are local (0 .. n-1, global row0 + local), w
+// pointers are shifted by row0 so that local rows index them directly.
+struct RowsDev {
+    const int32_t *outdeg;  // of the range's rows
+    const uint2 *desc;
+    const uint2 *tinfo;
+    const int32_t *perm;
+    const int64_t *apre;
+    double *rinv;
+    const void *w_in;       // w of every row, shifted by row0
+    void *w_out;            // w' of every row, shifted by row0
+    void *ranks;            // shifted by row0
+    unsigned long long *sums;
+    int64_t n, n_all;       // rows of the range, of the graph
+    double alpha, scale;
+    unsigned long long dangling;
+};
+
+template <int W>
+__device__ __forceinline__ void add_sums(const RowsDev &R, const Fix3 &f) {
+    const Fix3 b = block_sum_fix<W>(f);
+    if (threadIdx.x == 0) {
+        if (b.r) atomicAdd(R.sums + 0, static_cast<unsigned long long>(b.r));
+        if (b.d) atomicAdd(R.sums + 1, static_cast<unsigned long long>(b.d));
+        if (b.s) atomicAdd(R.sums + 2, static_cast<unsigned long long>(b.s));
+    }
+}
+
+// w of the range's rows from the start vector (ranks, or 1/n_all), the
+// per-row reciprocals, and the range's dangling mass
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_init(const RowsDev R) {
+    using WS = typename Rows<T>::W;
+    using Rr = typename Rows<T>::Real;
+    WS *wo = static_cast<WS *>(R.w_out);
+    const Rr *x = static_cast<const Rr *>(R.ranks);
+    const double inv_n = 1.0 / static_cast<double>(R.n_all);
+    Fix3 f;
+    for (int64_t v = int64_t(blockIdx.x) * 256 + threadIdx.x; v < R.n;
+         v += int64_t(gridDim.x) * 256) {
+        const double x0 = x ? static_cast<double>(x[v]) : inv_n;
+        const int32_t od = __ldg(R.outdeg + v);
+        wo[v] = Rows<T>::init(x0, od);
+        R.rinv[v] = od ? 1.0 / od : 1.0;
+        if (od == 0) f.d += to_fix(x0);
+    }
+    add_sums<8>(R, f);
+}
+
+// one iteration over the range's tiles (each warp takes every nw-th tile,
+// the next one loaded while the current one is summed), then its rows
+// without in-edges; sums[3] counts bounded waits that expired
+template <typename T, int W>
+__global__ void __launch_bounds__(32 * W, 1) k_rows_step(const RowsDev R) {
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    Stream st = make_stream<W>(s_dyn);
+    using WS = typename Rows<T>::W;
+    using Rr = typename Rows<T>::Real;
+    const WS *wc = static_cast<const WS *>(R.w_in);
+    WS *wn = static_cast<WS *>(R.w_out);
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = int64_t(blockIdx.x) * W + (threadIdx.x >> 5);
+    const int64_t nw = int64_t(gridDim.x) * W;
+    const int ni = static_cast<int>(R.n);
+    const int64_t ntiles = (R.apre[R.n] - R.apre[0] + 31) >> 5;
+    const Rr a = static_cast<Rr>(R.alpha);
+    const Rr c = static_cast<Rr>(teleport(R.alpha, R.dangling, R.n_all));
+    Fix3 f;
+    bool failed = false;
+    if (gw < ntiles) {
+        int t = static_cast<int>(gw);
+        TileInfo<T> cur = load_head<T>(t, ni, R.tinfo, R.perm, lane);
+        load_row<T>(cur, R.outdeg, wc, R.rinv);
+        while (true) {
+            const int64_t tn = t + nw;
+            const bool has_next = tn < ntiles;
+            TileInfo<T> nxt = load_head<T>(has_next ? static_cast<int>(tn) : t, ni, R.tinfo,
+                                           R.perm, lane);
+            if (has_next) load_row<T>(nxt, R.outdeg, wc, R.rinv);
+            const int v = cur.v;
+            Rr sum = Rr(0);
+            if (!tile_sum<T>(R.desc, cur, nxt, has_next, st, wc + (v < 0 ? 0 : v), 1u << lane,
+                             lane, sum)) {
+                failed = true;
+                break;
+            }
+            if (v >= 0) Rows<T>::update(sum, a, c, cur.od, cur.wv, cur.ex, wn + v, f);
+            if (!has_next) break;
+            cur = nxt;
+            t = static_cast<int>(tn);
+        }
+    }
+    if (failed || st.issued) st.drain();
+    // rows without in-edges: x' = c
+    const int64_t slot_empty = ntiles << 5;
+    for (int64_t i = slot_empty + int64_t(blockIdx.x) * 32 * W + threadIdx.x; i < R.n;
+         i += int64_t(gridDim.x) * 32 * W) {
+        const int v = __ldg(R.perm + i);
+        typename Rows<T>::Extra ex;
+        Rows<T>::load_extra(ex, R.rinv, v);
+        Rows<T>::update(Rr(0), a, c, __ldg(R.outdeg + v), wc[v], ex, wn + v, f);
+    }
+    add_sums<W>(R, f);
+    if (failed && lane == 0) atomicAdd(R.sums + 3, 1ULL);
+}
+
+// sum of x over the range (sums[2]), or, with ranks set, x * scale into ranks
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_finish(const RowsDev R) {
+    using WS = typename Rows<T>::W;
+    using Rr = typename Rows<T>::Real;
+    const WS *wc = static_cast<const WS *>(R.w_in);
+    Rr *x = static_cast<Rr *>(R.ranks);
+    Fix3 f;
+    for (int64_t v = int64_t(blockIdx.x) * 256 + threadIdx.x; v < R.n;
+         v += int64_t(gridDim.x) * 256) {
+        const int32_t od = __ldg(R.outdeg + v);
+        if (x) x[v] = static_cast<Rr>(Rows<T>::x_of(wc[v], od) * R.scale);
+        else f.s += Rows<T>::fix_x(wc[v], od);
+    }
+    if (!x) add_sums<8>(R, f);
+}
+
+ffg_status rows_check(const ffg_graph *g, int64_t row0, int64_t row1, ffg_prec prec) {
+    if (!g || g->n_nodes <= 0 || !g->in_ptr || !g->outdeg || (g->n_edges > 0 && !g->in_idx))
+        return set_error("graph is empty or incomplete"), FFG_ERR_INVALID_ARG;
+    if (g->n_nodes >= (int64_t(1) << 31)) return set_error("too many nodes"), FFG_ERR_OVERFLOW;
+    if (!(0 <= row0 && row0 < row1 && row1 <= g->n_nodes))
+        return set_error("rows [%lld, %lld) outside [0, %lld)", (long long)row0,
+                         (long long)row1, (long long)g->n_nodes),
+               FFG_ERR_INVALID_ARG;
+    if (prec != FFG_F64 && prec != FFG_F32)
+        return set_error("unknown precision %d", (int)prec), FFG_ERR_INVALID_ARG;
+    return FFG_OK;
+}
+
+// in-edges of the range: in_ptr[row0] and in_ptr[row1] (a synchronous read)
+ffg_status rows_edges(const ffg_graph *g, int64_t row0, int64_t row1, int64_t *ebase,
+                      int64_t *eend) {
+    FFG_TRY(check_cuda(cudaMemcpy(ebase, g->in_ptr + row0, sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost), "read in_ptr"));
+    FFG_TRY(check_cuda(cudaMemcpy(eend, g->in_ptr + row1, sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost), "read in_ptr"));
+    if (!(0 <= *ebase && *ebase <= *eend && *eend <= g->n_edges))
+        return set_error("in_ptr is not a row-pointer array"), FFG_ERR_INVALID_ARG;
+    if (!desc_fits(row1 - row0, *eend - *ebase))
+        return set_error("too many edges in the range"), FFG_ERR_OVERFLOW;
+    return FFG_OK;
+}
+
+}  // namespace
+}  // namespace ffg
+
+extern "C" size_t pagerank_rows_w_bytes(ffg_prec prec) {
+    return prec == FFG_F32 ? sizeof(float) : prec == FFG_F64 ? sizeof(Fx) : 0;
+}
+
+extern "C" size_t pagerank_rows_workspace_bytes(const ffg_graph *g, int64_t row0, int64_t row1,
+                                                ffg_prec prec) {
+    clear_error();
+    int64_t eb = 0, ee = 0;
+    if (rows_check(g, row0, row1, prec) != FFG_OK || rows_edges(g, row0, row1, &eb, &ee) != FFG_OK)
+        return 0;
+    return carve_rows(nullptr, row1 - row0, ee - eb).bytes;
+}
+
+extern "C" ffg_status pagerank_rows_prepare(const ffg_graph *g, int64_t row0, int64_t row1,
+                                            ffg_prec prec, void *workspace, size_t ws_bytes,
+                                            void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    FFG_TRY(rows_check(g, row0, row1, prec));
+    if (!workspace || !aligned256(workspace))
+        return set_error("workspace NULL or not 256-byte aligned"), FFG_ERR_INVALID_ARG;
+    int64_t eb = 0, ee = 0;
+    FFG_TRY(rows_edges(g, row0, row1, &eb, &ee));
+    const int64_t n = row1 - row0, tiles = (n + 31) / 32;
+    RowsWs w = carve_rows(workspace, n, ee - eb);
+    if (ws_bytes < w.bytes)
+        return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
+    int sms = 0;
+    FFG_TRY(device_sms(&sms));
+    const int64_t *in_ptr = g->in_ptr + row0;
+    k_active_flags<<<grid_for(n, 256, sms), 256, 0, stream>>>(in_ptr, n, w.aflag);
+    count_launch();
+    FFG_TRY(check_launch("k_active_flags"));
+    FFG_TRY(scan_exclusive(w.aflag, w.apre, n, w.ascan, stream));
+    k_perm<<<grid_for(n, 256, sms), 256, 0, stream>>>(w.apre, n, w.perm);
+    count_launch();
+    FFG_TRY(check_launch("k_perm"));
+    k_pr_layout<<<grid_for(tiles, kLayoutThreads / 32, sms), kLayoutThreads, 0, stream>>>(
+        in_ptr, g->in_idx, w.perm, n, ee, eb, row0, w.desc, w.cnt, w.tinfo);
+    count_launch();
+    FFG_TRY(check_launch("k_pr_layout"));
+    return scan_exclusive(w.cnt, w.tpre, tiles, w.scan, stream);
+}
+
+namespace ffg {
+namespace {
+
+template <typename T, int W>
+ffg_status launch_rows_step(const RowsDev &R, cudaStream_t stream) {
+    int per_sm = 0, sms = 0;
+    FFG_TRY((kernel_config<W>((const void *)k_rows_step<T, W>, &per_sm, &sms)));
+    const int64_t tiles = (R.n + 31) / 32;
+    const int64_t want = (tiles + W - 1) / W;  // a tile per warp at least
+    const int64_t most = int64_t(sms) * per_sm;
+    const unsigned grid = static_cast<unsigned>(want < 1 ? 1 : (want < most ? want : most));
+    k_rows_step<T, W><<<grid, 32 * W, pr_smem_bytes<W>(), stream>>>(R);
+    count_launch();
+    return check_launch("k_rows_step");
+}
+
+template <typename T>
+ffg_status launch_rows(int op, const RowsDev &R, cudaStream_t stream) {
+    int sms = 0;
+    FFG_TRY(device_sms(&sms));
+    const unsigned grid = grid_for(R.n, 256, sms);
+    switch (op) {
+    case FFG_ROWS_INIT:
+        k_rows_init<T><<<grid, 256, 0, stream>>>(R);
+        count_launch();
+        return check_launch("k_rows_init");
+    case FFG_ROWS_STEP:
+        return launch_rows_step<T, sizeof(typename Rows<T>::Real) == 8 ? kWarpsSingle64
+                                                                       : kWarpsSingle>(R, stream);
+    default:
+        k_rows_finish<T><<<grid, 256, 0, stream>>>(R);
+        count_launch();
+        return check_launch("k_rows_finish");
+    }
+}
+
+}  // namespace
+}  // namespace ffg
+
+extern "C" ffg_status pagerank_rows_run(const ffg_graph *g, int64_t row0, int64_t row1,
+                                        ffg_prec prec, const ffg_rows_op *op, void *workspace,
+                                        size_t ws_bytes, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    FFG_TRY(rows_check(g, row0, row1, prec));
+    if (!op || op->op < FFG_ROWS_INIT || op->op > FFG_ROWS_WRITE || !op->sums)
+        return set_error("op: unknown operation or sums NULL"), FFG_ERR_INVALID_ARG;
+    if (!workspace || !aligned256(workspace))
+        return set_error("workspace NULL or not 256-byte aligned"), FFG_ERR_INVALID_ARG;
+    const int k = op->op;
+    if ((k != FFG_ROWS_INIT && !op->w_in) || ((k == FFG_ROWS_INIT || k == FFG_ROWS_STEP) && !op->w_out) ||
+        (k == FFG_ROWS_WRITE && !op->ranks))
+        return set_error("op %d: w_in, w_out or ranks missing", k), FFG_ERR_INVALID_ARG;
+    if (k == FFG_ROWS_STEP && !(op->damping > 0.0 && op->damping < 1.0))
+        return set_error("damping must lie in (0, 1)"), FFG_ERR_INVALID_ARG;
+    // the tables' places depend on the rows only (the descriptors come
+    // last), so an iteration needs no device read; the full size was checked
+    // by pagerank_rows_prepare
+    const int64_t n = row1 - row0;
+    if (ws_bytes < carve_rows(nullptr, n, 0).bytes)
+        return set_error("workspace smaller than any range of %lld rows", (long long)n),
+               FFG_ERR_NO_MEMORY;
+    const RowsWs w = carve_rows(workspace, n, 0);
+    const size_t wb = pagerank_rows_w_bytes(prec);
+    RowsDev R;
+    R.outdeg = g->outdeg + row0;
+    R.rinv = w.rinv;
+    R.n = n;
+    R.n_all = g->n_nodes;
+    R.alpha = op->damping;
+    R.scale = op->scale;
+    R.dangling = op->dangling;
+    R.sums = reinterpret_cast<unsigned long long *>(op->sums);
+    R.w_in = op->w_in ? static_cast<const char *>(op->w_in) + size_t(row0) * wb : nullptr;
+    R.w_out = op->w_out ? static_cast<char *>(op->w_out) + size_t(row0) * wb : nullptr;
+    const size_t rb = prec == FFG_F32 ? sizeof(float) : sizeof(double);
+    R.ranks = op->ranks ? static_cast<char *>(op->ranks) + size_t(row0) * rb : nullptr;
+    if (k == FFG_ROWS_SUM) R.ranks = nullptr;
+    R.desc = w.desc;
+    R.tinfo = w.tinfo;
+    R.perm = w.perm;
+    R.apre = w.apre;
+    if (prec == FFG_F32) return launch_rows<float>(k, R, stream);
+    return launch_rows<F64x>(k, R, stream);
 }
 
 // ---------------------------------------------------------------------------

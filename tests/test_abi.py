@@ -137,6 +137,34 @@ def test_batch_tuning_validated_on_host(lib):
     assert lib.pagerank_batch_times(None, None, None) == ffg.FFG_ERR_INVALID_ARG
 
 
+def test_rows_validated_on_host(lib):
+    """The row-range entry points refuse bad ranges, operations and dampings
+    before any device access."""
+    g = ffg.ffg_graph()
+    g.n_nodes, g.n_edges = 100, 400
+    g.in_ptr, g.in_idx, g.outdeg = 256, 256, 256
+    assert ffg.pagerank_rows_w_bytes(ffg.F32) == 4 and ffg.pagerank_rows_w_bytes(ffg.F64) == 16
+    assert ffg.pagerank_rows_w_bytes(7) == 0
+    for r0, r1 in ((0, 0), (5, 4), (-1, 10), (90, 101)):
+        assert ffg.pagerank_rows_workspace_bytes(g, r0, r1, ffg.F32) == 0
+        assert ffg.pagerank_rows_prepare(g, r0, r1, ffg.F32, 256, 1 << 20) == \
+            ffg.FFG_ERR_INVALID_ARG
+        assert "rows" in ffg.ffg_last_error()
+    before = lib.ffg_launch_count()
+    sums = np.zeros(4, dtype=np.uint64)
+    op = ffg.ffg_rows_op(ffg.ROWS_STEP, 0, 1.0, 0, 1.0, 256, 256, None, sums.ctypes.data)
+    assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 256, 1 << 20) == ffg.FFG_ERR_INVALID_ARG
+    assert "damping" in ffg.ffg_last_error()
+    op.op = 9
+    assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 256, 1 << 20) == ffg.FFG_ERR_INVALID_ARG
+    op.op = ffg.ROWS_WRITE
+    assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 256, 1 << 20) == ffg.FFG_ERR_INVALID_ARG
+    op.op, op.damping = ffg.ROWS_STEP, 0.85
+    assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 258, 1 << 20) == ffg.FFG_ERR_INVALID_ARG
+    assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 256, 64) == ffg.FFG_ERR_NO_MEMORY
+    assert lib.ffg_launch_count() == before
+
+
 def test_batch_run_validated_on_host(lib):
     """ffg_batch_run refuses a missing plan or incomplete C_p arguments
     before it launches anything."""

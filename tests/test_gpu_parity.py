@@ -745,3 +745,46 @@ def test_graph_checkpoint_resumes_on_gpu(tmp_path):
     z, it3, res3, conv3 = ffg.pagerank(h, 0.85, 1e-12, prec=ffg.F64, init=x0)
     assert conv3 and it3 <= 2
     assert np.abs(_np(z) - oracle.pagerank_exact(og, 0.85)).sum() <= F64_L1
+
+
+def test_row_partitioned_fp64_equals_single_solve():
+    """The row-partitioned form (several ranges, one process standing for
+    several ranks) gives pagerank_solve's FP64 ranks bit for bit: the same
+    exact fixed-point sums, the same stopping decisions."""
+    from paper_2210_01465_gb300.multi import solve_rows, split_rows
+    cases = [(fi.single_small(), 2, "hamming", 3), (fi.pnpoly_space(), 3, "adjacent", 5),
+             (fi.single_large(), 1, "hamming", 4)]
+    for spec, seed, nbh, parts in cases:
+        f = fi.runtimes(spec, seed, fail_frac=0.3 if parts == 5 else 0.03)
+        g, _ = run_build(spec, f, nbh)
+        x, it, res, conv = ffg.pagerank(g, 0.85, 1e-12, prec=ffg.F64)
+        bounds = split_rows(_np(g.in_ptr), parts)
+        for ranges in (bounds, [(0, g.n_nodes)]):
+            y, it2, res2, conv2 = solve_rows(g, ranges, 0.85, 1e-12, prec=ffg.F64)
+            assert conv2 and it2 == it and res2 == res
+            np.testing.assert_array_equal(_np(y), _np(x))
+
+
+def test_row_partitioned_fp32_and_warm_start():
+    """FP32 over ranges (tile groupings differ from the single solve, so the
+    FP32 sums are not bit-identical): C_p within the FP32 bar of the oracle's
+    exact solve; a warm start from the exact ranks converges at once; tiny
+    ranges (one row, rows without in-edges) work."""
+    from paper_2210_01465_gb300.multi import solve_rows, split_rows
+    spec = fi.conv_mi50_space()
+    f = fi.runtimes(spec, 11)
+    og = oracle.build(spec, f, oracle.HAMMING)
+    g, fd = run_build(spec, f, "hamming")
+    xe = oracle.pagerank_exact(og, 0.85)
+    p = [0.0, 0.05, 0.1]
+    cpe = oracle.centrality(og, xe, p)
+    n = g.n_nodes
+    for ranges in (split_rows(_np(g.in_ptr), 4), [(0, 1), (1, 2), (2, n)]):
+        y, it, res, conv = solve_rows(g, ranges, 0.85, 1e-12, prec=ffg.F32)
+        assert conv
+        assert np.abs(_np(y).astype(np.float64) - xe).sum() < 1e-5
+        cp = ffg.centrality(g, fd, y, p)
+        assert np.abs(cp - cpe).max() <= F32_CP
+    y, it, res, conv = solve_rows(g, split_rows(_np(g.in_ptr), 3), 0.85, 1e-12, prec=ffg.F64,
+                                  init=torch.from_numpy(xe).cuda())
+    assert conv and it <= 2 and np.abs(_np(y) - xe).sum() <= F64_L1
