@@ -129,12 +129,12 @@ def _rows_worker(rank, world, port, q):
     q.put((rank, x))
 
 
-@pytest.mark.timeout(180)
-def test_two_ranks_gloo_row_exchange_power_iteration():
+@pytest.mark.timeout(240)
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_row_exchange_power_iteration(world):
     import numpy as np
     import ffg_inputs as fi
     import oracle
-    world = 2
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -150,4 +150,4 @@ def test_two_ranks_gloo_row_exchange_power_iteration():
     xo, _, _, _ = oracle.pagerank_power(og, 0.85, 0.0, max_iter=60)
     for rank in range(world):   # every rank holds every row, equal to the oracle's iterate
         assert np.abs(res[rank] - xo).sum() < 1e-12
-    np.testing.assert_array_equal(res[0], res[1])
+        np.testing.assert_array_equal(res[rank], res[0])
