@@ -446,10 +446,11 @@ ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream);
 ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *iters_out,
                                 double *residual_out, int32_t *status_out, void *stream);
 
-/* Per-job busy time of the last run: block_seconds_out (HOST, n_jobs)
- * receives, for every job, the sum over its blocks of the time each spent
- * on it, from the moment all of them had started it to the block's end of
- * it (device global timer).  The total over the jobs, divided by the
+/* Per-job busy time of the last run (a scheduling aid for the batched form
+ * of Sec. VII-B's survey; the paper has no counterpart): block_seconds_out
+ * (HOST, n_jobs) receives, for every job, the sum over its blocks of the
+ * time each spent on it, from the moment all of them had started it to the
+ * block's end of it (device global timer).  The total over the jobs, divided by the
  * plan's n_blocks, is the time an ideally balanced schedule would take.
  * Synchronises `stream`. */
 ffg_status pagerank_batch_times(const ffg_pr_batch *plan, double *block_seconds_out,
