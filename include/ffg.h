@@ -206,12 +206,15 @@ ffg_status ffg_build_batch_query(const ffg_build_batch *plan, int32_t *status_ou
  * iters_out / residual_out (HOST) receive the iteration count and the last
  * residual; when both are NULL nothing is synchronised and the result is
  * read later with pagerank_query.  FFG_ERR_NOT_CONVERGED after max_iter.
+ * max_iter lies in [1, FFG_MAX_ITER] (else FFG_ERR_INVALID_ARG): the
+ * blocks of a solve count their barrier arrivals in 32 bits.
  * `init` is a set of flags: FFG_INIT_RANKS (warm start from `ranks`) and
  * FFG_INIT_LAYOUT (the workspace already holds this graph's edge layout from
  * pagerank_prepare, or from an earlier solve of the same graph with the same
  * workspace and precision; without it the solve builds the layout first). */
 #define FFG_INIT_RANKS 1
 #define FFG_INIT_LAYOUT 2
+#define FFG_MAX_ITER 1000000
 
 size_t pagerank_workspace_bytes(int64_t n_nodes, int64_t n_edges, ffg_prec prec);
 
@@ -238,13 +241,15 @@ ffg_status pagerank_solve(const ffg_graph *g, double damping, double tol, int32_
  * holds from the moment the library is loaded until the process exits.
  * Graphs whose pagerank_workspace_bytes exceeds 8 MiB are rejected with
  * FFG_ERR_NO_MEMORY (about 48,000 nodes at 20 in-edges per node in FP32).
- * The first call on a device looks up the array's device address; make
- * that first call before any stream capture.  Every call shares the one
+ * Every call looks up the array's device address on the current device;
+ * the first lookup on a device loads the library's device code there, so
+ * make the first call on a device before any stream capture.  Every call shares the one
  * array (the parts that must start at zero are cleared by each call), so
  * calls that overlap on the GPU -- from other streams or host threads --
  * race and must be serialised by the caller.  Always synchronises `stream`
  * once and returns the solve's status; iters_out / residual_out may be
- * NULL.  FFG_INIT_LAYOUT is ignored (the layout is always rebuilt). */
+ * NULL.  FFG_INIT_LAYOUT is ignored (the layout is always rebuilt); other
+ * unknown init bits give FFG_ERR_INVALID_ARG. */
 ffg_status pagerank_solve_static(const ffg_graph *g, double damping, double tol,
                                  int32_t max_iter, ffg_prec prec, void *ranks, int init,
                                  int32_t *iters_out, double *residual_out, void *stream);

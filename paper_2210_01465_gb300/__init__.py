@@ -33,6 +33,7 @@ HAMMING, ADJACENT = 0, 1
 F64, F32 = 0, 1
 PROD_LE, PROD_GE, DIVIDES, PROD_LE_PROD = 0, 1, 2, 3
 INIT_RANKS, INIT_LAYOUT = 1, 2
+MAX_ITER = 1000000  # FFG_MAX_ITER
 MAX_PARAMS, MAX_VALUES, MAX_CONSTRAINTS, MAX_P = 16, 1024, 16, 32
 _KIND = {"prod_le": PROD_LE, "prod_ge": PROD_GE, "divides": DIVIDES,
          "prod_le_prod": PROD_LE_PROD}

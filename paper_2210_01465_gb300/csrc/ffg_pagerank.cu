@@ -69,6 +69,10 @@ constexpr int kWarpsSingle64 = FFG_PR_WARPS64;  // single FP64 solves
 constexpr int kWarpsBatch = 8;
 constexpr int kWarpsBatchWide = 16;
 constexpr int kMaxBlocks = 4096;
+// a block's barrier targets (phase * blocks, phase <= max_iter + 3) fit the
+// 32-bit arrival counter
+static_assert((uint64_t(FFG_MAX_ITER) + 3) * kMaxBlocks < (uint64_t(1) << 32),
+              "barrier targets fit 32 bits");
 constexpr uint64_t kTimeoutNs = 2000000000ULL;
 #ifndef FFG_PR_SEG
 #define FFG_PR_SEG 128
@@ -1397,8 +1401,9 @@ extern "C" ffg_status pagerank_solve(const ffg_graph *g, double damping, double 
         return set_error("too many nodes or edges"), FFG_ERR_OVERFLOW;
     if (!(damping > 0.0 && damping < 1.0))
         return set_error("damping must lie in (0,1)"), FFG_ERR_INVALID_ARG;
-    if (!(tol >= 0.0) || max_iter < 1)
-        return set_error("tol must be >= 0 and max_iter >= 1"), FFG_ERR_INVALID_ARG;
+    if (!(tol >= 0.0) || max_iter < 1 || max_iter > FFG_MAX_ITER)
+        return set_error("tol must be >= 0 and max_iter in [1, %d]", FFG_MAX_ITER),
+               FFG_ERR_INVALID_ARG;
     if (prec != FFG_F64 && prec != FFG_F32)
         return set_error("unknown precision %d", (int)prec), FFG_ERR_INVALID_ARG;
     if (!ranks || !workspace) return set_error("ranks/workspace NULL"), FFG_ERR_INVALID_ARG;
@@ -1818,7 +1823,7 @@ ffg_status check_job(const ffg_pr_job &j, int idx) {
     if (g->n_nodes >= (int64_t(1) << 31) || !desc_fits(g->n_nodes, g->n_edges))
         return set_error("job %d: too many nodes or edges", idx), FFG_ERR_OVERFLOW;
     if (!(j.damping > 0.0 && j.damping < 1.0) || !(j.tol >= 0.0) || j.max_iter < 1 ||
-        (j.init & ~FFG_INIT_RANKS))
+        j.max_iter > FFG_MAX_ITER || (j.init & ~FFG_INIT_RANKS))
         return set_error("job %d: bad damping, tol, max_iter or init", idx), FFG_ERR_INVALID_ARG;
     return FFG_OK;
 }

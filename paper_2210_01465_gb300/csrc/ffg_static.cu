@@ -20,21 +20,16 @@ namespace {
 constexpr size_t kStaticScratchBytes = size_t(8) << 20;  // 8 MiB per device
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::atomic<void *> g_static_ptr[kMaxDevices];
-
-// Device address of g_static_scratch on the current device (looked up once
-// per device; the host-side symbol itself is not a device address).
+// Device address of g_static_scratch on the current device.  The host-side
+// symbol is not a device address.  The lookup is repeated on every call: it
+// is cheap next to the synchronising solve, and the address can change when
+// the device's primary context is reset and the module loaded again.  The
+// first lookup on a device loads the library's module there, which must not
+// happen inside a stream capture.
 ffg_status static_scratch(void **out) {
-    int dev = 0;
-    FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
-    if (dev < 0 || dev >= kMaxDevices) return set_error("device index %d too large", dev), FFG_ERR_CUDA;
-    void *p = g_static_ptr[dev].load();
-    if (!p) {
-        FFG_TRY(check_cuda(cudaGetSymbolAddress(&p, g_static_scratch),
-                           "cudaGetSymbolAddress(static scratch)"));
-        g_static_ptr[dev].store(p);
-    }
+    void *p = nullptr;
+    FFG_TRY(check_cuda(cudaGetSymbolAddress(&p, g_static_scratch),
+                       "cudaGetSymbolAddress(static scratch)"));
     *out = p;
     return FFG_OK;
 }
@@ -48,6 +43,8 @@ extern "C" ffg_status pagerank_solve_static(const ffg_graph *g, double damping, 
     clear_error();
     if (!g || g->n_nodes <= 0 || g->n_edges < 0)
         return set_error("graph is empty or incomplete"), FFG_ERR_INVALID_ARG;
+    if (init & ~(FFG_INIT_RANKS | FFG_INIT_LAYOUT))
+        return set_error("unknown init flags 0x%x", init), FFG_ERR_INVALID_ARG;
     const size_t need = pagerank_workspace_bytes(g->n_nodes, g->n_edges, prec);
     if (need > kStaticScratchBytes) {
         set_error("pagerank_solve_static: this graph needs %zu bytes of scratch, the static "

@@ -81,6 +81,11 @@ def test_argument_errors_before_cuda(lib):
     for damping in (0.0, 1.0, -0.5, float("nan")):
         assert ffg.pagerank_solve(g, damping, 1e-9, 10, 0, 256, 0, 256, 1 << 20)[0] == 1
     assert ffg.pagerank_solve(g, 0.85, 1e-9, 0, 0, 256, 0, 256, 1 << 20)[0] == 1
+    assert ffg.pagerank_solve(g, 0.85, 1e-9, ffg.MAX_ITER + 1, 0, 256, 0, 256, 1 << 20)[0] == 1
+    assert "max_iter" in ffg.ffg_last_error()
+    # the entry point without a workspace refuses unknown init flags up front
+    assert ffg.pagerank_solve_static(g, 0.85, 1e-9, 10, 0, 256, 4, 0)[0] == 1
+    assert "init" in ffg.ffg_last_error()
     assert ffg.pagerank_solve(g, 0.85, 1e-9, 10, 5, 256, 0, 256, 1 << 20)[0] == 1
     assert ffg.pagerank_solve(g, 0.85, 1e-9, 10, 0, 256, 0, 256, 8)[0] == ffg.FFG_ERR_NO_MEMORY
     assert ffg.pagerank_solve(g, 0.85, 1e-9, 10, 0, 256, 4, 256, 1 << 30)[0] == 1

@@ -51,6 +51,15 @@ def test_static_scratch_matches_workspace_entry_point(prec):
             assert it == it_ref
             l1 = float((x.double() - ref.double()).abs().sum())
             assert l1 <= bar, (spec.name, l1)
+        # warm start from the converged ranks, against the same warm start
+        # through the workspace entry point
+        warm, it_w, _, _ = ffg.pagerank(g, 0.85, 1e-12, prec=prec, init=ref)
+        x = ref.clone()
+        st, it, res = ffg.pagerank_solve_static(g.c, 0.85, 1e-12, 10000, prec, x.data_ptr(),
+                                                ffg.INIT_RANKS, stream)
+        assert st == ffg.FFG_OK, ffg.ffg_last_error()
+        assert it == it_w and it <= 3, (it, it_w)
+        assert float((x.double() - warm.double()).abs().sum()) <= bar
 
 
 def test_static_scratch_rejects_large_graphs():
