@@ -36,7 +36,9 @@ An empty index tuple has product 1.
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -329,7 +331,11 @@ def random_space(seed: int, n_params: int, max_radix: int = 12, n_clauses: int =
 
 def sized_random_space(seed: int, target_raw: int, max_radix: int = 12) -> SpaceSpec:
     """Random space whose raw size lies close to ``target_raw``: radices are
-    drawn one parameter at a time until the product reaches the target."""
+    drawn one parameter at a time until the product reaches the target.
+    Clauses: a product upper bound on one pair of parameters (always), a
+    product lower bound on another pair (for about half of the seeds) and a
+    divisibility clause (for about 60 % of the seeds with a list starting
+    at 1)."""
     vals = []
     stream = 0
     total = 1
@@ -351,10 +357,6 @@ def sized_random_space(seed: int, target_raw: int, max_radix: int = 12) -> Space
         total *= k
         stream += 1
     n = len(vals)
-    # Clauses that the configuration of all list minima satisfies (so the
-    # space is never empty): a product upper bound no smaller than the
-    # product of the minima, and divisibility by a parameter whose list
-    # starts at 1.
     cu = uniform01(seed, 90, np.arange(16))
     clauses = []
     if n >= 2:
@@ -372,6 +374,15 @@ def sized_random_space(seed: int, target_raw: int, max_radix: int = 12) -> Space
             a = (d + 1 + int(cu[5] * (n - 1))) % n
             if a != d:
                 clauses.append(Clause("divides", (a,), (d,)))
+        if n >= 3 and cu[6] < 0.5:
+            i2 = int(cu[7] * n)
+            j2 = (i2 + 1 + int(cu[8] * (n - 1))) % n
+            lo2 = max(min(vals[i2]), 1) * max(min(vals[j2]), 1)
+            hi2 = max(max(vals[i2]), 1) * max(max(vals[j2]), 1)
+            if hi2 > lo2:
+                bound = int(round(lo2 * (hi2 / lo2) ** (0.05 + 0.25 * cu[9])))
+                if bound > lo2:
+                    clauses.append(Clause("prod_ge", tuple(sorted((i2, j2))), (), bound))
     return SpaceSpec(f"sized_{seed}_{target_raw}", tuple(f"p{i}" for i in range(n)),
                      tuple(vals), tuple(clauses))
 
@@ -399,45 +410,81 @@ def _loguniform(seed: int, stream: int, count: int, lo: float, hi: float) -> np.
     return np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))
 
 
-def batch_templates(count: int = 26, seed: int = 7, lo: float = 1.5e3, hi: float = 6e6):
-    """The paper's convolution, GEMM and PnPoly spaces plus seeded random
-    templates whose raw size is drawn log-uniformly in [lo, hi] (the valid
-    count is whatever the template's clauses leave)."""
-    out = [conv_space(), gemm_space(), pnpoly_space()]
-    targets = _loguniform(seed, 1, count, lo, hi)
-    k = 0
-    while len(out) < count:
-        sp = sized_random_space(seed * 1000 + k, int(targets[len(out)]))
-        k += 1
-        if 3 <= sp.n_params <= 10:
-            out.append(SpaceSpec(f"template_{len(out)}", sp.names, sp.values, sp.clauses))
+# Valid-size targets: templates are rejection-sampled until their number of
+# VALID configurations lies within +-20 % of a log-uniform target.  Counting
+# valid configurations is the method's own arithmetic (the constraint mask),
+# which this module does not hold, so the accepted candidates are read from a
+# table (candidate index and raw-size target per template) that
+# tests/golden/make_templates.py writes with the CPU oracle; that script
+# also records each template's valid count, which a test re-checks.
+TEMPLATE_TABLE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                              "tests", "golden", "templates.json")
+VALID_TOL = 0.20
+
+# (seed, count of random templates, log-uniform valid-size range) per family
+TEMPLATE_FAMILIES = {
+    "batch": (7, 23, 1e3, 5e6),    # + the paper's three spaces = 26 templates
+    "sweep": (11, 64, 1e4, 2e6),
+}
+
+
+def valid_targets(family: str) -> np.ndarray:
+    """The valid-size target of every random template of ``family``:
+    log-uniform over the family's range, drawn stratified (one target per
+    equal slice of the log range, slices assigned to templates in a seeded
+    random order), so that the batch's total size stays near its expected
+    value instead of following the heavy tail of independent draws."""
+    seed, count, lo, hi = TEMPLATE_FAMILIES[family]
+    order = np.argsort(uniform01(seed, 1, np.arange(count)), kind="stable")
+    u = (order + uniform01(seed, 2, np.arange(count))) / count
+    return np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))
+
+
+def template_candidate(family: str, t: int, k: int, target_raw: int) -> SpaceSpec:
+    """Candidate k of template t of ``family``, with about target_raw raw points."""
+    seed = TEMPLATE_FAMILIES[family][0]
+    return sized_random_space(seed * 100000 + t * 1000 + k, int(target_raw))
+
+
+def _template_table():
+    with open(TEMPLATE_TABLE) as fh:
+        return json.load(fh)
+
+
+def family_templates(family: str, prefix: str):
+    """The accepted random templates of ``family`` (see TEMPLATE_TABLE)."""
+    rows = _template_table()[family]
+    out = []
+    for t, row in enumerate(rows):
+        sp = template_candidate(family, t, row["k"], row["raw_target"])
+        out.append(SpaceSpec(f"{prefix}_{t}", sp.names, sp.values, sp.clauses))
     return out
+
+
+def batch_templates():
+    """The paper's convolution, GEMM and PnPoly spaces plus 23 seeded random
+    templates whose valid sizes are log-uniform in [1e3, 5e6] (+-20 %)."""
+    return [conv_space(), gemm_space(), pnpoly_space()] + family_templates("batch", "template")
 
 
 FAIL_LEVELS = (0.03, 0.30, 0.70)
 
 
-def batch_workload(n_templates: int = 26, n_seeds: int = 9):
-    """(space, seed, fail_frac) for every template x fitness seed; the failure
-    fraction cycles over 3 %, 30 % and 70 % by template."""
+def batch_workload(n_seeds: int = 9):
+    """(space, seed, fail_frac) for every template x fitness seed (26 x 9 =
+    234 spaces); the failure fraction cycles over 3 %, 30 % and 70 % by
+    template."""
     jobs = []
-    for t, sp in enumerate(batch_templates(n_templates)):
+    for t, sp in enumerate(batch_templates()):
         for s in range(n_seeds):
             jobs.append((sp, 100 * t + s + 1, FAIL_LEVELS[t % 3]))
     return jobs
 
 
-def sweep_spaces(count: int = 64, seed: int = 11, lo: float = 1.5e4, hi: float = 3e6):
-    """Random spaces with raw sizes log-uniform in [lo, hi]."""
-    targets = _loguniform(seed, 2, count, lo, hi)
-    out = []
-    k = 0
-    while len(out) < count:
-        sp = sized_random_space(seed * 1000 + k, int(targets[len(out)]))
-        k += 1
-        if 3 <= sp.n_params <= 10:
-            out.append(SpaceSpec(f"sweep_{len(out)}", sp.names, sp.values, sp.clauses))
-    return out
+def sweep_spaces():
+    """64 seeded random spaces whose valid sizes are log-uniform in [1e4, 2e6]
+    (+-20 %)."""
+    return family_templates("sweep", "sweep")
 
 
 def _mix64_t(z):
