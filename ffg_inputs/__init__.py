@@ -470,14 +470,15 @@ def batch_templates():
 FAIL_LEVELS = (0.03, 0.30, 0.70)
 
 
-def batch_workload(n_seeds: int = 9):
+def batch_workload(n_seeds: int = 9, seed_base: int = 0):
     """(space, seed, fail_frac) for every template x fitness seed (26 x 9 =
     234 spaces); the failure fraction cycles over 3 %, 30 % and 70 % by
-    template."""
+    template.  ``seed_base`` shifts every fitness seed (another draw of the
+    same templates)."""
     jobs = []
     for t, sp in enumerate(batch_templates()):
         for s in range(n_seeds):
-            jobs.append((sp, 100 * t + s + 1, FAIL_LEVELS[t % 3]))
+            jobs.append((sp, seed_base + 100 * t + s + 1, FAIL_LEVELS[t % 3]))
     return jobs
 
 

@@ -328,31 +328,54 @@ ffg_status walk_simulate(const ffg_graph *g, uint64_t seed, int64_t n_walks, uin
  * from the global row); it also reads those two values.
  *
  * pagerank_rows_run enqueues one operation on the range (no host read, no
- * synchronisation).  `sums` (DEVICE, 4 uint64, added to, never cleared):
- * [0] residual sum |x' - x|, [1] dangling mass, [2] sum of x, each fixed
- * point with quantum 2^-60, and [3] the number of bounded waits that
- * expired (then report FFG_ERR_TIMEOUT; results are undefined).  w_in,
- * w_out: DEVICE, n_nodes w elements each (every row; w_out's rows of the
- * range are written).  ranks: DEVICE, n_nodes reals of the precision.
- *   FFG_ROWS_INIT:  w_out from x0 = ranks (or 1/n_nodes when NULL); sums[1].
- *   FFG_ROWS_STEP:  w_out = one iteration on w_in with `damping` and the
- *                   previous dangling mass `dangling` (sums[1] of every
- *                   rank, fixed point); sums[0], sums[1], sums[3].
- *   FFG_ROWS_SUM:   sums[2] from w_in.
- *   FFG_ROWS_WRITE: ranks = x * scale from w_in (scale = 1 / sum of x).
- * Stop as pagerank_solve does: residual < tol, or (FFG_F32) a residual that
- * stops decreasing, or max_iter. */
-typedef enum { FFG_ROWS_INIT = 0, FFG_ROWS_STEP = 1, FFG_ROWS_SUM = 2, FFG_ROWS_WRITE = 3 } ffg_rows_kind;
+ * synchronisation).  `sums` (DEVICE, 4 uint64, added to): [0] residual
+ * sum |x' - x|, [1] dangling mass, [2] sum of x, each fixed point with
+ * quantum 2^-60, and [3] the number of bounded waits that expired.  `ctl`
+ * (DEVICE, one ffg_rows_ctl, caller-owned) carries the solve's state
+ * between operations; the decisions are taken there, on the device, from
+ * the summed fixed-point values, with the arithmetic of pagerank_solve, so
+ * that the host only moves bytes and reads ctl->stop.  w_in, w_out:
+ * DEVICE, n_nodes w elements each (every row; w_out's rows of the range
+ * are written).  ranks: DEVICE, n_nodes reals of the precision.
+ *   FFG_ROWS_INIT:    w_out from x0 = ranks (or 1/n_nodes when NULL);
+ *                     sums[1]; resets ctl.
+ *   FFG_ROWS_STEP:    w_out = one iteration on w_in with `damping` and the
+ *                     dangling mass in ctl; sums[0], sums[1], sums[3].
+ *   FFG_ROWS_SUM:     sums[2] from w_in.
+ *   FFG_ROWS_WRITE:   ranks = x * ctl->scale from w_in.
+ * and three operations on ctl and the sums of every rank (after their
+ * all-reduce), which also clear the sums they consume:
+ *   FFG_ROWS_START:   ctl->dangling = sums[1] (after INIT).
+ *   FFG_ROWS_ADVANCE: after a STEP: ctl->iters + 1, ctl->residual =
+ *                     sums[0] / 2^60, ctl->dangling = sums[1]; ctl->stop
+ *                     and ctl->converged when the residual is below `tol`
+ *                     or (FFG_F32) stops decreasing, ctl->stop alone at
+ *                     `max_iter`; ctl->status FFG_ERR_TIMEOUT (and stop)
+ *                     if sums[3] is not 0.
+ *   FFG_ROWS_SCALE:   ctl->scale = 1 / (sums[2] / 2^60) (after SUM).
+ * The START, ADVANCE and SCALE launches are one thread each; with several
+ * ranges in one process run them once, not per range. */
+typedef enum {
+    FFG_ROWS_INIT = 0, FFG_ROWS_STEP = 1, FFG_ROWS_SUM = 2, FFG_ROWS_WRITE = 3,
+    FFG_ROWS_START = 4, FFG_ROWS_ADVANCE = 5, FFG_ROWS_SCALE = 6
+} ffg_rows_kind;
+
+typedef struct {               /* DEVICE; read by the host, written by the ops */
+    int32_t iters, stop, converged, status;
+    double residual, prev_residual, scale;
+    uint64_t dangling;
+} ffg_rows_ctl;
 
 typedef struct {
-    int32_t op, reserved;  /* ffg_rows_kind */
+    int32_t op;            /* ffg_rows_kind */
+    int32_t max_iter;      /* ADVANCE */
     double damping;        /* STEP */
-    uint64_t dangling;     /* STEP */
-    double scale;          /* WRITE */
+    double tol;            /* ADVANCE */
     const void *w_in;
     void *w_out;
     void *ranks;
     uint64_t *sums;
+    ffg_rows_ctl *ctl;
 } ffg_rows_op;
 
 size_t pagerank_rows_w_bytes(ffg_prec prec);
@@ -389,7 +412,7 @@ typedef struct {
     int64_t total_tiles;
     void *jobs, *graphs, *items, *first, *queue, *ctl;
     int64_t total_rows;
-    void *tables[8];  /* per-row and per-tile tables of all graphs (internal) */
+    void *tables[10]; /* per-row and per-tile tables of all graphs (internal) */
     int32_t param_jobs, reserved; /* jobs in `params` (n_jobs or 0) */
     uint64_t params[FFG_PR_PARAM_JOBS * 16]; /* the job table (internal) */
 } ffg_pr_batch;
@@ -437,12 +460,18 @@ ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t n_jobs, ffg
                                      const ffg_pr_tuning *tuning, void *workspace,
                                      size_t ws_bytes, ffg_pr_batch *plan, void *stream);
 
-/* Enqueues the whole batch: one layout launch over every distinct graph and
- * one persistent launch that runs every job to its own convergence.  Host
- * work is argument checking only, so the call can be captured in a CUDA
- * graph and replayed (the graphs' contents may change between replays, not
- * their sizes or addresses). */
+/* Enqueues the whole batch: the edge layout of every distinct graph (a few
+ * launches over all of them) and one persistent launch that runs every job
+ * to its own convergence.  Host work is argument checking only, so the
+ * call can be captured in a CUDA graph and replayed (the graphs' contents
+ * may change between replays, not their sizes or addresses).
+ * pagerank_batch_prepare enqueues the layout step alone and
+ * pagerank_batch_solve the solve alone; a solve needs the layout of the
+ * graphs' current contents, from a prepare or an earlier run of the same
+ * plan.  Run = prepare + solve. */
 ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream);
+ffg_status pagerank_batch_prepare(const ffg_pr_batch *plan, void *stream);
+ffg_status pagerank_batch_solve(const ffg_pr_batch *plan, void *stream);
 
 /* Per-job iterations, residuals and statuses (HOST arrays of n_jobs, each
  * may be NULL) of the last run; synchronises `stream`.  Returns FFG_OK if
@@ -481,19 +510,46 @@ ffg_status centrality_proportion(const ffg_graph *g, const double *fitness_raw,
                                  int32_t n_p, double *cp_out, void *workspace, size_t ws_bytes,
                                  void *stream);
 
-/* Batched C_p: the same quantity for n_jobs graphs at once (one launch for
- * the sums of every job, one read-back).  Job j: g (host struct with DEVICE
- * arrays, host fields from ffg_build_count), fitness_raw and ranks (DEVICE,
- * precision `prec`).  cp_out (HOST) is n_jobs x n_p, row-major.  A job
- * whose graph has no local minimum gets NaN and the call returns
- * FFG_ERR_EMPTY (the other rows are valid).  Synchronises `stream` once. */
+/* Batched C_p: the same quantity for n_jobs graphs at once.  Job j: g (host
+ * struct with DEVICE arrays), fitness_raw and ranks (DEVICE, precision
+ * `prec`).  f_opt is taken on the device as the smallest fitness of a
+ * local minimum (the global optimum is one, and no minimum is failed, so it
+ * equals the build's f_opt), and thr_k = f_opt * (1 + p[k]) is formed there
+ * with the same two FP64 roundings; the host fields f_opt / n_minima of g
+ * are not read, so a graph rebuilt on the device needs no new plan.
+ *
+ * centrality_batch_plan uploads the job table and p into `workspace`
+ * (DEVICE, centrality_batch_workspace_bytes(n_jobs, n_p), 256-byte
+ * aligned) and fills `plan` (plain data owned by the caller; synchronises
+ * `stream` once).  centrality_batch_run enqueues the computation -- a reset
+ * and three launches, no host work beyond argument checks, so it can be
+ * captured in a CUDA graph -- and writes plan->cp (DEVICE, n_jobs x n_p
+ * doubles, row-major) and plan->status (DEVICE, per job FFG_OK, or
+ * FFG_ERR_EMPTY when the graph has no local minimum: its row is NaN).
+ * centrality_batch_query synchronises `stream` and copies them to cp_out /
+ * status_out (HOST, each may be NULL); it returns FFG_ERR_EMPTY if any job
+ * is empty.  centrality_batch does all three (cp_out required). */
 typedef struct {
     const ffg_graph *g;
     const double *fitness_raw;
     const void *ranks;
 } ffg_cp_job;
 
+typedef struct {
+    int32_t n_jobs, n_p, prec, reserved;
+    double *cp;        /* DEVICE results, n_jobs x n_p (in the workspace) */
+    int32_t *status;   /* DEVICE per-job status (in the workspace) */
+    void *tables[8];   /* device pointers into the workspace (internal) */
+} ffg_cp_batch;
+
 size_t centrality_batch_workspace_bytes(int32_t n_jobs, int32_t n_p);
+
+ffg_status centrality_batch_plan(const ffg_cp_job *jobs, int32_t n_jobs, ffg_prec prec,
+                                 const double *p, int32_t n_p, void *workspace,
+                                 size_t ws_bytes, ffg_cp_batch *plan, void *stream);
+ffg_status centrality_batch_run(const ffg_cp_batch *plan, void *stream);
+ffg_status centrality_batch_query(const ffg_cp_batch *plan, double *cp_out,
+                                  int32_t *status_out, void *stream);
 
 ffg_status centrality_batch(const ffg_cp_job *jobs, int32_t n_jobs, ffg_prec prec,
                             const double *p, int32_t n_p, double *cp_out, void *workspace,
@@ -505,30 +561,28 @@ ffg_status centrality_batch(const ffg_cp_job *jobs, int32_t n_jobs, ffg_prec pre
  *   1. every FFG (ffg_build_batch_rerun of `build`; skipped when NULL,
  *      e.g. when the graphs are built once and only the dampings vary);
  *   2. every PageRank solve (pagerank_batch_run of `pagerank`);
- *   3. when out->cp is non-NULL, C_p of every cp job at every p
- *      (centrality_batch in the PageRank plan's precision; cp_jobs normally
- *      pair each PageRank job's graph and ranks with the graph's fitness).
- * With out == NULL only steps 1-2 are enqueued: no host work beyond argument
- * checks, no synchronisation, so the call can be captured in a CUDA graph.
- * Otherwise the call synchronises `stream` and fills every non-NULL field of
- * `out` (HOST arrays): build_status (one per build job; FFG_ERR_INVALID_ARG
- * marks a job whose recomputed sizes no longer fit its arrays, which keeps
- * its previous graph), iters / residual / pr_status (one per PageRank job)
- * and cp (n_cp_jobs x n_p, row-major).  The plans, the workspaces and every
- * buffer they name belong to the caller and must stay valid.
- * Returns the worst status: FFG_ERR_CUDA or FFG_ERR_TIMEOUT first (C_p is
- * then not computed), else the first of the build, PageRank
- * (FFG_ERR_NOT_CONVERGED) and C_p (FFG_ERR_EMPTY: a graph without a local
- * minimum, its row NaN) statuses; FFG_ERR_INVALID_ARG for a missing plan or
- * incomplete C_p arguments (nothing launched). */
+ *   3. C_p of every job of `cp` at its fractions (centrality_batch_run;
+ *      skipped when NULL).  Its jobs normally pair each PageRank job's graph
+ *      and ranks with the graph's fitness, in the PageRank plan's precision.
+ * With out == NULL the three steps are only enqueued: no host work beyond
+ * argument checks, no synchronisation, so the call can be captured in a
+ * CUDA graph (the results stay in device memory: the plans' cp / status
+ * arrays and the PageRank job outputs).  Otherwise the call synchronises
+ * `stream` and fills every non-NULL field of `out` (HOST arrays):
+ * build_status (one per build job; FFG_ERR_INVALID_ARG marks a job whose
+ * recomputed sizes no longer fit its arrays, which keeps its previous
+ * graph), iters / residual / pr_status (one per PageRank job) and cp
+ * (cp->n_jobs x cp->n_p, row-major; needs `cp`).  The plans, the workspaces
+ * and every buffer they name belong to the caller and must stay valid.
+ * Returns the worst status: FFG_ERR_CUDA or FFG_ERR_TIMEOUT first, else the
+ * first of the build, PageRank (FFG_ERR_NOT_CONVERGED) and C_p
+ * (FFG_ERR_EMPTY: a graph without a local minimum, its row NaN) statuses;
+ * FFG_ERR_INVALID_ARG for a missing or empty plan, or out->cp without `cp`
+ * (nothing launched). */
 typedef struct {
     const ffg_build_batch *build;  /* from ffg_build_batch_count + _fill, or NULL */
     const ffg_pr_batch *pagerank;  /* from pagerank_batch_plan(_tuned); required */
-    const ffg_cp_job *cp_jobs;     /* HOST, n_cp_jobs (used when out->cp != NULL) */
-    int32_t n_cp_jobs, n_p;
-    const double *p;               /* HOST, n_p fractions (e.g. 0.05) */
-    void *cp_workspace;            /* DEVICE, centrality_batch_workspace_bytes(n_cp_jobs, n_p) */
-    size_t cp_ws_bytes;
+    const ffg_cp_batch *cp;        /* from centrality_batch_plan, or NULL */
 } ffg_batch_desc;
 
 typedef struct {
@@ -536,7 +590,7 @@ typedef struct {
     int32_t *iters;                /* HOST, one per PageRank job, or NULL */
     double *residual;              /* HOST, one per PageRank job, or NULL */
     int32_t *pr_status;            /* HOST, one per PageRank job, or NULL */
-    double *cp;                    /* HOST, n_cp_jobs x n_p, or NULL (no C_p) */
+    double *cp;                    /* HOST, cp->n_jobs x cp->n_p, or NULL */
 } ffg_batch_out;
 
 ffg_status ffg_batch_run(const ffg_batch_desc *desc, ffg_batch_out *out, void *stream);

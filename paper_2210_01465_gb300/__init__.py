@@ -79,7 +79,7 @@ class ffg_pr_batch(C.Structure):
                 ("total_tiles", C.c_int64), ("jobs", C.c_void_p),
                 ("graphs", C.c_void_p), ("items", C.c_void_p), ("first", C.c_void_p),
                 ("queue", C.c_void_p),
-                ("ctl", C.c_void_p), ("total_rows", C.c_int64), ("tables", C.c_void_p * 8),
+                ("ctl", C.c_void_p), ("total_rows", C.c_int64), ("tables", C.c_void_p * 10),
                 ("param_jobs", C.c_int32), ("reserved", C.c_int32),
                 ("params", C.c_uint64 * (PARAM_JOBS * 16))]
 
@@ -107,19 +107,26 @@ class ffg_cp_job(C.Structure):
 
 
 class ffg_rows_op(C.Structure):
-    _fields_ = [("op", C.c_int32), ("reserved", C.c_int32), ("damping", C.c_double),
-                ("dangling", C.c_uint64), ("scale", C.c_double), ("w_in", C.c_void_p),
-                ("w_out", C.c_void_p), ("ranks", C.c_void_p), ("sums", C.c_void_p)]
+    _fields_ = [("op", C.c_int32), ("max_iter", C.c_int32), ("damping", C.c_double),
+                ("tol", C.c_double), ("w_in", C.c_void_p), ("w_out", C.c_void_p),
+                ("ranks", C.c_void_p), ("sums", C.c_void_p), ("ctl", C.c_void_p)]
 
 
 ROWS_INIT, ROWS_STEP, ROWS_SUM, ROWS_WRITE = 0, 1, 2, 3
+ROWS_START, ROWS_ADVANCE, ROWS_SCALE = 4, 5, 6
+ROWS_CTL_BYTES = 48   # sizeof(ffg_rows_ctl): iters, stop, converged, status (int32),
+                      # residual, prev_residual, scale (double), dangling (uint64)
+
+
+class ffg_cp_batch(C.Structure):
+    _fields_ = [("n_jobs", C.c_int32), ("n_p", C.c_int32), ("prec", C.c_int32),
+                ("reserved", C.c_int32), ("cp", C.c_void_p), ("status", C.c_void_p),
+                ("tables", C.c_void_p * 8)]
 
 
 class ffg_batch_desc(C.Structure):
     _fields_ = [("build", C.POINTER(ffg_build_batch)), ("pagerank", C.POINTER(ffg_pr_batch)),
-                ("cp_jobs", C.POINTER(ffg_cp_job)), ("n_cp_jobs", C.c_int32),
-                ("n_p", C.c_int32), ("p", C.POINTER(C.c_double)), ("cp_workspace", C.c_void_p),
-                ("cp_ws_bytes", C.c_size_t)]
+                ("cp", C.POINTER(ffg_cp_batch))]
 
 
 class ffg_batch_out(C.Structure):
@@ -138,11 +145,14 @@ ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
                 "minima_workspace_bytes", "minima_fraction",
                 "pagerank_batch_workspace_bytes", "pagerank_batch_plan",
                 "pagerank_batch_plan_tuned",
-                "pagerank_batch_run", "pagerank_batch_query", "pagerank_batch_times",
+                "pagerank_batch_run", "pagerank_batch_prepare", "pagerank_batch_solve",
+                "pagerank_batch_query", "pagerank_batch_times",
                 "pagerank_rows_w_bytes", "pagerank_rows_workspace_bytes",
                 "pagerank_rows_prepare", "pagerank_rows_run",
                 "centrality_workspace_bytes", "centrality_proportion",
-                "centrality_batch_workspace_bytes", "centrality_batch", "ffg_batch_run",
+                "centrality_batch_workspace_bytes", "centrality_batch_plan",
+                "centrality_batch_run", "centrality_batch_query", "centrality_batch",
+                "ffg_batch_run",
                 "ffg_status_str",
                 "ffg_last_error", "ffg_launch_count")
 
@@ -196,6 +206,8 @@ def load(path: str | None = None):
     lib.pagerank_batch_plan_tuned.argtypes = [P(ffg_pr_job), i32, C.c_int, P(ffg_pr_tuning), vp,
                                               sz, P(ffg_pr_batch), vp]
     lib.pagerank_batch_run.argtypes = [P(ffg_pr_batch), vp]
+    lib.pagerank_batch_prepare.argtypes = [P(ffg_pr_batch), vp]
+    lib.pagerank_batch_solve.argtypes = [P(ffg_pr_batch), vp]
     lib.pagerank_batch_query.argtypes = [P(ffg_pr_batch), vp, vp, vp, vp]
     lib.pagerank_batch_times.argtypes = [P(ffg_pr_batch), vp, vp]
     lib.pagerank_rows_w_bytes.argtypes = [C.c_int]
@@ -211,6 +223,10 @@ def load(path: str | None = None):
     lib.centrality_batch_workspace_bytes.argtypes = [i32, i32]
     lib.centrality_batch_workspace_bytes.restype = sz
     lib.centrality_batch.argtypes = [P(ffg_cp_job), i32, C.c_int, vp, i32, vp, vp, sz, vp]
+    lib.centrality_batch_plan.argtypes = [P(ffg_cp_job), i32, C.c_int, vp, i32, vp, sz,
+                                          P(ffg_cp_batch), vp]
+    lib.centrality_batch_run.argtypes = [P(ffg_cp_batch), vp]
+    lib.centrality_batch_query.argtypes = [P(ffg_cp_batch), vp, vp, vp]
     lib.ffg_batch_run.argtypes = [P(ffg_batch_desc), P(ffg_batch_out), vp]
     lib.ffg_status_str.argtypes = [C.c_int]
     lib.ffg_status_str.restype = C.c_char_p
@@ -319,6 +335,14 @@ def pagerank_batch_plan_tuned(jobs, prec: int, tuning, ws: int, ws_bytes: int,
 
 def pagerank_batch_run(plan: "ffg_pr_batch", stream: int = 0) -> int:
     return int(load().pagerank_batch_run(C.byref(plan), C.c_void_p(stream)))
+
+
+def pagerank_batch_prepare(plan: "ffg_pr_batch", stream: int = 0) -> int:
+    return int(load().pagerank_batch_prepare(C.byref(plan), C.c_void_p(stream)))
+
+
+def pagerank_batch_solve(plan: "ffg_pr_batch", stream: int = 0) -> int:
+    return int(load().pagerank_batch_solve(C.byref(plan), C.c_void_p(stream)))
 
 
 def pagerank_batch_query(plan: "ffg_pr_batch", stream: int = 0):
@@ -695,6 +719,57 @@ def centrality_many(specs, p, stream=None) -> np.ndarray:
     return out
 
 
+def centrality_batch_plan(jobs, prec: int, p, ws: int, ws_bytes: int, plan: "ffg_cp_batch",
+                          stream: int = 0) -> int:
+    pv = np.ascontiguousarray(p, dtype=np.float64)
+    return int(load().centrality_batch_plan(jobs, len(jobs), int(prec), C.c_void_p(pv.ctypes.data),
+                                            len(pv), C.c_void_p(ws), int(ws_bytes),
+                                            C.byref(plan), C.c_void_p(stream)))
+
+
+def centrality_batch_run(plan: "ffg_cp_batch", stream: int = 0) -> int:
+    return int(load().centrality_batch_run(C.byref(plan), C.c_void_p(stream)))
+
+
+def centrality_batch_query(plan: "ffg_cp_batch", stream: int = 0):
+    """Returns (status, cp (n_jobs x n_p), per-job statuses)."""
+    cp = np.full((plan.n_jobs, plan.n_p), np.nan)
+    st = np.zeros(plan.n_jobs, dtype=np.int32)
+    s = int(load().centrality_batch_query(C.byref(plan), C.c_void_p(cp.ctypes.data),
+                                          C.c_void_p(st.ctypes.data), C.c_void_p(stream)))
+    return s, cp, st
+
+
+class CentralityBatch:
+    """C_p of many graphs, planned once (``centrality_batch_plan``); ``run()``
+    only enqueues kernels (capturable), the results stay on the device in
+    ``cp`` / ``status`` until ``query()``.  ``specs``: list of (Graph,
+    fitness, ranks)."""
+
+    def __init__(self, specs, p, stream=None):
+        torch = _torch()
+        self.jobs = (ffg_cp_job * len(specs))()
+        for k, (g, fit, x) in enumerate(specs):
+            self.jobs[k].g = C.pointer(g.c)
+            self.jobs[k].fitness_raw = fit.data_ptr()
+            self.jobs[k].ranks = x.data_ptr()
+        self.prec = F64 if specs[0][2].dtype == torch.float64 else F32
+        self.p = np.ascontiguousarray(p, dtype=np.float64)
+        need = centrality_batch_workspace_bytes(len(specs), len(self.p))
+        self.ws = workspace(need, specs[0][2].device)
+        self.plan = ffg_cp_batch()
+        _check(centrality_batch_plan(self.jobs, self.prec, self.p, self.ws.data_ptr(), need,
+                                     self.plan, _stream_handle(stream)), "centrality_batch_plan")
+
+    def run(self, stream=None):
+        _check(centrality_batch_run(self.plan, _stream_handle(stream)), "centrality_batch_run")
+
+    def query(self, stream=None):
+        st, cp, sts = centrality_batch_query(self.plan, _stream_handle(stream))
+        _check(st, "centrality_batch_query", ok=(FFG_OK, FFG_ERR_EMPTY))
+        return cp, sts
+
+
 class PageRankBatch:
     """Many PageRank solves in one persistent launch (``pagerank_batch_*``).
 
@@ -742,6 +817,15 @@ class PageRankBatch:
     def run(self, stream=None):
         _check(pagerank_batch_run(self.plan, _stream_handle(stream)), "pagerank_batch_run")
 
+    def prepare(self, stream=None):
+        """The edge layout of every graph alone (``pagerank_batch_prepare``)."""
+        _check(pagerank_batch_prepare(self.plan, _stream_handle(stream)),
+               "pagerank_batch_prepare")
+
+    def solve(self, stream=None):
+        """The persistent solve alone, on the current layout (``pagerank_batch_solve``)."""
+        _check(pagerank_batch_solve(self.plan, _stream_handle(stream)), "pagerank_batch_solve")
+
     def query(self, stream=None):
         st, it, res, sts = pagerank_batch_query(self.plan, _stream_handle(stream))
         _check(st, "pagerank_batch_query", ok=(FFG_OK, FFG_ERR_NOT_CONVERGED))
@@ -770,38 +854,20 @@ def centrality(g: Graph, fitness, ranks, p, ws=None, stream=None) -> np.ndarray:
 class SpaceBatch:
     """A whole batch per call (``ffg_batch_run``): ``solves`` is a
     PageRankBatch; ``builds`` the BuildBatch of its graphs (rebuilt on every
-    run) or None; ``cp_specs`` a list of (Graph, fitness, ranks) whose C_p at
-    the fractions ``p`` every synchronising run returns (or None).
+    run) or None; ``cp`` a CentralityBatch over the solves' graphs and ranks
+    (or None).
 
     ``run(sync=False)`` only enqueues kernels (capturable in a CUDA graph);
     ``run()`` synchronises and returns (status, outputs)."""
 
-    def __init__(self, solves, builds=None, cp_specs=None, p=None):
-        self.solves, self.builds = solves, builds
+    def __init__(self, solves, builds=None, cp=None):
+        self.solves, self.builds, self.cp = solves, builds, cp
         self.desc = ffg_batch_desc()
         self.desc.pagerank = C.pointer(solves.plan)
         if builds is not None:
             self.desc.build = C.pointer(builds.plan)
-        self.n_cp = 0
-        self.p = None
-        if cp_specs:
-            if p is None or len(p) == 0:
-                raise ValueError("C_p needs the fractions p")
-            self.cp_jobs = (ffg_cp_job * len(cp_specs))()
-            for k, (g, fit, x) in enumerate(cp_specs):
-                self.cp_jobs[k].g = C.pointer(g.c)
-                self.cp_jobs[k].fitness_raw = fit.data_ptr()
-                self.cp_jobs[k].ranks = x.data_ptr()
-            self.p = np.ascontiguousarray(p, dtype=np.float64)
-            self.n_cp = len(cp_specs)
-            need = centrality_batch_workspace_bytes(self.n_cp, len(self.p))
-            self.cp_ws = workspace(need, cp_specs[0][2].device)
-            self.desc.cp_jobs = self.cp_jobs
-            self.desc.n_cp_jobs = self.n_cp
-            self.desc.n_p = len(self.p)
-            self.desc.p = self.p.ctypes.data_as(C.POINTER(C.c_double))
-            self.desc.cp_workspace = self.cp_ws.data_ptr()
-            self.desc.cp_ws_bytes = need
+        if cp is not None:
+            self.desc.cp = C.pointer(cp.plan)
 
     def run(self, sync: bool = True, stream=None):
         sh = _stream_handle(stream)
@@ -818,8 +884,8 @@ class SpaceBatch:
         if self.builds is not None:
             res["build_status"] = np.zeros(self.builds.plan.n_jobs, np.int32)
             out.build_status = res["build_status"].ctypes.data
-        if self.n_cp:
-            res["cp"] = np.full((self.n_cp, len(self.p)), np.nan)
+        if self.cp is not None:
+            res["cp"] = np.full((self.cp.plan.n_jobs, self.cp.plan.n_p), np.nan)
             out.cp = res["cp"].ctypes.data
         st = ffg_batch_run(self.desc, out, sh)
         return st, res

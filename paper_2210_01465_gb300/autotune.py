@@ -6,10 +6,11 @@ workload is the schedule of a batch: which jobs get dedicated blocks
 (`split`), how many (`grain`), how large the grid is (`max_blocks`) and how
 wide its blocks are (`block_warps`: 8 warps, several blocks per SM; 16, one
 block per SM with room for every job pointer in registers; or 24, one block
-per SM) and whether blocks follow fixed per-block lists or claim
-jobs as they free up (`claim`).  ``tune`` runs the
-batch once per candidate (same workspace, re-planned), times it with CUDA
-events and leaves the fastest plan in place.
+per SM) and the order (`claim`): fixed per-block lists, blocks claiming
+jobs as they free up, or the sweep, where every job advances one step per
+phase on the whole grid.  ``tune`` runs the batch once per candidate (same
+workspace, re-planned), times it with CUDA events and leaves the fastest
+plan in place.
 
 The plan balances the blocks with a cost model per job (edges + 20 x nodes,
 times an iteration estimate); what a job really costs also depends on how
@@ -39,6 +40,8 @@ CANDIDATES = (
     (0.1, 0.02, 0, 24, 0),
     (0.05, 0.005, 0, 24, 0),
     (0.5, 0.5, 0, 24, 1),
+    (1.0, 1.0, 0, 24, 2),
+    (1.0, 1.0, 0, 16, 2),
 )
 MEASURED = 3  # candidates re-planned with measured job costs
 
@@ -69,7 +72,9 @@ def tune(batch, candidates=CANDIDATES, reps: int = 1, table_path: str | None = N
         batch.replan(cand)
         times[(cand, False)] = _time(batch, reps)
         costs[cand] = np.maximum(batch.times(), 1e-9)  # a cost must be positive
-    for cand in sorted(candidates, key=lambda c: times[(c, False)])[:measured]:
+    # job costs only place jobs on blocks: the sweep order has no placement
+    placed = [c for c in candidates if len(c) < 5 or c[4] != 2]
+    for cand in sorted(placed, key=lambda c: times[(c, False)])[:measured]:
         batch.replan(cand, job_cost=costs[cand])
         times[(cand, True)] = _time(batch, reps)
     best_key = min(times, key=times.get)

@@ -36,14 +36,14 @@ extern "C" ffg_status ffg_batch_run(const ffg_batch_desc *d, ffg_batch_out *out,
         return set_error("desc and a planned pagerank batch are required"), FFG_ERR_INVALID_ARG;
     if (d->build && d->build->n_jobs < 1)
         return set_error("build plan is empty"), FFG_ERR_INVALID_ARG;
-    const bool want_cp = out && out->cp;
-    if (want_cp && (!d->cp_jobs || d->n_cp_jobs < 1 || !d->p || d->n_p < 1 || !d->cp_workspace))
-        return set_error("C_p needs cp_jobs, n_cp_jobs >= 1, p, n_p >= 1 and cp_workspace"),
-               FFG_ERR_INVALID_ARG;
+    if (d->cp && d->cp->n_jobs < 1) return set_error("C_p plan is empty"), FFG_ERR_INVALID_ARG;
+    if (out && out->cp && !d->cp)
+        return set_error("out->cp needs a C_p plan (desc->cp)"), FFG_ERR_INVALID_ARG;
 
-    // launches only: the graphs, then every solve
+    // launches only: the graphs, every solve, every C_p
     if (d->build) FFG_TRY(ffg_build_batch_rerun(d->build, stream));
     FFG_TRY(pagerank_batch_run(d->pagerank, stream));
+    if (d->cp) FFG_TRY(centrality_batch_run(d->cp, stream));
     if (!out) return FFG_OK;
 
     Worst w;
@@ -60,9 +60,7 @@ extern "C" ffg_status ffg_batch_run(const ffg_batch_desc *d, ffg_batch_out *out,
     w.add(pagerank_batch_query(d->pagerank, out->iters, out->residual, out->pr_status, stream));
     if (w.st == FFG_ERR_CUDA || w.st == FFG_ERR_TIMEOUT)
         return set_error("%s", w.detail.c_str()), w.st;
-    if (want_cp)
-        w.add(centrality_batch(d->cp_jobs, d->n_cp_jobs, static_cast<ffg_prec>(d->pagerank->prec),
-                               d->p, d->n_p, out->cp, d->cp_workspace, d->cp_ws_bytes, stream));
+    if (d->cp) w.add(centrality_batch_query(d->cp, out->cp, nullptr, stream));
     if (w.st != FFG_OK) set_error("%s", w.detail.c_str());
     return w.st;
 }

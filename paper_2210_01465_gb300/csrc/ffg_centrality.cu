@@ -112,6 +112,13 @@ __global__ void k_cp_final(const double *__restrict__ partials, int nblocks, int
     }
 }
 
+// the same compensated sum on the device (same operations, same order)
+__device__ double dev_neumaier(const double *v, int n) {
+    double s = 0.0, c = 0.0;
+    for (int k = 0; k < n; ++k) neumaier(s, c, v[k]);
+    return s + c;
+}
+
 double host_neumaier(const double *v, int n) {
     double s = 0.0, c = 0.0;
     for (int k = 0; k < n; ++k) {
@@ -201,9 +208,14 @@ extern "C" ffg_status centrality_proportion(const ffg_graph *g, const double *fi
 }
 
 // ---------------------------------------------------------------------------
-// batched C_p: one launch for the bucket sums of every job (blockIdx.y = job,
-// kCpBatchBlocks blocks per job), one launch for the per-job final sums, one
-// read-back.
+// batched C_p, planned once and re-run with launches only (capturable in a
+// CUDA graph).  f_opt is taken on the device as the smallest fitness of a
+// local minimum -- the global optimum is a local minimum (no neighbour is
+// better) and no minimum is failed, so this is the build's f_opt -- and the
+// thresholds f_opt * (1 + p_k) are formed there with the same two roundings
+// as on the host.  Per run: a reset of the per-job minima, one launch for
+// the minima (blockIdx.y = job), one for the bucket sums of every job, one
+// for the per-job final sums and ratios (written to device memory).
 // ---------------------------------------------------------------------------
 namespace ffg {
 namespace {
@@ -216,28 +228,100 @@ struct CpJobDev {
     const double *fit;
     const void *ranks;
     int64_t n;
-    Thresholds th;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kCpThreads) k_cp_partial_batch(const CpJobDev *__restrict__ jobs,
-                                                                  double *__restrict__ partials) {
+struct CpBatchWs {
+    CpJobDev *jobs;
+    double *p;                    // n_p fractions
+    unsigned long long *fopt;     // per job: ordered bits of the smallest minimum fitness
+    double *partials;
+    double *buckets;
+    double *cp;                   // n_jobs x n_p
+    int32_t *status;              // per job
+    size_t bytes;
+};
+
+CpBatchWs carve_cp_batch(void *base, int n_jobs) {
+    Carver c(base);
+    CpBatchWs w;
+    w.jobs = c.take<CpJobDev>(n_jobs);
+    w.p = c.take<double>(FFG_MAX_P);
+    w.fopt = c.take<unsigned long long>(n_jobs);
+    w.partials = c.take<double>(size_t(n_jobs) * kCpBatchBlocks * kBuckets * 2);
+    w.buckets = c.take<double>(size_t(n_jobs) * kBuckets);
+    w.cp = c.take<double>(size_t(n_jobs) * FFG_MAX_P);
+    w.status = c.take<int32_t>(n_jobs);
+    w.bytes = c.off;
+    return w;
+}
+
+// smallest fitness over the job's local minima (ordered bits, atomicMin)
+__global__ void __launch_bounds__(kCpThreads) k_cp_fopt_batch(const CpJobDev *__restrict__ jobs,
+                                                               unsigned long long *fopt) {
     const CpJobDev &J = jobs[blockIdx.y];
+    unsigned long long m = ~0ULL;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < J.n; v += stride)
+        if (J.is_min[v]) {
+            const unsigned long long b = ordered_bits(J.fit[J.node_raw[v]]);
+            m = b < m ? b : m;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t < m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m != ~0ULL) atomicMin(fopt + blockIdx.y, m);
+}
+
+// the job's thresholds in ascending order and the position of each p:
+// thr_k = f_opt * (1 + p_k), (1 + p_k) rounded first; equal thresholds keep
+// the order of p (a stable sort, as on the host)
+__device__ void cp_thresholds(unsigned long long fbits, const double *__restrict__ p, int n_p,
+                              Thresholds &th, int *order) {
+    const double f_opt = fbits == ~0ULL ? __builtin_nan("") : from_ordered_bits(fbits);
+    double thr[FFG_MAX_P];
+    for (int k = 0; k < n_p; ++k) thr[k] = __dmul_rn(f_opt, __dadd_rn(1.0, p[k]));
+    for (int k = 0; k < n_p; ++k) order[k] = k;
+    for (int i = 1; i < n_p; ++i) {  // insertion sort: stable
+        const int o = order[i];
+        int j = i - 1;
+        while (j >= 0 && thr[order[j]] > thr[o]) {
+            order[j + 1] = order[j];
+            --j;
+        }
+        order[j + 1] = o;
+    }
+    th.n = n_p;
+    for (int k = 0; k < n_p; ++k) th.thr[k] = thr[order[k]];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCpThreads) k_cp_partial_batch(
+    const CpJobDev *__restrict__ jobs, const double *__restrict__ p, int n_p,
+    const unsigned long long *__restrict__ fopt, double *__restrict__ partials) {
+    const CpJobDev &J = jobs[blockIdx.y];
+    __shared__ Thresholds s_th;
+    if (threadIdx.x == 0) {
+        int order[FFG_MAX_P];
+        cp_thresholds(fopt[blockIdx.y], p, n_p, s_th, order);
+    }
+    __syncthreads();
     const T *x = static_cast<const T *>(J.ranks);
     double acc[kBuckets];
-    for (int b = 0; b <= J.th.n; ++b) acc[b] = 0.0;
+    for (int b = 0; b <= n_p; ++b) acc[b] = 0.0;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < J.n; v += stride) {
         if (!J.is_min[v]) continue;
         const double f = J.fit[J.node_raw[v]];
         int b = 0;
-        while (b < J.th.n && !(f <= J.th.thr[b])) ++b;
+        while (b < n_p && !(f <= s_th.thr[b])) ++b;
         acc[b] += static_cast<double>(x[v]);
     }
     __shared__ double red[kCpThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double *out = partials + (size_t(blockIdx.y) * kCpBatchBlocks + blockIdx.x) * kBuckets * 2;
-    for (int b = 0; b <= J.th.n; ++b) {
+    for (int b = 0; b <= n_p; ++b) {
         double v = acc[b];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -253,15 +337,20 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_partial_batch(const CpJobDev 
     }
 }
 
-// block j: lane-strided compensated sums of job j's block partials per bucket
-__global__ void k_cp_final_batch(const double *__restrict__ partials, int nb,
-                                 double *__restrict__ buckets) {
+// block j: lane-strided compensated sums of job j's block partials per
+// bucket, then C_p of every p (compensated prefix sums over the sum over
+// all buckets), or NaN and FFG_ERR_EMPTY when the minima hold nothing
+__global__ void k_cp_final_batch(const double *__restrict__ partials, const double *__restrict__ p,
+                                 int n_p, const unsigned long long *__restrict__ fopt,
+                                 double *__restrict__ buckets, double *__restrict__ cp,
+                                 int32_t *__restrict__ status) {
     const int job = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     __shared__ double red[32][32][2];
     const double *base = partials + size_t(job) * kCpBatchBlocks * kBuckets * 2;
-    for (int b = warp; b <= nb; b += nwarps) {
+    double *bk = buckets + size_t(job) * kBuckets;
+    for (int b = warp; b <= n_p; b += nwarps) {
         double s = 0.0, c = 0.0;
         for (int k = lane; k < kCpBatchBlocks; k += 32) {
             neumaier(s, c, base[(size_t(k) * kBuckets + b) * 2 + 0]);
@@ -276,27 +365,30 @@ __global__ void k_cp_final_batch(const double *__restrict__ partials, int nb,
                 neumaier(ts, tc, red[warp][k][0]);
                 neumaier(ts, tc, red[warp][k][1]);
             }
-            buckets[size_t(job) * kBuckets + b] = ts + tc;
+            bk[b] = ts + tc;
         }
         __syncwarp();
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Thresholds th;
+        int order[FFG_MAX_P];
+        cp_thresholds(fopt[job], p, n_p, th, order);
+        const double sl = dev_neumaier(bk, n_p + 1);
+        const bool ok = sl > 0.0;
+        for (int k = 0; k < n_p; ++k)
+            cp[size_t(job) * n_p + order[k]] = ok ? dev_neumaier(bk, k + 1) / sl
+                                                  : __builtin_nan("");
+        status[job] = ok ? FFG_OK : FFG_ERR_EMPTY;
+    }
 }
 
-struct CpBatchWs {
-    CpJobDev *jobs;
-    double *partials;
-    double *buckets;
-    size_t bytes;
-};
-
-CpBatchWs carve_cp_batch(void *base, int n_jobs) {
-    Carver c(base);
-    CpBatchWs w;
-    w.jobs = c.take<CpJobDev>(n_jobs);
-    w.partials = c.take<double>(size_t(n_jobs) * kCpBatchBlocks * kBuckets * 2);
-    w.buckets = c.take<double>(size_t(n_jobs) * kBuckets);
-    w.bytes = c.off;
-    return w;
+ffg_status cp_batch_check(const ffg_cp_batch *plan) {
+    if (!plan || plan->n_jobs < 1 || plan->n_jobs > 65535 || plan->n_p < 1 ||
+        plan->n_p > FFG_MAX_P || !plan->tables[0] || !plan->cp || !plan->status ||
+        (plan->prec != FFG_F64 && plan->prec != FFG_F32))
+        return set_error("C_p plan is empty or incomplete"), FFG_ERR_INVALID_ARG;
+    return FFG_OK;
 }
 
 }  // namespace
@@ -308,13 +400,14 @@ extern "C" size_t centrality_batch_workspace_bytes(int32_t n_jobs, int32_t n_p) 
     return carve_cp_batch(nullptr, n_jobs).bytes;
 }
 
-extern "C" ffg_status centrality_batch(const ffg_cp_job *jobs, int32_t n_jobs, ffg_prec prec,
-                                       const double *p, int32_t n_p, double *cp_out,
-                                       void *workspace, size_t ws_bytes, void *stream_) {
+extern "C" ffg_status centrality_batch_plan(const ffg_cp_job *jobs, int32_t n_jobs,
+                                            ffg_prec prec, const double *p, int32_t n_p,
+                                            void *workspace, size_t ws_bytes,
+                                            ffg_cp_batch *plan, void *stream_) {
     clear_error();
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-    if (!jobs || n_jobs < 1 || n_jobs > 65535 || !p || !cp_out || !workspace)
-        return set_error("jobs, p, cp_out, workspace non-NULL and 1 <= n_jobs <= 65535"),
+    if (!jobs || n_jobs < 1 || n_jobs > 65535 || !p || !plan || !workspace)
+        return set_error("jobs, p, plan, workspace non-NULL and 1 <= n_jobs <= 65535"),
                FFG_ERR_INVALID_ARG;
     if (n_p < 1 || n_p > FFG_MAX_P)
         return set_error("n_p must lie in [1,%d]", FFG_MAX_P), FFG_ERR_INVALID_ARG;
@@ -329,54 +422,93 @@ extern "C" ffg_status centrality_batch(const ffg_cp_job *jobs, int32_t n_jobs, f
     if (ws_bytes < w.bytes)
         return set_error("workspace %zu bytes, need %zu", ws_bytes, w.bytes), FFG_ERR_NO_MEMORY;
     std::vector<CpJobDev> jd(n_jobs);
-    std::vector<std::vector<int>> orders(n_jobs, std::vector<int>(n_p));
-    bool empty = false;
     for (int j = 0; j < n_jobs; ++j) {
         const ffg_graph *g = jobs[j].g;
         if (!g || g->n_nodes <= 0 || !g->is_min || !g->node_raw || !jobs[j].fitness_raw ||
             !jobs[j].ranks)
             return set_error("job %d: graph, fitness or ranks missing", j), FFG_ERR_INVALID_ARG;
-        empty = empty || g->n_minima <= 0;
-        std::vector<double> thr(n_p);
-        for (int k = 0; k < n_p; ++k) {
-            volatile double onep = 1.0 + p[k];
-            thr[k] = g->f_opt * onep;
-        }
-        std::vector<int> &order = orders[j];
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return thr[a] < thr[b]; });
         jd[j].is_min = g->is_min;
         jd[j].node_raw = g->node_raw;
         jd[j].fit = jobs[j].fitness_raw;
         jd[j].ranks = jobs[j].ranks;
         jd[j].n = g->n_nodes;
-        jd[j].th.n = n_p;
-        for (int k = 0; k < n_p; ++k) jd[j].th.thr[k] = thr[order[k]];
     }
     FFG_TRY(check_cuda(cudaMemcpyAsync(w.jobs, jd.data(), sizeof(CpJobDev) * n_jobs,
                                        cudaMemcpyHostToDevice, stream), "upload jobs"));
-    const dim3 grid(kCpBatchBlocks, n_jobs);
-    if (prec == FFG_F64)
-        k_cp_partial_batch<double><<<grid, kCpThreads, 0, stream>>>(w.jobs, w.partials);
-    else
-        k_cp_partial_batch<float><<<grid, kCpThreads, 0, stream>>>(w.jobs, w.partials);
-    FFG_TRY(check_launch("k_cp_partial_batch"));
-    k_cp_final_batch<<<n_jobs, 32 * std::min(n_p + 1, 32), 0, stream>>>(w.partials, n_p, w.buckets);
-    count_launch(2);
-    FFG_TRY(check_launch("k_cp_final_batch"));
-    std::vector<double> h(size_t(n_jobs) * kBuckets);
-    FFG_TRY(check_cuda(cudaMemcpyAsync(h.data(), w.buckets, sizeof(double) * h.size(),
-                                       cudaMemcpyDeviceToHost, stream), "read buckets"));
-    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync centrality"));
-    for (int j = 0; j < n_jobs; ++j) {
-        const double *b = h.data() + size_t(j) * kBuckets;
-        const double sl = host_neumaier(b, n_p + 1);
-        for (int k = 0; k < n_p; ++k)
-            cp_out[size_t(j) * n_p + orders[j][k]] =
-                sl > 0.0 ? host_neumaier(b, k + 1) / sl : __builtin_nan("");
-    }
-    if (empty) return set_error("a job's graph has no local minimum (its C_p is NaN)"), FFG_ERR_EMPTY;
+    FFG_TRY(check_cuda(cudaMemcpyAsync(w.p, p, sizeof(double) * n_p, cudaMemcpyHostToDevice,
+                                       stream), "upload p"));
+    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync C_p plan"));
+    plan->n_jobs = n_jobs;
+    plan->n_p = n_p;
+    plan->prec = prec;
+    plan->reserved = 0;
+    plan->cp = w.cp;
+    plan->status = w.status;
+    plan->tables[0] = w.jobs;
+    plan->tables[1] = w.p;
+    plan->tables[2] = w.fopt;
+    plan->tables[3] = w.partials;
+    plan->tables[4] = w.buckets;
     return FFG_OK;
+}
+
+extern "C" ffg_status centrality_batch_run(const ffg_cp_batch *plan, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    FFG_TRY(cp_batch_check(plan));
+    const CpJobDev *jobs = static_cast<const CpJobDev *>(plan->tables[0]);
+    const double *p = static_cast<const double *>(plan->tables[1]);
+    unsigned long long *fopt = static_cast<unsigned long long *>(plan->tables[2]);
+    double *partials = static_cast<double *>(plan->tables[3]);
+    double *buckets = static_cast<double *>(plan->tables[4]);
+    const int n_jobs = plan->n_jobs, n_p = plan->n_p;
+    FFG_TRY(check_cuda(cudaMemsetAsync(fopt, 0xff, sizeof(unsigned long long) * n_jobs, stream),
+                       "memset"));
+    const dim3 grid(kCpBatchBlocks, n_jobs);
+    k_cp_fopt_batch<<<grid, kCpThreads, 0, stream>>>(jobs, fopt);
+    FFG_TRY(check_launch("k_cp_fopt_batch"));
+    if (plan->prec == FFG_F64)
+        k_cp_partial_batch<double><<<grid, kCpThreads, 0, stream>>>(jobs, p, n_p, fopt, partials);
+    else
+        k_cp_partial_batch<float><<<grid, kCpThreads, 0, stream>>>(jobs, p, n_p, fopt, partials);
+    FFG_TRY(check_launch("k_cp_partial_batch"));
+    k_cp_final_batch<<<n_jobs, 32 * std::min(n_p + 1, 32), 0, stream>>>(
+        partials, p, n_p, fopt, buckets, plan->cp, plan->status);
+    count_launch(3);
+    return check_launch("k_cp_final_batch");
+}
+
+extern "C" ffg_status centrality_batch_query(const ffg_cp_batch *plan, double *cp_out,
+                                             int32_t *status_out, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    FFG_TRY(cp_batch_check(plan));
+    std::vector<int32_t> st(plan->n_jobs);
+    if (cp_out)
+        FFG_TRY(check_cuda(cudaMemcpyAsync(cp_out, plan->cp,
+                                           sizeof(double) * plan->n_jobs * plan->n_p,
+                                           cudaMemcpyDeviceToHost, stream), "read C_p"));
+    FFG_TRY(check_cuda(cudaMemcpyAsync(st.data(), plan->status, sizeof(int32_t) * st.size(),
+                                       cudaMemcpyDeviceToHost, stream), "read C_p status"));
+    FFG_TRY(check_cuda(cudaStreamSynchronize(stream), "sync C_p"));
+    if (status_out) std::copy(st.begin(), st.end(), status_out);
+    for (int32_t s : st)
+        if (s != FFG_OK)
+            return set_error("a job's graph has no local minimum (its C_p is NaN)"), FFG_ERR_EMPTY;
+    return FFG_OK;
+}
+
+extern "C" ffg_status centrality_batch(const ffg_cp_job *jobs, int32_t n_jobs, ffg_prec prec,
+                                       const double *p, int32_t n_p, double *cp_out,
+                                       void *workspace, size_t ws_bytes, void *stream) {
+    if (!cp_out) {
+        clear_error();
+        return set_error("cp_out is NULL"), FFG_ERR_INVALID_ARG;
+    }
+    ffg_cp_batch plan;
+    FFG_TRY(centrality_batch_plan(jobs, n_jobs, prec, p, n_p, workspace, ws_bytes, &plan, stream));
+    FFG_TRY(centrality_batch_run(&plan, stream));
+    return centrality_batch_query(&plan, cp_out, nullptr, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -128,7 +128,7 @@ struct PrCtl {
 struct PrWs {
     PrCtl *ctl;
     void *w0, *w1;
-    double *rinv;         // FP64: 1 / outdeg per row
+    double *rinv;         // 1 / outdeg per row (FP32: as floats)
     uint2 *desc;          // tile descriptors (off, mask)
     int32_t *cnt;         // per tile: descriptors, padded to a multiple of kU
     uint2 *tinfo;         // per tile: (first descriptor / kU, cnt)
@@ -160,7 +160,8 @@ PrWs carve(void *base, int64_t n, int64_t e, ffg_prec prec) {
     w.ctl = c.take<PrCtl>(1);
     w.w0 = c.take<char>(size_t(n) * w_bytes(prec));
     w.w1 = c.take<char>(size_t(n) * w_bytes(prec));
-    w.rinv = prec == FFG_F64 ? c.take<double>(size_t(n)) : nullptr;
+    w.rinv = prec == FFG_F64 ? c.take<double>(size_t(n))
+                             : reinterpret_cast<double *>(c.take<float>(size_t(n)));
     w.desc = c.take<uint2>(size_t(desc_capacity(n, e)));
     w.cnt = c.take<int32_t>(size_t((n + 31) / 32));
     w.tinfo = c.take<uint2>(size_t((n + 31) / 32));
@@ -273,19 +274,35 @@ __device__ bool group_barrier(PrCtl *ctl, unsigned target, int group) {
 // The residual, the dangling mass and the sum of x are accumulated as 64-bit
 // fixed-point integers with quantum 2^-60 (all three are sums of
 // non-negative values below 8).  Integer sums are exact and independent of
-// order, so they are deterministic however tiles are scheduled.  The
-// conversion truncates the significand shifted into place, with integer
-// instructions only: conversions to 64-bit integers, like FP64 arithmetic,
-// run on a narrow pipe on this part.
+// order, so they are deterministic however tiles are scheduled.  Each
+// conversion truncates, floor(x * 2^60), without conversions to 64-bit
+// integers (those, like FP64 arithmetic, run on a narrow pipe on this
+// part): an FP32 value splits into floor(x * 2^28) and the rest of x * 2^28
+// times 2^32, both exact in FP32 and converted to 32 bits (the same integer
+// as shifting the significand into place, for every float below 4: checked
+// exhaustively on the host); an FP64 value has its significand shifted into
+// place with integer instructions.
 constexpr double kFix = 1152921504606846976.0;  // 2^60
 constexpr long long kFixSat = 1LL << 62;        // stands for values >= 4 (never reached)
+#ifndef FFG_PR_FIXCONV
+#define FFG_PR_FIXCONV 1
+#endif
 __device__ __forceinline__ long long to_fix(float x) {  // x >= 0
+#if FFG_PR_FIXCONV
+    if (!(x < 4.0f)) return kFixSat;
+    const float y = __fmul_rn(x, 268435456.0f);  // x * 2^28, exact
+    const float h = floorf(y);
+    const uint32_t hi = static_cast<uint32_t>(h);  // < 2^30
+    const uint32_t lo = static_cast<uint32_t>(__fmul_rn(__fsub_rn(y, h), 4294967296.0f));
+    return static_cast<long long>((static_cast<unsigned long long>(hi) << 32) | lo);
+#else
     const uint32_t b = __float_as_uint(x);
     if (b < 0x00800000u) return 0;                    // zero or below 2^-126
     const int e = static_cast<int>(b >> 23) - 90;     // x * 2^60 = m * 2^e
     const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
     if (e >= 39) return kFixSat;
     return e >= 0 ? static_cast<long long>(m << e) : (e > -24 ? static_cast<long long>(m >> -e) : 0);
+#endif
 }
 __device__ __forceinline__ long long to_fix(double x) {  // x >= 0
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
@@ -544,25 +561,48 @@ template <typename T>
 struct Rows;
 
 template <>
+#ifndef FFG_PR_RCP32
+#define FFG_PR_RCP32 0
+#endif
+template <>
 struct Rows<float> {
     using Real = float;
     using W = float;
+#if FFG_PR_RCP32
+    // the correctly rounded reciprocal of the out-degree, formed once per
+    // solve by the prologue (the array `rinv` then holds floats)
+    struct Extra {
+        float r;
+    };
+    __device__ static void store_rinv(double *rinv, int64_t v, int od) {
+        reinterpret_cast<float *>(rinv)[v] = od ? __frcp_rn(static_cast<float>(od)) : 1.0f;
+    }
+    __device__ static void load_extra(Extra &e, const double *rinv, int v) {
+        e.r = v >= 0 ? reinterpret_cast<const float *>(rinv)[v] : 1.0f;
+    }
+    __device__ static float recip(const Extra &e, int) { return e.r; }
+#else
     struct Extra {};
+    __device__ static void store_rinv(double *, int64_t, int) {}
+    __device__ static void load_extra(Extra &, const double *, int) {}
+    __device__ static float recip(const Extra &, int od) {
+        return __frcp_rn(static_cast<float>(od));
+    }
+#endif
     __device__ static W init(double x0, int od) { return static_cast<float>(od ? x0 / od : x0); }
     __device__ static double x_of(W w, int od) {
         return od ? static_cast<double>(w) * od : static_cast<double>(w);
     }
     __device__ static long long fix_x(W w, int od) { return to_fix(x_of(w, od)); }
-    __device__ static void load_extra(Extra &, const double *, int) {}
     // x' = alpha*s + c from the row's in-sum; w' = x'/outdeg as x' times the
     // correctly rounded reciprocal (two roundings, no division sequence)
-    __device__ static void update(float s, float a, float c, int od, W wold, const Extra &,
+    __device__ static void update(float s, float a, float c, int od, W wold, const Extra &e,
                                   W *dst, Fix3 &f) {
         const float xo = od ? wold * static_cast<float>(od) : wold;
         const float xn = a * s + c;
         f.r += to_fix(xn > xo ? xn - xo : xo - xn);
         if (od == 0) f.d += to_fix(xn);
-        *dst = od ? xn * __frcp_rn(static_cast<float>(od)) : xn;
+        *dst = od ? xn * recip(e, od) : xn;
     }
 };
 
@@ -576,8 +616,11 @@ struct Rows<double> {
     __device__ static W init(double x0, int od) { return od ? x0 / od : x0; }
     __device__ static double x_of(W w, int od) { return od ? w * od : w; }
     __device__ static long long fix_x(W w, int od) { return to_fix(x_of(w, od)); }
+    __device__ static void store_rinv(double *rinv, int64_t v, int od) {
+        rinv[v] = od ? 1.0 / od : 1.0;
+    }
     __device__ static void load_extra(Extra &e, const double *rinv, int v) {
-        e.rinv = v >= 0 ? __ldg(rinv + v) : 1.0;
+        e.rinv = v >= 0 ? rinv[v] : 1.0;  // written by the prologue: a plain load
     }
     __device__ static void update(double s, double a, double c, int od, W wold, const Extra &e,
                                   W *dst, Fix3 &f) {
@@ -603,8 +646,11 @@ struct Rows<F64x> {
     __device__ static long long fix_x(W w, int od) {
         return fix60(od ? fx_mul(w, static_cast<uint32_t>(od)) : w);
     }
+    __device__ static void store_rinv(double *rinv, int64_t v, int od) {
+        rinv[v] = od ? 1.0 / od : 1.0;
+    }
     __device__ static void load_extra(Extra &e, const double *rinv, int v) {
-        e.rinv = v >= 0 ? __ldg(rinv + v) : 1.0;
+        e.rinv = v >= 0 ? rinv[v] : 1.0;  // written by the prologue: a plain load
     }
     __device__ static void update(double s, double a, double c, int od, W wold, const Extra &e,
                                   W *dst, Fix3 &f) {
@@ -755,30 +801,27 @@ struct Accum<F64x> {
 };
 
 // Sum over the in-edges of this lane's row (wrow = w + row): the tile's
-// descriptors stream in segments of kSegD; the segment after the current one
-// (or the first segment of the next tile) is copied while the current one is
+// `cnt` descriptors (from dcur) stream in segments of kSegD; the segment
+// after the current one (or the first segment of the next tile: ncnt
+// descriptors from dnxt, when next_any) is copied while the current one is
 // gathered.
 template <typename T>
-__device__ __forceinline__ bool tile_sum(const uint2 *__restrict__ desc, const TileInfo<T> &cur,
-                                         const TileInfo<T> &nxt, bool has_next, Stream &st,
+__device__ __forceinline__ bool tile_sum(const uint2 *dcur, int cnt, const uint2 *dnxt, int ncnt,
+                                         bool next_any, Stream &st,
                                          const typename Rows<T>::W *wrow, uint32_t bit, int lane,
                                          typename Rows<T>::Real &sum) {
-    const int cnt = cur.cnt;
     const int nseg = (cnt + kSegD - 1) / kSegD;
-    const bool next_any = has_next && nxt.cnt > 0;
     Accum<T> acc;
     for (int sg = 0; sg < nseg; ++sg) {
         const int c0 = sg * kSegD;
         const int m = cnt - c0 < kSegD ? cnt - c0 : kSegD;
-        if (!st.issued) st.issue(desc + size_t(cur.d8) * kU + c0, m, st.buf, lane);
+        if (!st.issued) st.issue(dcur + c0, m, st.buf, lane);
         if (sg + 1 < nseg) {
             const int c1 = c0 + kSegD;
-            st.issue(desc + size_t(cur.d8) * kU + c1, cnt - c1 < kSegD ? cnt - c1 : kSegD,
-                     st.buf ^ 1, lane);
+            st.issue(dcur + c1, cnt - c1 < kSegD ? cnt - c1 : kSegD, st.buf ^ 1, lane);
             st.issued = true;
         } else if (next_any) {
-            st.issue(desc + size_t(nxt.d8) * kU, nxt.cnt < kSegD ? nxt.cnt : kSegD, st.buf ^ 1,
-                     lane);
+            st.issue(dnxt, ncnt < kSegD ? ncnt : kSegD, st.buf ^ 1, lane);
             st.issued = true;
         } else {
             st.issued = false;
@@ -793,11 +836,21 @@ __device__ __forceinline__ bool tile_sum(const uint2 *__restrict__ desc, const T
         st.buf ^= 1;
     }
     if (nseg == 0 && !st.issued && next_any) {
-        st.issue(desc + size_t(nxt.d8) * kU, nxt.cnt < kSegD ? nxt.cnt : kSegD, st.buf, lane);
+        st.issue(dnxt, ncnt < kSegD ? ncnt : kSegD, st.buf, lane);
         st.issued = true;
     }
     sum = acc.value();
     return true;
+}
+
+// tile_sum for two tiles of one layout
+template <typename T>
+__device__ __forceinline__ bool tile_sum(const uint2 *__restrict__ desc, const TileInfo<T> &cur,
+                                         const TileInfo<T> &nxt, bool has_next, Stream &st,
+                                         const typename Rows<T>::W *wrow, uint32_t bit, int lane,
+                                         typename Rows<T>::Real &sum) {
+    return tile_sum<T>(desc + size_t(cur.d8) * kU, cur.cnt, desc + size_t(nxt.d8) * kU, nxt.cnt,
+                       has_next && nxt.cnt > 0, st, wrow, bit, lane, sum);
 }
 
 // First tile of part w when the tiles are split into nw contiguous ranges of
@@ -833,7 +886,7 @@ struct JobDev {
     const uint2 *desc;
     const uint2 *tinfo;
     const int32_t *perm;
-    double *rinv;  // FP64 only: 1 / outdeg per row
+    double *rinv;  // 1 / outdeg per row (FP32: as floats), written by the prologue
     const int64_t *tpre;
     const int64_t *apre;  // rows with in-edges: apre[n] - apre[0]
     void *ranks, *w0, *w1;
@@ -889,7 +942,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     const int nb = J.group;
     using WS = typename Rows<T>::W;
     WS *w0 = static_cast<WS *>(J.w0), *w1 = static_cast<WS *>(J.w1);
-    double *rinv = J.rinv;  // FP64: 1 / outdeg per row
+    double *rinv = J.rinv;  // 1 / outdeg per row
     PrCtl *ctl = J.ctl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -927,7 +980,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
             const double x0 = J.init ? static_cast<double>(ranks[v]) : inv_n;
             const int32_t od = __ldg(outdeg + v);
             w0[v] = Rows<T>::init(x0, od);
-            if (rinv) rinv[v] = od ? 1.0 / od : 1.0;
+            Rows<T>::store_rinv(rinv, v, od);
             if (od == 0) acc0.d += to_fix(x0);
         }
         const Fix3 b = block_sum_fix<W>(acc0);
@@ -1185,6 +1238,465 @@ __global__ void __launch_bounds__(32 * W, W == kWarpsBatch ? FFG_PR_MINBLOCKS : 
         const int2 item = P.items[i];
         if (!run_job<T, W>(P.jobs[item.x], item.y, st)) return;
     }
+}
+
+// ---------------------------------------------------------------------------
+// The sweep schedule: all jobs of a batch advance in lock-step on the whole
+// grid.  A phase is one step of every unfinished job -- its prologue, one
+// iteration, the sum of its x, or the write of its normalised ranks -- and
+// one grid barrier separates phases.  A step's work is cut into units:
+// tiles of 32 slots (an iteration's rows with in-edges) and chunks of
+// kSweepRows rows (the element-wise work: prologue, rows without in-edges,
+// sum, write), numbered over all jobs, job after job.  Block b owns the
+// b-th equal share of a phase's units and its warps claim them in order
+// through a counter in global memory; a warp whose block's share is used up
+// claims units left in the other blocks' shares, so the phase ends when the
+// work does, whatever each unit cost.  After the barrier every block reads
+// the jobs' fixed-point sums and takes the same decisions (iteration count,
+// stop, teleport term, normalisation) in its own shared-memory copy of the
+// jobs' states: exact integer sums do not depend on which block added what.
+// One iteration of every job costs one barrier, not one per job, and no
+// block waits for another job's blocks.
+// ---------------------------------------------------------------------------
+constexpr int kSweepRows = 256;   // rows of an element-wise unit
+constexpr int kSweepClaim = 2;    // units taken per claim from a block's share
+enum : int { kSwInit = 0, kSwIter = 1, kSwSum = 2, kSwWrite = 3, kSwDone = 4 };
+
+// one job's state, identical in every block (shared memory)
+struct SwJob {
+    double res, prev_res, inv_s, c;
+    int mode, it, converged, wsel;  // wsel: the w buffer holding the current x
+    int ntiles, nempty, nrows, units;  // tiles, chunks of rows without in-edges, chunks of rows
+};
+
+struct SweepCtl {
+    unsigned int barrier;  // grid barrier arrivals
+    int status;            // first failure (FFG_ERR_TIMEOUT), 0 if none
+};
+struct SweepRange {
+    int tag, start, len, pad;  // the phase it belongs to, its units
+};
+
+struct SweepArgs {
+    const JobDev *jobs;
+    SweepCtl *ctl;
+    SweepRange *ranges;  // [2][nb], by phase parity
+    int *ctr;            // [2][nb]: units claimed from each block's share
+    int n_jobs, nb;
+};
+
+template <int W>
+constexpr size_t sweep_smem_bytes(int n_jobs) {
+    return pr_smem_bytes<W>() + size_t(n_jobs) * (sizeof(SwJob) + sizeof(JobDev)) +
+           (size_t(n_jobs) + 1) * sizeof(int);
+}
+
+// grid barrier over all nb blocks (bounded); false if the run must stop
+__device__ bool sweep_barrier(SweepCtl *ctl, unsigned target, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        red_release_add(&ctl->barrier, 1u);
+        const uint64_t t0 = global_ns();
+        unsigned ns = 0;
+        int ok = 1;
+        for (uint32_t polls = 0; ld_acquire(&ctl->barrier) < target; ++polls) {
+            if ((polls & 15) == 15 && *(volatile int *)&ctl->status != 0) { ok = 0; break; }
+            if (polls > (1u << 24) || global_ns() - t0 > kTimeoutNs) {
+                atomicCAS(&ctl->status, 0, (int)FFG_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            if (polls > 64) {
+                __nanosleep(ns);
+                ns = ns < 32 ? 32 : (ns < 256 ? ns << 1 : ns);
+            }
+        }
+        if (*(volatile int *)&ctl->status != 0) ok = 0;
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// A unit: its job, kind (0 none, 1 tile, 2 chunk) and index within the step.
+struct SwUnit {
+    int job, kind, idx;
+};
+
+// global unit u -> its job (binary search over the jobs' first units, from
+// the job of the previous unit) and its kind
+__device__ __forceinline__ SwUnit sweep_unit(int u, const int *spre, const SwJob *sj, int n_jobs,
+                                             int hint) {
+    SwUnit r;
+    if (u < 0) {
+        r.job = 0;
+        r.kind = 0;
+        r.idx = 0;
+        return r;
+    }
+    int j = hint;
+    if (!(spre[j] <= u && u < spre[j + 1])) {
+        int lo = 0, hi = n_jobs - 1;  // last job whose first unit is <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (spre[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        j = lo;
+    }
+    r.job = j;
+    r.idx = u - spre[j];
+    r.kind = (sj[j].mode == kSwIter && r.idx < sj[j].ntiles) ? 1 : 2;
+    return r;
+}
+
+// element-wise unit: chunk `idx` of job J in state s (mode INIT, ITER rows
+// without in-edges, SUM or WRITE); each lane takes every 32nd row of the
+// chunk, four at a time
+template <typename T>
+__device__ void sweep_chunk(const JobDev &J, const SwJob &s, int idx, Fix3 &f, int lane) {
+    using WS = typename Rows<T>::W;
+    using R = typename Rows<T>::Real;
+    WS *wb[2] = {static_cast<WS *>(J.w0), static_cast<WS *>(J.w1)};
+    const int64_t n = J.n;
+    constexpr int kI = 4;
+    if (s.mode == kSwInit) {
+        const double inv_n = 1.0 / static_cast<double>(n);
+        const R *ranks = static_cast<const R *>(J.ranks);
+        for (int r0 = 0; r0 < kSweepRows; r0 += 32 * kI) {
+            int32_t od[kI];
+            double x0[kI];
+#pragma unroll
+            for (int k = 0; k < kI; ++k) {
+                const int64_t v = int64_t(idx) * kSweepRows + r0 + 32 * k + lane;
+                od[k] = v < n ? __ldg(J.outdeg + v) : 0;
+                x0[k] = (v < n && J.init) ? static_cast<double>(ranks[v]) : inv_n;
+            }
+#pragma unroll
+            for (int k = 0; k < kI; ++k) {
+                const int64_t v = int64_t(idx) * kSweepRows + r0 + 32 * k + lane;
+                if (v >= n) continue;
+                wb[0][v] = Rows<T>::init(x0[k], od[k]);
+                Rows<T>::store_rinv(J.rinv, v, od[k]);
+                if (od[k] == 0) f.d += to_fix(x0[k]);
+            }
+        }
+        return;
+    }
+    if (s.mode == kSwIter) {  // rows without in-edges: x' = c
+        const WS *wc = wb[s.wsel];
+        WS *wn = wb[s.wsel ^ 1];
+        const R a = static_cast<R>(J.alpha), c = static_cast<R>(s.c);
+        const int64_t base = (int64_t(s.ntiles) << 5) + int64_t(idx) * kSweepRows;
+        for (int r0 = 0; r0 < kSweepRows; r0 += 32 * kI) {
+            int v[kI];
+#pragma unroll
+            for (int k = 0; k < kI; ++k) {
+                const int64_t i = base + r0 + 32 * k + lane;
+                v[k] = i < n ? __ldg(J.perm + i) : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < kI; ++k) {
+                if (v[k] < 0) continue;
+                typename Rows<T>::Extra ex;
+                Rows<T>::load_extra(ex, J.rinv, v[k]);
+                Rows<T>::update(R(0), a, c, __ldg(J.outdeg + v[k]), wc[v[k]], ex, wn + v[k], f);
+            }
+        }
+        return;
+    }
+    const WS *wc = wb[s.wsel];
+    R *ranks = static_cast<R *>(J.ranks);
+    for (int r0 = 0; r0 < kSweepRows; r0 += 32 * kI) {
+        int32_t od[kI];
+        WS w[kI];
+#pragma unroll
+        for (int k = 0; k < kI; ++k) {
+            const int64_t v = int64_t(idx) * kSweepRows + r0 + 32 * k + lane;
+            od[k] = v < n ? __ldg(J.outdeg + v) : 0;
+            w[k] = v < n ? wc[v] : WS{};
+        }
+#pragma unroll
+        for (int k = 0; k < kI; ++k) {
+            const int64_t v = int64_t(idx) * kSweepRows + r0 + 32 * k + lane;
+            if (v >= n) continue;
+            if (s.mode == kSwSum) f.s += Rows<T>::fix_x(w[k], od[k]);
+            else ranks[v] = static_cast<R>(Rows<T>::x_of(w[k], od[k]) * s.inv_s);
+        }
+    }
+}
+
+// a warp's sums of one job into the job's accumulator of this phase
+__device__ __forceinline__ void sweep_flush(const JobDev *sjd, int job, int buf, Fix3 &f,
+                                            int lane) {
+    if (job < 0) return;
+    const long long r = warp_sum_ll(f.r), d = warp_sum_ll(f.d), s = warp_sum_ll(f.s);
+    if (lane == 0) {
+        unsigned long long *acc = sjd[job].ctl->acc[buf];
+        if (r) atomicAdd(acc + 0, static_cast<unsigned long long>(r));
+        if (d) atomicAdd(acc + 1, static_cast<unsigned long long>(d));
+        if (s) atomicAdd(acc + 2, static_cast<unsigned long long>(s));
+    }
+    f = Fix3{};
+}
+
+// the next batch of units for this warp: from its block's share while it
+// lasts, then from another block's share that has units left (lanes look at
+// the blocks in parallel); returns [*u0, *u1), empty when the phase's work
+// is all claimed
+__device__ void sweep_claim(const SweepArgs &A, int parity, int phase, int own_start,
+                            int own_len, bool &own_left, int *u0, int *u1, int lane) {
+    int a = 0, b = 0;
+    if (own_left) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(A.ctr + parity * A.nb + blockIdx.x, kSweepClaim);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k < own_len) {
+            *u0 = own_start + k;
+            *u1 = own_start + (k + kSweepClaim < own_len ? k + kSweepClaim : own_len);
+            return;
+        }
+        own_left = false;
+    }
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        int cand = -1, cstart = 0, clen = 0;
+        for (int i = lane; i < A.nb && cand < 0; i += 32) {
+            const int v = (blockIdx.x + 1 + i) % A.nb;
+            const SweepRange *rg = A.ranges + parity * A.nb + v;
+            if (ld_acquire(reinterpret_cast<const unsigned *>(&rg->tag)) != unsigned(phase))
+                continue;
+            const int len = *(volatile const int *)&rg->len;
+            if (*(volatile const int *)(A.ctr + parity * A.nb + v) < len) {
+                cand = v;
+                cstart = *(volatile const int *)&rg->start;
+                clen = len;
+            }
+        }
+        const unsigned any = __ballot_sync(0xffffffffu, cand >= 0);
+        if (!any) break;
+        const int src = __ffs(any) - 1;
+        const int v = __shfl_sync(0xffffffffu, cand, src);
+        const int vs = __shfl_sync(0xffffffffu, cstart, src);
+        const int vl = __shfl_sync(0xffffffffu, clen, src);
+        int k = 0;
+        if (lane == 0) k = atomicAdd(A.ctr + parity * A.nb + v, kSweepClaim);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k < vl) {
+            a = vs + k;
+            b = vs + (k + kSweepClaim < vl ? k + kSweepClaim : vl);
+            break;
+        }
+    }
+    *u0 = a;
+    *u1 = b;
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(32 * W, 1) k_pagerank_sweep(const SweepArgs A) {
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    Stream st = make_stream<W>(s_dyn);
+    using R = typename Rows<T>::Real;
+    using WS = typename Rows<T>::W;
+    JobDev *sjd = reinterpret_cast<JobDev *>(s_dyn + pr_smem_bytes<W>());
+    SwJob *sj = reinterpret_cast<SwJob *>(sjd + A.n_jobs);
+    int *spre = reinterpret_cast<int *>(sj + A.n_jobs);
+    __shared__ int s_ok, s_start, s_len;
+    __shared__ int s_wsum[W];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nj = A.n_jobs;
+
+    // the job table and every job's first state
+    for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+        sjd[j] = A.jobs[j];
+        const JobDev &J = sjd[j];
+        SwJob s;
+        s.res = s.prev_res = __longlong_as_double(0x7ff0000000000000LL);
+        s.inv_s = 1.0;
+        s.c = 0.0;
+        s.mode = kSwInit;
+        s.it = s.converged = s.wsel = 0;
+        const int64_t act = J.apre[J.n] - J.apre[0];
+        s.ntiles = static_cast<int>((act + 31) >> 5);
+        const int64_t rest = J.n - (int64_t(s.ntiles) << 5);
+        s.nempty = rest > 0 ? static_cast<int>((rest + kSweepRows - 1) / kSweepRows) : 0;
+        s.nrows = static_cast<int>((J.n + kSweepRows - 1) / kSweepRows);
+        s.units = 0;
+        sj[j] = s;
+    }
+    __syncthreads();
+
+    for (int phase = 0;; ++phase) {
+        const int buf = phase % 3, parity = phase & 1;
+        // advance every job on the sums of the previous phase
+        for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+            SwJob &s = sj[j];
+            const JobDev &J = sjd[j];
+            if (phase > 0 && s.mode != kSwDone) {
+                const unsigned long long *acc = J.ctl->acc[(phase - 1) % 3];
+                if (s.mode == kSwInit) {
+                    s.c = teleport(J.alpha, __ldcg(acc + 1), J.n);
+                    s.mode = kSwIter;
+                } else if (s.mode == kSwIter) {
+                    const double r = static_cast<double>(__ldcg(acc + 0)) / kFix;
+                    s.prev_res = s.res;
+                    s.res = r;
+                    ++s.it;
+                    s.wsel ^= 1;
+                    bool stop = false;
+                    if (r < J.tol) s.converged = 1, stop = true;
+                    else if (sizeof(R) == 4 && r >= s.prev_res) s.converged = 1, stop = true;
+                    else if (s.it >= J.max_iter) stop = true;
+                    if (stop) s.mode = kSwSum;
+                    else s.c = teleport(J.alpha, __ldcg(acc + 1), J.n);
+                } else if (s.mode == kSwSum) {
+                    s.inv_s = 1.0 / (static_cast<double>(__ldcg(acc + 2)) / kFix);
+                    s.mode = kSwWrite;
+                } else {  // the ranks are written
+                    s.mode = kSwDone;
+                    if (blockIdx.x == 0) {
+                        J.ctl->iters = s.it;
+                        J.ctl->residual = s.res;
+                        J.ctl->converged = s.converged;
+                        J.ctl->nblocks = A.nb;
+                    }
+                }
+            }
+            s.units = s.mode == kSwIter ? s.ntiles + s.nempty
+                      : s.mode == kSwDone ? 0
+                                          : s.nrows;
+            // the accumulator of the next phase starts at zero; its last
+            // readers passed the previous barrier
+            if (blockIdx.x == 0) {
+                unsigned long long *nx = J.ctl->acc[(phase + 1) % 3];
+                nx[0] = nx[1] = nx[2] = 0;
+            }
+        }
+        __syncthreads();
+        // first unit of every job (exclusive scan, consecutive jobs per thread)
+        {
+            const int per = (nj + blockDim.x - 1) / blockDim.x;
+            const int j0 = threadIdx.x * per;
+            int tot = 0;
+            for (int j = j0; j < j0 + per && j < nj; ++j) tot += sj[j].units;
+            int incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            int before = 0;
+            for (int w = 0; w < warp; ++w) before += s_wsum[w];
+            int run = before + incl - tot;
+            for (int j = j0; j < j0 + per && j < nj; ++j) {
+                spre[j] = run;
+                run += sj[j].units;
+            }
+            if (threadIdx.x == blockDim.x - 1) spre[nj] = before + incl;
+        }
+        __syncthreads();
+        const int total = spre[nj];
+        if (total == 0) break;  // every job is done
+        if (threadIdx.x == 0) {
+            const int a = static_cast<int>(int64_t(total) * blockIdx.x / A.nb);
+            const int b = static_cast<int>(int64_t(total) * (blockIdx.x + 1) / A.nb);
+            s_start = a;
+            s_len = b - a;
+            SweepRange *rg = A.ranges + parity * A.nb + blockIdx.x;
+            rg->start = a;
+            rg->len = b - a;
+            __threadfence();
+            atomicExch(&rg->tag, phase);
+            A.ctr[(parity ^ 1) * A.nb + blockIdx.x] = 0;  // the next phase's counter
+        }
+        __syncthreads();
+
+        // the units: a pipeline of tiles (the next tile's head and row data
+        // and its first descriptor segment load while the current one is
+        // summed); chunks are done as they come
+        bool own_left = true;
+        int q0 = 0, q1 = 0;   // this warp's claimed, not yet taken units
+        int acc_job = -1;
+        Fix3 facc;
+        bool failed = false;
+        const int own_start = s_start, own_len = s_len;
+        auto next = [&](int hint) -> SwUnit {
+            if (q0 == q1) sweep_claim(A, parity, phase, own_start, own_len, own_left, &q0, &q1,
+                                      lane);
+            const int u = q0 < q1 ? q0++ : -1;
+            return sweep_unit(u, spre, sj, nj, hint);
+        };
+        SwUnit u0 = next(0);
+        SwUnit u1 = next(u0.job);
+        TileInfo<T> cur, nxt;
+        bool cur_row = false;
+        if (u0.kind == 1) cur = load_head<T>(u0.idx, static_cast<int>(sjd[u0.job].n),
+                                             sjd[u0.job].tinfo, sjd[u0.job].perm, lane);
+        if (u1.kind == 1) nxt = load_head<T>(u1.idx, static_cast<int>(sjd[u1.job].n),
+                                             sjd[u1.job].tinfo, sjd[u1.job].perm, lane);
+        while (u0.kind != 0 && !failed) {
+            const JobDev &J0 = sjd[u0.job];
+            const SwJob &s0 = sj[u0.job];
+            if (u0.job != acc_job) {
+                sweep_flush(sjd, acc_job, buf, facc, lane);
+                acc_job = u0.job;
+            }
+            WS *wb0[2] = {static_cast<WS *>(J0.w0), static_cast<WS *>(J0.w1)};
+            if (u0.kind == 2) {
+                sweep_chunk<T>(J0, s0, u0.idx - (s0.mode == kSwIter ? s0.ntiles : 0), facc,
+                               lane);
+                u0 = u1;
+                cur = nxt;
+                cur_row = false;
+                u1 = next(u0.job);
+                if (u1.kind == 1) nxt = load_head<T>(u1.idx, static_cast<int>(sjd[u1.job].n),
+                                                     sjd[u1.job].tinfo, sjd[u1.job].perm, lane);
+                continue;
+            }
+            if (!cur_row) load_row<T>(cur, J0.outdeg, wb0[s0.wsel], J0.rinv);
+            const SwUnit u2 = next(u1.kind ? u1.job : u0.job);
+            if (u1.kind == 1) {
+                const JobDev &J1 = sjd[u1.job];
+                WS *w1c = static_cast<WS *>(sj[u1.job].wsel ? J1.w1 : J1.w0);
+                load_row<T>(nxt, J1.outdeg, w1c, J1.rinv);
+            }
+            TileInfo<T> nx2;
+            if (u2.kind == 1) nx2 = load_head<T>(u2.idx, static_cast<int>(sjd[u2.job].n),
+                                                 sjd[u2.job].tinfo, sjd[u2.job].perm, lane);
+            const int v = cur.v;
+            const WS *wc = wb0[s0.wsel];
+            R sum = R(0);
+            const bool next_tile = u1.kind == 1 && nxt.cnt > 0;
+            const uint2 *dn = next_tile ? sjd[u1.job].desc + size_t(nxt.d8) * kU : nullptr;
+            if (!tile_sum<T>(J0.desc + size_t(cur.d8) * kU, cur.cnt, dn, next_tile ? nxt.cnt : 0,
+                             next_tile, st, wc + (v < 0 ? 0 : v), 1u << lane, lane, sum)) {
+                failed = true;
+                break;
+            }
+            if (v >= 0)
+                Rows<T>::update(sum, static_cast<R>(J0.alpha), static_cast<R>(s0.c), cur.od,
+                                cur.wv, cur.ex, wb0[s0.wsel ^ 1] + v, facc);
+            u0 = u1;
+            cur = nxt;
+            cur_row = u0.kind == 1;
+            u1 = u2;
+            nxt = nx2;
+        }
+        if (failed) {
+            st.drain();
+            if (lane == 0) atomicCAS(&A.ctl->status, 0, (int)FFG_ERR_TIMEOUT);
+        } else if (st.issued) {
+            st.drain();
+        }
+        st.issued = false;
+        sweep_flush(sjd, acc_job, buf, facc, lane);
+        if (!sweep_barrier(A.ctl, unsigned(phase + 1) * unsigned(A.nb), &s_ok)) break;
+    }
+    // a failure: every unfinished job reports it
+    if (blockIdx.x == 0 && *(volatile int *)&A.ctl->status != 0)
+        for (int j = threadIdx.x; j < nj; j += blockDim.x)
+            if (sj[j].mode != kSwDone) atomicCAS(&sjd[j].ctl->status, 0, A.ctl->status);
 }
 
 // Layout kernels over every distinct graph of a batch: a global row or tile
@@ -1511,9 +2023,9 @@ struct RowsDev {
     void *w_out;            // w' of every row, shifted by row0
     void *ranks;            // shifted by row0
     unsigned long long *sums;
+    ffg_rows_ctl *ctl;      // the solve's state: dangling mass, scale, decisions
     int64_t n, n_all;       // rows of the range, of the graph
-    double alpha, scale;
-    unsigned long long dangling;
+    double alpha;
 };
 
 template <int W>
@@ -1541,7 +2053,7 @@ __global__ void __launch_bounds__(256) k_rows_init(const RowsDev R) {
         const double x0 = x ? static_cast<double>(x[v]) : inv_n;
         const int32_t od = __ldg(R.outdeg + v);
         wo[v] = Rows<T>::init(x0, od);
-        R.rinv[v] = od ? 1.0 / od : 1.0;
+        Rows<T>::store_rinv(R.rinv, v, od);
         if (od == 0) f.d += to_fix(x0);
     }
     add_sums<8>(R, f);
@@ -1564,7 +2076,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_rows_step(const RowsDev R) {
     const int ni = static_cast<int>(R.n);
     const int64_t ntiles = (R.apre[R.n] - R.apre[0] + 31) >> 5;
     const Rr a = static_cast<Rr>(R.alpha);
-    const Rr c = static_cast<Rr>(teleport(R.alpha, R.dangling, R.n_all));
+    const Rr c = static_cast<Rr>(teleport(R.alpha, R.ctl->dangling, R.n_all));
     Fix3 f;
     bool failed = false;
     if (gw < ntiles) {
@@ -1615,10 +2127,48 @@ __global__ void __launch_bounds__(256) k_rows_finish(const RowsDev R) {
     for (int64_t v = int64_t(blockIdx.x) * 256 + threadIdx.x; v < R.n;
          v += int64_t(gridDim.x) * 256) {
         const int32_t od = __ldg(R.outdeg + v);
-        if (x) x[v] = static_cast<Rr>(Rows<T>::x_of(wc[v], od) * R.scale);
+        if (x) x[v] = static_cast<Rr>(Rows<T>::x_of(wc[v], od) * R.ctl->scale);
         else f.s += Rows<T>::fix_x(wc[v], od);
     }
     if (!x) add_sums<8>(R, f);
+}
+
+// The solve's control between operations (one thread): the stopping rule
+// and the normalisation of pagerank_solve (advance() and the epilogue of
+// run_job), taken from the fixed-point sums of every rank; the sums used are
+// cleared for the next operation.
+__global__ void k_rows_ctl(ffg_rows_ctl *ctl, unsigned long long *sums, int op, double tol,
+                           int max_iter, int fp32) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (op == FFG_ROWS_INIT) {
+        ctl->iters = ctl->stop = ctl->converged = ctl->status = 0;
+        ctl->residual = ctl->prev_residual = __longlong_as_double(0x7ff0000000000000LL);
+        ctl->scale = 1.0;
+        ctl->dangling = 0;
+        return;
+    }
+    if (op == FFG_ROWS_START) {
+        ctl->dangling = sums[1];
+    } else if (op == FFG_ROWS_ADVANCE) {
+        const double r = static_cast<double>(sums[0]) / kFix;
+        ctl->prev_residual = ctl->residual;
+        ctl->residual = r;
+        ctl->dangling = sums[1];
+        ++ctl->iters;
+        if (sums[3]) {
+            ctl->status = FFG_ERR_TIMEOUT;
+            ctl->stop = 1;
+        } else if (r < tol) {
+            ctl->converged = ctl->stop = 1;
+        } else if (fp32 && r >= ctl->prev_residual) {
+            ctl->converged = ctl->stop = 1;
+        } else if (ctl->iters >= max_iter) {
+            ctl->stop = 1;
+        }
+    } else {  // FFG_ROWS_SCALE
+        ctl->scale = 1.0 / (static_cast<double>(sums[2]) / kFix);
+    }
+    sums[0] = sums[1] = sums[2] = sums[3] = 0;
 }
 
 ffg_status rows_check(const ffg_graph *g, int64_t row0, int64_t row1, ffg_prec prec) {
@@ -1740,16 +2290,21 @@ extern "C" ffg_status pagerank_rows_run(const ffg_graph *g, int64_t row0, int64_
     clear_error();
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     FFG_TRY(rows_check(g, row0, row1, prec));
-    if (!op || op->op < FFG_ROWS_INIT || op->op > FFG_ROWS_WRITE || !op->sums)
-        return set_error("op: unknown operation or sums NULL"), FFG_ERR_INVALID_ARG;
+    if (!op || op->op < FFG_ROWS_INIT || op->op > FFG_ROWS_SCALE || !op->sums || !op->ctl)
+        return set_error("op: unknown operation, or sums or ctl NULL"), FFG_ERR_INVALID_ARG;
     if (!workspace || !aligned256(workspace))
         return set_error("workspace NULL or not 256-byte aligned"), FFG_ERR_INVALID_ARG;
     const int k = op->op;
-    if ((k != FFG_ROWS_INIT && !op->w_in) || ((k == FFG_ROWS_INIT || k == FFG_ROWS_STEP) && !op->w_out) ||
-        (k == FFG_ROWS_WRITE && !op->ranks))
-        return set_error("op %d: w_in, w_out or ranks missing", k), FFG_ERR_INVALID_ARG;
+    if ((k == FFG_ROWS_STEP || k == FFG_ROWS_SUM || k == FFG_ROWS_WRITE) && !op->w_in)
+        return set_error("op %d: w_in missing", k), FFG_ERR_INVALID_ARG;
+    if ((k == FFG_ROWS_INIT || k == FFG_ROWS_STEP) && !op->w_out)
+        return set_error("op %d: w_out missing", k), FFG_ERR_INVALID_ARG;
+    if (k == FFG_ROWS_WRITE && !op->ranks)
+        return set_error("op %d: ranks missing", k), FFG_ERR_INVALID_ARG;
     if (k == FFG_ROWS_STEP && !(op->damping > 0.0 && op->damping < 1.0))
         return set_error("damping must lie in (0, 1)"), FFG_ERR_INVALID_ARG;
+    if (k == FFG_ROWS_ADVANCE && (!(op->tol >= 0.0) || op->max_iter < 1))
+        return set_error("tol must be >= 0 and max_iter >= 1"), FFG_ERR_INVALID_ARG;
     // the tables' places depend on the rows only (the descriptors come
     // last), so an iteration needs no device read; the full size was checked
     // by pagerank_rows_prepare
@@ -1757,6 +2312,18 @@ extern "C" ffg_status pagerank_rows_run(const ffg_graph *g, int64_t row0, int64_
     if (ws_bytes < carve_rows(nullptr, n, 0).bytes)
         return set_error("workspace smaller than any range of %lld rows", (long long)n),
                FFG_ERR_NO_MEMORY;
+    unsigned long long *sums = reinterpret_cast<unsigned long long *>(op->sums);
+    if (k == FFG_ROWS_START || k == FFG_ROWS_ADVANCE || k == FFG_ROWS_SCALE) {
+        k_rows_ctl<<<1, 32, 0, stream>>>(op->ctl, sums, k, op->tol, op->max_iter,
+                                         prec == FFG_F32 ? 1 : 0);
+        count_launch();
+        return check_launch("k_rows_ctl");
+    }
+    if (k == FFG_ROWS_INIT) {
+        k_rows_ctl<<<1, 32, 0, stream>>>(op->ctl, sums, k, 0.0, 1, 0);
+        count_launch();
+        FFG_TRY(check_launch("k_rows_ctl"));
+    }
     const RowsWs w = carve_rows(workspace, n, 0);
     const size_t wb = pagerank_rows_w_bytes(prec);
     RowsDev R;
@@ -1765,9 +2332,8 @@ extern "C" ffg_status pagerank_rows_run(const ffg_graph *g, int64_t row0, int64_
     R.n = n;
     R.n_all = g->n_nodes;
     R.alpha = op->damping;
-    R.scale = op->scale;
-    R.dangling = op->dangling;
-    R.sums = reinterpret_cast<unsigned long long *>(op->sums);
+    R.ctl = op->ctl;
+    R.sums = sums;
     R.w_in = op->w_in ? static_cast<const char *>(op->w_in) + size_t(row0) * wb : nullptr;
     R.w_out = op->w_out ? static_cast<char *>(op->w_out) + size_t(row0) * wb : nullptr;
     const size_t rb = prec == FFG_F32 ? sizeof(float) : sizeof(double);
@@ -1861,6 +2427,13 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, int warps,
     if (tu.max_blocks > 0 && tu.max_blocks < cap) cap = tu.max_blocks;
     const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(cap, useful)));
     P.nb = nb;
+    if (P.claim == 2) {  // sweep: every block on every job, phase by phase
+        P.nb = cap;
+        P.group.assign(n_jobs, 1);
+        P.items.clear();
+        P.first.clear();
+        return FFG_OK;
+    }
     const double total = std::accumulate(cost.begin(), cost.end(), 0.0);
     const double share = total / nb;
     std::vector<int> order(n_jobs);
@@ -1941,6 +2514,9 @@ struct BatchWs {
     int *first;
     int2 *items;
     PrCtl *ctl;
+    SweepCtl *sweep_ctl;        // sweep schedule: grid barrier and failure flag
+    SweepRange *sweep_ranges;   // ... each block's share of a phase, by parity
+    int *sweep_ctr;             // ... units claimed from each share, by parity
     int32_t *cnt;    // per tile of every graph
     uint2 *tinfo;    // per tile of every graph
     int64_t *tpre;   // its prefix sums
@@ -1967,6 +2543,9 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, ffg_prec pre
     w.first = c.take<int>(size_t(cap) + 1);
     w.items = c.take<int2>(size_t(n_jobs) * cap);
     w.ctl = c.take<PrCtl>(n_jobs);
+    w.sweep_ctl = c.take<SweepCtl>(1);
+    w.sweep_ranges = c.take<SweepRange>(size_t(2) * cap);
+    w.sweep_ctr = c.take<int>(size_t(2) * cap);
     int64_t total_tiles = 0;
     for (const ffg_graph *g : P.graphs) total_tiles += (g->n_nodes + 31) / 32;
     // per-tile descriptor counts of all graphs in one array, scanned at once
@@ -2013,7 +2592,9 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, ffg_prec pre
         J.ranks = jobs[j].ranks;
         J.w0 = c.take<char>(size_t(g->n_nodes) * w_bytes(prec));
         J.w1 = c.take<char>(size_t(g->n_nodes) * w_bytes(prec));
-        J.rinv = prec == FFG_F64 ? c.take<double>(size_t(g->n_nodes)) : nullptr;
+        J.rinv = prec == FFG_F64
+                     ? c.take<double>(size_t(g->n_nodes))
+                     : reinterpret_cast<double *>(c.take<float>(size_t(g->n_nodes)));
         J.ctl = w.ctl + j;
         J.n = g->n_nodes;
         J.alpha = jobs[j].damping;
@@ -2141,10 +2722,13 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
                       : n_jobs <= kParamJobs ? kWarpsSingle
                                              : kWarpsBatchWide;
     if (!(tu.split > 0.0) || !(tu.grain > 0.0) || tu.max_blocks < 0 || !batch_width_ok(warps) ||
-        (tu.claim != 0 && tu.claim != 1) || tu.fp64_form < 0 || tu.fp64_form > 2)
+        tu.claim < 0 || tu.claim > 2 || (tu.claim == 2 && warps == kWarpsBatch) ||
+        tu.fp64_form < 0 || tu.fp64_form > 2)
         return set_error("tuning: split and grain must be > 0, max_blocks >= 0, block_warps "
-                         "0, %d, %d or %d, claim 0 or 1, fp64_form 0, 1 or 2",
-                         kWarpsBatch, kWarpsBatchWide, kWarpsSingle),
+                         "0, %d, %d or %d, claim 0, 1 or 2 (2 with %d or %d warps), fp64_form "
+                         "0, 1 or 2",
+                         kWarpsBatch, kWarpsBatchWide, kWarpsSingle, kWarpsBatchWide,
+                         kWarpsSingle),
                FFG_ERR_INVALID_ARG;
     if (tu.job_cost)
         for (int j = 0; j < n_jobs; ++j)
@@ -2154,6 +2738,17 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     int cap = 0, nb_max = 0;
     FFG_TRY(batch_cap(prec, &cap));
     FFG_TRY(batch_blocks(prec, warps, &nb_max));
+    if (tu.claim == 2) {  // the sweep keeps every job's state in shared memory
+        int dev = 0, optin = 0;
+        FFG_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
+        FFG_TRY(check_cuda(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                                  dev), "attr"));
+        const size_t need = warps == kWarpsBatchWide ? sweep_smem_bytes<kWarpsBatchWide>(n_jobs)
+                                                     : sweep_smem_bytes<kWarpsSingle>(n_jobs);
+        if (need > size_t(optin))
+            return set_error("tuning: %d jobs are too many for the sweep order", n_jobs),
+                   FFG_ERR_INVALID_ARG;
+    }
     PlanHost P;
     FFG_TRY(make_plan(jobs, n_jobs, nb_max, warps, tu, P));
     std::vector<JobDev> jd;
@@ -2203,28 +2798,36 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
     plan->tables[3] = w.aflag;
     plan->tables[4] = w.apre;
     plan->tables[5] = w.ascan;
+    plan->tables[6] = w.sweep_ctl;
+    plan->tables[7] = w.sweep_ranges;
+    plan->tables[8] = w.sweep_ctr;
     plan->param_jobs = n_jobs <= kParamJobs ? n_jobs : 0;
     memset(plan->params, 0, sizeof(plan->params));
     if (plan->param_jobs) memcpy(plan->params, jd.data(), sizeof(JobDev) * jd.size());
     return FFG_OK;
 }
 
-extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_) {
-    clear_error();
-    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+namespace ffg {
+namespace {
+
+ffg_status batch_check(const ffg_pr_batch *plan) {
     if (!plan || plan->n_jobs < 1 || !plan->jobs || !plan->ctl || plan->n_blocks < 1)
         return set_error("plan is empty"), FFG_ERR_INVALID_ARG;
-    const ffg_prec prec = static_cast<ffg_prec>(plan->prec);
     if (!batch_width_ok(plan->warps))
         return set_error("plan has %d warps per block", plan->warps), FFG_ERR_INVALID_ARG;
     int nb_max = 0;
-    FFG_TRY(batch_blocks(prec, plan->warps, &nb_max));
+    FFG_TRY(batch_blocks(static_cast<ffg_prec>(plan->prec), plan->warps, &nb_max));
     if (plan->n_blocks > nb_max)
         return set_error("plan made for %d blocks, %d fit", plan->n_blocks, nb_max),
                FFG_ERR_INVALID_ARG;
-    FFG_TRY(check_cuda(cudaMemsetAsync(plan->ctl, 0, sizeof(PrCtl) * plan->n_jobs, stream),
-                       "memset"));
-    FFG_TRY(check_cuda(cudaMemsetAsync(plan->queue, 0, sizeof(int), stream), "memset"));
+    if (plan->param_jobs > 0 &&
+        (plan->param_jobs != plan->n_jobs || plan->param_jobs > kParamJobs))
+        return set_error("plan's parameter table does not match its jobs"), FFG_ERR_INVALID_ARG;
+    return FFG_OK;
+}
+
+// slots, descriptors and tile costs of every distinct graph of the plan
+ffg_status batch_layout(const ffg_pr_batch *plan, cudaStream_t stream) {
     int sms = 0;
     FFG_TRY(device_sms(&sms));
     const GraphDev *gr = static_cast<const GraphDev *>(plan->graphs);
@@ -2242,9 +2845,65 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
                         stream>>>(gr, plan->n_graphs, plan->total_tiles);
     count_launch();
     FFG_TRY(check_launch("k_pr_layout_batch"));
-    FFG_TRY(scan_exclusive(static_cast<const int32_t *>(plan->tables[0]),
-                           static_cast<int64_t *>(plan->tables[1]), plan->total_tiles,
-                           static_cast<int64_t *>(plan->tables[2]), stream));
+    return scan_exclusive(static_cast<const int32_t *>(plan->tables[0]),
+                          static_cast<int64_t *>(plan->tables[1]), plan->total_tiles,
+                          static_cast<int64_t *>(plan->tables[2]), stream);
+}
+
+// the sweep kernel for the plan's precision and storage form of w
+template <typename T, int W>
+ffg_status launch_sweep_t(const SweepArgs &A, cudaStream_t stream) {
+    const size_t smem = sweep_smem_bytes<W>(A.n_jobs);
+    const void *kern = (const void *)k_pagerank_sweep<T, W>;
+    FFG_TRY(check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(smem)),
+                       "smem attribute"));
+    int per_sm = 0;
+    FFG_TRY(check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * W, smem),
+                       "occupancy"));
+    int sms = 0;
+    FFG_TRY(device_sms(&sms));
+    if (per_sm < 1 || A.nb > sms * per_sm)
+        return set_error("sweep plan of %d blocks does not fit (%d per SM)", A.nb, per_sm),
+               FFG_ERR_INVALID_ARG;
+    SweepArgs a = A;
+    void *args[] = {(void *)&a};
+    FFG_TRY(check_cuda(cudaLaunchCooperativeKernel(kern, dim3(A.nb), dim3(32 * W), args, smem,
+                                                   stream),
+                       "k_pagerank_sweep"));
+    count_launch();
+    return FFG_OK;
+}
+
+template <int W>
+ffg_status launch_sweep(ffg_prec prec, bool fx, const SweepArgs &A, cudaStream_t stream) {
+    if (prec == FFG_F32) return launch_sweep_t<float, W>(A, stream);
+    if (fx) return launch_sweep_t<F64x, W>(A, stream);
+    return launch_sweep_t<double, W>(A, stream);
+}
+
+// the persistent launch over every job
+ffg_status batch_solve(const ffg_pr_batch *plan, cudaStream_t stream) {
+    const ffg_prec prec = static_cast<ffg_prec>(plan->prec);
+    FFG_TRY(check_cuda(cudaMemsetAsync(plan->ctl, 0, sizeof(PrCtl) * plan->n_jobs, stream),
+                       "memset"));
+    if (plan->claim == 2) {
+        SweepArgs A;
+        A.jobs = static_cast<const JobDev *>(plan->jobs);
+        A.ctl = static_cast<SweepCtl *>(plan->tables[6]);
+        A.ranges = static_cast<SweepRange *>(plan->tables[7]);
+        A.ctr = static_cast<int *>(plan->tables[8]);
+        A.n_jobs = plan->n_jobs;
+        A.nb = plan->n_blocks;
+        FFG_TRY(check_cuda(cudaMemsetAsync(A.ctl, 0, sizeof(SweepCtl), stream), "memset"));
+        FFG_TRY(check_cuda(cudaMemsetAsync(A.ranges, 0xff, sizeof(SweepRange) * 2 * A.nb, stream),
+                           "memset"));
+        FFG_TRY(check_cuda(cudaMemsetAsync(A.ctr, 0, sizeof(int) * 2 * A.nb, stream), "memset"));
+        const bool fx = plan->w_form != 0;
+        if (plan->warps == kWarpsBatchWide) return launch_sweep<kWarpsBatchWide>(prec, fx, A, stream);
+        return launch_sweep<kWarpsSingle>(prec, fx, A, stream);
+    }
+    FFG_TRY(check_cuda(cudaMemsetAsync(plan->queue, 0, sizeof(int), stream), "memset"));
     const JobDev *jobs = static_cast<const JobDev *>(plan->jobs);
     const int2 *items = static_cast<const int2 *>(plan->items);
     const int *first = static_cast<const int *>(plan->first);
@@ -2254,9 +2913,6 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
     // batches of at most kParamJobs jobs pass their job table as parameters
     std::unique_ptr<BatchParams> params;
     if (plan->param_jobs > 0) {
-        if (plan->param_jobs != plan->n_jobs || plan->param_jobs > kParamJobs)
-            return set_error("plan's parameter table does not match its jobs"),
-                   FFG_ERR_INVALID_ARG;
         params.reset(new BatchParams());
         params->items = items;
         params->first = first;
@@ -2271,6 +2927,29 @@ extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_
         return launch_batch<kWarpsBatchWide>(prec, fx, P, jobs, items, first, queue, ni, nb,
                                              stream);
     return launch_batch<kWarpsSingle>(prec, fx, P, jobs, items, first, queue, ni, nb, stream);
+}
+
+}  // namespace
+}  // namespace ffg
+
+extern "C" ffg_status pagerank_batch_run(const ffg_pr_batch *plan, void *stream_) {
+    clear_error();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    FFG_TRY(batch_check(plan));
+    FFG_TRY(batch_layout(plan, stream));
+    return batch_solve(plan, stream);
+}
+
+extern "C" ffg_status pagerank_batch_prepare(const ffg_pr_batch *plan, void *stream_) {
+    clear_error();
+    FFG_TRY(batch_check(plan));
+    return batch_layout(plan, static_cast<cudaStream_t>(stream_));
+}
+
+extern "C" ffg_status pagerank_batch_solve(const ffg_pr_batch *plan, void *stream_) {
+    clear_error();
+    FFG_TRY(batch_check(plan));
+    return batch_solve(plan, static_cast<cudaStream_t>(stream_));
 }
 
 extern "C" ffg_status pagerank_batch_query(const ffg_pr_batch *plan, int32_t *iters_out,

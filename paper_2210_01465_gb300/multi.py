@@ -62,12 +62,15 @@ def split_rows(in_ptr, parts: int, row_cost: int = 20):
 class RowExchange:
     """The exchange of a row-partitioned solve between processes: rank r owns
     ``bounds[r]``; ``gather`` all-gathers every rank's rows of w (bytes,
-    ``elem`` per row) into the full vector, ``reduce`` adds the ranks' sums."""
+    ``elem`` per row) into the full vector, ``reduce`` adds the ranks' sums.
+    With ``host=True`` (a process group whose backend takes CPU tensors, such
+    as gloo) both go through host memory."""
 
-    def __init__(self, bounds, elem: int, group=None):
+    def __init__(self, bounds, elem: int, group=None, host: bool = False):
         self.bounds = [(int(a), int(b)) for a, b in bounds]
         self.elem = int(elem)
         self.group = group
+        self.host = bool(host)
         self.longest = max(b - a for a, b in self.bounds) * self.elem
 
     def gather(self, w):
@@ -76,16 +79,23 @@ class RowExchange:
         rank = dist.get_rank(self.group)
         e, L = self.elem, self.longest
         a, b = self.bounds[rank]
-        send = torch.zeros(L, dtype=torch.uint8, device=w.device)
-        send[:(b - a) * e] = w[a * e:b * e]
-        parts = [torch.empty(L, dtype=torch.uint8, device=w.device) for _ in self.bounds]
-        dist.all_gather(parts, send, group=self.group)
-        for (a, b), p in zip(self.bounds, parts):
-            w[a * e:b * e] = p[:(b - a) * e]
+        dev = torch.device("cpu") if self.host else w.device
+        send = torch.zeros(L, dtype=torch.uint8, device=dev)
+        send[:(b - a) * e] = w[a * e:b * e].to(dev)
+        recv = torch.empty(len(self.bounds) * L, dtype=torch.uint8, device=dev)
+        dist.all_gather(list(recv.split(L)), send, group=self.group)
+        for r, (a, b) in enumerate(self.bounds):
+            if r != rank:
+                w[a * e:b * e].copy_(recv[r * L:r * L + (b - a) * e])
 
     def reduce(self, sums):
         import torch.distributed as dist
-        dist.all_reduce(sums, group=self.group)
+        if self.host:
+            h = sums.cpu()
+            dist.all_reduce(h, group=self.group)
+            sums.copy_(h)
+        else:
+            dist.all_reduce(sums, group=self.group)
 
     def __call__(self, w, sums):
         self.gather(w)
@@ -108,13 +118,14 @@ class RowRange:
                                              need, ffg._stream_handle(stream)),
                    "pagerank_rows_prepare")
 
-    def run(self, kind: int, sums, w_in=None, w_out=None, ranks=None, damping: float = 0.0,
-            dangling: int = 0, scale: float = 1.0, stream=None):
+    def run(self, kind: int, sums, ctl, w_in=None, w_out=None, ranks=None, damping: float = 0.0,
+            tol: float = 0.0, max_iter: int = 1, stream=None):
         import paper_2210_01465_gb300 as ffg
-        op = ffg.ffg_rows_op(int(kind), 0, float(damping), int(dangling), float(scale),
+        op = ffg.ffg_rows_op(int(kind), int(max_iter), float(damping), float(tol),
                              None if w_in is None else w_in.data_ptr(),
                              None if w_out is None else w_out.data_ptr(),
-                             None if ranks is None else ranks.data_ptr(), sums.data_ptr())
+                             None if ranks is None else ranks.data_ptr(), sums.data_ptr(),
+                             ctl.data_ptr())
         ffg._check(ffg.pagerank_rows_run(self.g.c, self.row0, self.row1, self.prec, op,
                                          self.ws.data_ptr(), self.need,
                                          ffg._stream_handle(stream)),
@@ -124,13 +135,18 @@ class RowRange:
 def solve_rows(g, ranges, damping: float = 0.85, tol: float = 1e-12, max_iter: int = 10000,
                prec=None, exchange=None, init=None, stream=None):
     """Row-partitioned PageRank of ``g``: this process works on ``ranges``
-    ((row0, row1) pairs, or RowRange objects laid out before).  Several ranges in one process stand for several
-    ranks (their rows of w land in the same buffers, nothing to exchange);
-    between processes ``exchange`` (a RowExchange) all-gathers w and adds
-    the sums, and the ranges of all ranks must cover every row.  The stopping
-    rule and the normalisation are pagerank_solve's, so FP64 results equal
-    its bit for bit.  Returns (ranks, iterations, residual, converged); the
-    ranks hold every row after an exchange, else this process's rows."""
+    ((row0, row1) pairs, or RowRange objects laid out before).  Several
+    ranges in one process stand for several ranks (their rows of w land in
+    the same buffers, nothing to exchange); between processes ``exchange``
+    (a RowExchange) all-gathers w and adds the sums, and the ranges of all
+    ranks must cover every row.  Every decision -- the stopping rule, the
+    teleport term, the normalisation -- is taken on the device from the
+    summed fixed-point values (pagerank_rows_run's control operations), with
+    pagerank_solve's arithmetic, so FP64 results equal its bit for bit; this
+    function only moves bytes and reads the stop flag once per iteration.
+    Returns (ranks, iterations, residual, converged); the ranks hold every
+    row after an exchange, else this process's rows."""
+    import numpy as np
     import torch
     import paper_2210_01465_gb300 as ffg
     prec = ffg.F64 if prec is None else prec
@@ -142,45 +158,45 @@ def solve_rows(g, ranges, damping: float = 0.85, tol: float = 1e-12, max_iter: i
     w_cur = torch.zeros(n * wb, dtype=torch.uint8, device=dev)
     w_next = torch.zeros(n * wb, dtype=torch.uint8, device=dev)
     sums = torch.zeros(4, dtype=torch.int64, device=dev)
+    ctl = torch.zeros(ffg.ROWS_CTL_BYTES, dtype=torch.uint8, device=dev)
     dt = torch.float64 if prec == ffg.F64 else torch.float32
     ranks = torch.zeros(n, dtype=dt, device=dev)
+    head = parts[0]   # the control operations run once per process
 
-    def settle(w):
-        if exchange is not None:
-            exchange(w, sums)
-        s = [int(v) for v in sums.cpu()]
-        if s[3]:
-            raise ffg.FFGError(ffg.FFG_ERR_TIMEOUT, "pagerank_rows_run")
-        return s
+    def flags():
+        c = ctl[:16].cpu().numpy().view(np.int32)   # iters, stop, converged, status
+        if c[3]:
+            raise ffg.FFGError(int(c[3]), "pagerank_rows_run")
+        return c
 
     for p in parts:
-        p.run(ffg.ROWS_INIT, sums, w_out=w_cur, ranks=init, stream=stream)
-    dangling = settle(w_cur)[1]
-    it, res, converged = 0, float("inf"), False
+        p.run(ffg.ROWS_INIT, sums, ctl, w_out=w_cur, ranks=init, stream=stream)
+    if exchange is not None:
+        exchange(w_cur, sums)
+    head.run(ffg.ROWS_START, sums, ctl, stream=stream)
     while True:
-        sums.zero_()
         for p in parts:
-            p.run(ffg.ROWS_STEP, sums, w_in=w_cur, w_out=w_next, damping=damping,
-                  dangling=dangling, stream=stream)
-        s = settle(w_next)
-        prev, res, dangling = res, s[0] / FIX, s[1]
-        it += 1
+            p.run(ffg.ROWS_STEP, sums, ctl, w_in=w_cur, w_out=w_next, damping=damping,
+                  stream=stream)
+        if exchange is not None:
+            exchange(w_next, sums)
+        head.run(ffg.ROWS_ADVANCE, sums, ctl, tol=tol, max_iter=max_iter, stream=stream)
         w_cur, w_next = w_next, w_cur
-        if res < tol or (prec == ffg.F32 and res >= prev):
-            converged = True
+        if flags()[1]:
             break
-        if it >= max_iter:
-            break
-    sums.zero_()
     for p in parts:
-        p.run(ffg.ROWS_SUM, sums, w_in=w_cur, stream=stream)
+        p.run(ffg.ROWS_SUM, sums, ctl, w_in=w_cur, stream=stream)
     if exchange is not None:
         exchange.reduce(sums)
-    xs = int(sums.cpu()[2]) / FIX
+    head.run(ffg.ROWS_SCALE, sums, ctl, stream=stream)
     for p in parts:
-        p.run(ffg.ROWS_WRITE, sums, w_in=w_cur, ranks=ranks, scale=1.0 / xs, stream=stream)
+        p.run(ffg.ROWS_WRITE, sums, ctl, w_in=w_cur, ranks=ranks, stream=stream)
     if exchange is not None:
         # every row's ranks on every rank: gather them like w
         raw = ranks.view(torch.uint8)
-        RowExchange(exchange.bounds, ranks.element_size(), exchange.group).gather(raw)
-    return ranks, it, res, converged
+        RowExchange(exchange.bounds, ranks.element_size(), exchange.group,
+                    exchange.host).gather(raw)
+    c = ctl.cpu().numpy()
+    it, _, conv, _ = c[:16].view(np.int32)
+    res = float(c[16:24].view(np.float64)[0])
+    return ranks, int(it), res, bool(conv)

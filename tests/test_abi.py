@@ -157,13 +157,20 @@ def test_rows_validated_on_host(lib):
         assert "rows" in ffg.ffg_last_error()
     before = lib.ffg_launch_count()
     sums = np.zeros(4, dtype=np.uint64)
-    op = ffg.ffg_rows_op(ffg.ROWS_STEP, 0, 1.0, 0, 1.0, 256, 256, None, sums.ctypes.data)
+    ctl = np.zeros(ffg.ROWS_CTL_BYTES, dtype=np.uint8)
+    op = ffg.ffg_rows_op(ffg.ROWS_STEP, 1, 1.0, 0.0, 256, 256, None, sums.ctypes.data,
+                         ctl.ctypes.data)
     assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 256, 1 << 20) == ffg.FFG_ERR_INVALID_ARG
     assert "damping" in ffg.ffg_last_error()
     op.op = 9
     assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 256, 1 << 20) == ffg.FFG_ERR_INVALID_ARG
     op.op = ffg.ROWS_WRITE
     assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 256, 1 << 20) == ffg.FFG_ERR_INVALID_ARG
+    op.op, op.max_iter = ffg.ROWS_ADVANCE, 0           # the stopping rule needs max_iter >= 1
+    assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 256, 1 << 20) == ffg.FFG_ERR_INVALID_ARG
+    op.op, op.ctl = ffg.ROWS_START, None               # every operation needs the control record
+    assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 256, 1 << 20) == ffg.FFG_ERR_INVALID_ARG
+    op.ctl = ctl.ctypes.data
     op.op, op.damping = ffg.ROWS_STEP, 0.85
     assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 258, 1 << 20) == ffg.FFG_ERR_INVALID_ARG
     assert ffg.pagerank_rows_run(g, 0, 50, ffg.F32, op, 256, 64) == ffg.FFG_ERR_NO_MEMORY
@@ -188,8 +195,20 @@ def test_batch_run_validated_on_host(lib):
     cp = np.zeros(4)
     out = ffg.ffg_batch_out()
     out.cp = cp.ctypes.data
-    assert ffg.ffg_batch_run(desc, out) == ffg.FFG_ERR_INVALID_ARG      # C_p without jobs
-    assert "cp_jobs" in ffg.ffg_last_error()
+    assert ffg.ffg_batch_run(desc, out) == ffg.FFG_ERR_INVALID_ARG      # C_p without a plan
+    assert "C_p plan" in ffg.ffg_last_error()
+    cplan = ffg.ffg_cp_batch()
+    desc.cp = C.pointer(cplan)
+    assert ffg.ffg_batch_run(desc, out) == ffg.FFG_ERR_INVALID_ARG      # empty C_p plan
+    assert ffg.centrality_batch_run(cplan) == ffg.FFG_ERR_INVALID_ARG
+    assert ffg.centrality_batch_query(cplan)[0] == ffg.FFG_ERR_INVALID_ARG
+    jobs = (ffg.ffg_cp_job * 2)()
+    assert ffg.centrality_batch_plan(jobs, ffg.F32, [0.05], 256, 1 << 20, cplan) == \
+        ffg.FFG_ERR_INVALID_ARG                                          # jobs without graphs
+    assert ffg.centrality_batch_plan(jobs, ffg.F32, [-0.05], 256, 1 << 20, cplan) == \
+        ffg.FFG_ERR_INVALID_ARG
+    assert ffg.centrality_batch_plan(jobs, ffg.F32, [0.05] * 33, 256, 1 << 20, cplan) == \
+        ffg.FFG_ERR_INVALID_ARG
     assert lib.ffg_launch_count() == before
 
 

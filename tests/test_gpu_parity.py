@@ -401,7 +401,8 @@ def test_batch_tuning_changes_schedule_not_results():
     for tuning in ((1.0, 1.0, 0), (0.1, 0.1, 0), (5.0, 1.0, 3), (1.0, 1.0, 0, 8),
                    (0.1, 0.1, 0, 8), (0.1, 0.1, 0, 8, 1), (0.5, 0.5, 0, 24, 1),
                    (1.0, 1.0, 0, 16), (0.1, 0.02, 0, 16, 0), (0.5, 0.5, 0, 16, 1),
-                   (1.0, 1.0, 0, 8, 0, 2), (0.1, 0.02, 0, 24, 0, 2), (0.1, 0.02, 0, 16, 0, 2)):
+                   (1.0, 1.0, 0, 8, 0, 2), (0.1, 0.02, 0, 24, 0, 2), (0.1, 0.02, 0, 16, 0, 2),
+                   (1.0, 1.0, 0, 24, 2), (1.0, 1.0, 0, 16, 2), (1.0, 1.0, 0, 24, 2, 2)):
         batch.replan(tuning)
         batch.run()
         it, res, st = batch.query()
@@ -418,6 +419,39 @@ def test_batch_tuning_changes_schedule_not_results():
             np.testing.assert_array_equal(it, first[form][0])
             for x, x0 in zip(xs, first[form][1]):
                 np.testing.assert_array_equal(x, x0)
+
+
+def test_batch_sweep_order_fp32_bit_exact():
+    """The sweep order (every job one step per phase on the whole grid, units
+    taken across blocks) gives the FP32 bits of the per-block lists, on jobs
+    of very different sizes and dampings, and repeats them run after run."""
+    specs, refs = [], []
+    cases = [(fi.single_large(), 1, "adjacent"), (fi.gemm_space(), 2, "hamming"),
+             (fi.single_small(), 3, "hamming"), (fi.pnpoly_space(), 4, "adjacent")]
+    for spec, seed, nbh in cases:
+        f = fi.runtimes(spec, seed, fail_frac=0.7 if spec.name == "gemm" else 0.03)
+        og = oracle.build(spec, f, NBH[nbh][1])
+        g, _ = run_build(spec, f, nbh)
+        for alpha in (0.5, 0.85, 0.95):
+            specs.append((g, alpha))
+            refs.append((og, alpha))
+    batch = ffg.PageRankBatch(specs, prec=ffg.F32, tol=1e-12)
+    out = {}
+    for tuning in ((0.05, 0.005, 0, 24, 0), (1.0, 1.0, 0, 24, 2), (1.0, 1.0, 0, 16, 2)):
+        batch.replan(tuning)
+        for _ in range(2):
+            batch.run()
+            it, res, st = batch.query()
+            assert (st == 0).all()
+            xs = [_np(x) for x in batch.ranks]
+            if "ref" not in out:
+                out["ref"] = (it.copy(), res.copy(), xs)
+            np.testing.assert_array_equal(it, out["ref"][0])
+            np.testing.assert_array_equal(res, out["ref"][1])
+            for x, x0 in zip(xs, out["ref"][2]):
+                np.testing.assert_array_equal(x, x0)
+    for x, (og, alpha) in zip(out["ref"][2], refs):
+        assert np.abs(x.astype(np.float64) - oracle.pagerank_exact(og, alpha)).sum() <= 1e-5
 
 
 def test_batch_measured_costs_change_schedule_not_results():
@@ -479,7 +513,8 @@ def test_batch_job_table_forms_agree():
     big = ffg.PageRankBatch(jobs, prec=ffg.F32, tol=1e-12)
     small = ffg.PageRankBatch(jobs[:ffg.PARAM_JOBS], prec=ffg.F32, tol=1e-12)
     assert big.plan.param_jobs == 0 and small.plan.param_jobs == ffg.PARAM_JOBS
-    for tuning in ((1.0, 1.0, 0, 8, 0), (0.1, 0.02, 0, 24, 0), (0.5, 0.5, 0, 16, 1)):
+    for tuning in ((1.0, 1.0, 0, 8, 0), (0.1, 0.02, 0, 24, 0), (0.5, 0.5, 0, 16, 1),
+                   (1.0, 1.0, 0, 24, 2), (1.0, 1.0, 0, 16, 2)):
         out = []
         for b in (big, small):
             b.replan(tuning)
@@ -522,7 +557,8 @@ def test_batch_run_one_call_matches_separate_calls():
     bb = ffg.BuildBatch(specs)
     batch = ffg.PageRankBatch([(g, 0.85) for g in bb.graphs], prec=ffg.F64, tol=1e-12)
     cp_specs = [(g, fd, x) for g, (_, fd, _), x in zip(bb.graphs, specs, batch.ranks)]
-    sb = ffg.SpaceBatch(batch, builds=bb, cp_specs=cp_specs, p=p)
+    cpb = ffg.CentralityBatch(cp_specs, p)
+    sb = ffg.SpaceBatch(batch, builds=bb, cp=cpb)
     for g in bb.graphs:
         g.out_idx.fill_(-1)
         g.in_ptr.fill_(-1)
@@ -544,7 +580,7 @@ def test_batch_run_one_call_matches_separate_calls():
     for x, x0 in zip(batch.ranks, xs):
         np.testing.assert_array_equal(_np(x), x0)
     np.testing.assert_array_equal(ffg.centrality_many(cp_specs, p), out["cp"])
-    # launches only, captured and replayed
+    # launches only -- builds, solves and C_p -- captured and replayed
     cg = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
@@ -555,11 +591,22 @@ def test_batch_run_one_call_matches_separate_calls():
     for g, x in zip(bb.graphs, batch.ranks):
         g.in_idx.fill_(-1)
         x.fill_(0)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(cpb.query()[0], out["cp"])
+    # the plan's device results are overwritten (NaN bytes) before the replay
+    off = cpb.plan.cp - cpb.ws.data_ptr()
+    cpb.ws[off:off + 8 * cpb.plan.n_jobs * cpb.plan.n_p].fill_(0xff)
+    assert np.isnan(cpb.query()[0]).all()
     cg.replay()
     torch.cuda.synchronize()
     for g, x, x0, (og, _, _) in zip(bb.graphs, batch.ranks, xs, refs):
         assert_same_graph(g, og)
         np.testing.assert_array_equal(_np(x), x0)
+    cp_replay, sts = cpb.query()
+    assert (sts == 0).all()
+    np.testing.assert_array_equal(cp_replay, out["cp"])
+    for row, (_, _, cpe) in zip(cp_replay, refs):
+        assert np.abs(row - cpe).max() <= F64_CP
 
 
 def test_batched_build_matches_per_space_builds():
