@@ -178,7 +178,7 @@ typedef struct {
 typedef struct {
     int32_t n_jobs, reserved;
     int64_t total_raw, total_words, total_blocks, total_rows;
-    void *tables[16]; /* device pointers into the workspace (internal) */
+    void *tables[20]; /* device pointers into the workspace (internal) */
 } ffg_build_batch;
 
 size_t ffg_build_batch_workspace_bytes(const ffg_build_job *jobs, int32_t n_jobs);

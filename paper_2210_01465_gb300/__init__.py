@@ -93,7 +93,7 @@ class ffg_build_job(C.Structure):
 class ffg_build_batch(C.Structure):
     _fields_ = [("n_jobs", C.c_int32), ("reserved", C.c_int32), ("total_raw", C.c_int64),
                 ("total_words", C.c_int64), ("total_blocks", C.c_int64),
-                ("total_rows", C.c_int64), ("tables", C.c_void_p * 16)]
+                ("total_rows", C.c_int64), ("tables", C.c_void_p * 20)]
 
 
 class ffg_pr_tuning(C.Structure):

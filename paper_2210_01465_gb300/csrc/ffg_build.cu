@@ -4,16 +4,22 @@
 // One thread per raw point r, warps over 32 consecutive raw points:
 //   k_valid  decodes r into mixed-radix digits, evaluates the clauses and
 //            writes one 32-bit word of the validity bitmap per warp (ballot)
-//            and the point's key (fitness, +inf if failed, NaN if invalid:
-//            every comparison with NaN is false, so an invalid neighbour
-//            needs no separate check); also reduces the node count and f_opt
-//            (best non-failed fitness).
+//            and the point's key: the fitness (+inf if failed) as an
+//            order-preserving 64-bit integer, 0 if invalid, so that the
+//            enumerations compare integers -- a warp-wide FP64 compare
+//            occupies an SM's narrow FP64 units on this part -- and an
+//            invalid neighbour fails both comparisons without a separate
+//            test; also reduces the node count and f_opt (best non-failed
+//            fitness).
 //   scan     of the per-word popcounts gives the rank directory: the node id
 //            of a valid raw point is prefix[r/32] + popc(word & lanes below).
-//   k_count  enumerates the neighbours of every valid point -- Hamming: every
+//   k_nodes  records every valid point's node id and the node list (raw
+//            point of every node), so that the enumerations below run one
+//            thread per node: no lane idles on an invalid point.
+//   k_count  enumerates the neighbours of every node -- Hamming: every
 //            other value of one parameter (Eq. 2); adjacent: the list
 //            neighbours d-1 and d+1 -- and counts those with strictly lower
-//            (out) and higher (in) key; it also records each point's node id.
+//            (out) and higher (in) key.
 //   scans    of the degrees give out_ptr / in_ptr.
 //   k_emit   enumerates again in ascending raw order and writes node ids.
 //
@@ -23,9 +29,9 @@
 // (r_i - 1) * stride_i < stride_{i-1}.  Node ids are monotone in raw index,
 // so the lists come out sorted by node id.
 //
-// For a warp of 32 consecutive raw points, the candidates for one (i, j)
-// are 32 shifted consecutive raw points, so the key and node-id loads of the
-// enumeration are coalesced.  Digits come from divisions by the radices done
+// For a warp of 32 consecutive nodes, the candidates for one (i, j) are
+// shifted nearly consecutive raw points, so the key and node-id loads of the
+// enumeration are close to coalesced.  Digits come from divisions by the radices done
 // as one multiply-high each (Lemire, Kaser and Kurz 2019: for 32-bit n and
 // d >= 2, floor(n / d) = (n * ceil(2^64 / d)) >> 64).
 #include <vector>
@@ -48,8 +54,9 @@ struct BuildCtl {
 
 struct BuildWs {
     BuildCtl *ctl;
-    double *key;       // per raw point: fitness key, NaN if invalid
+    unsigned long long *key;  // per raw point: ordered fitness key, 0 if invalid
     int32_t *node_of;  // per valid raw point: node id
+    int32_t *nodes;    // per node: its raw point
     uint32_t *bitmap;
     int32_t *wcount;
     int64_t *wprefix;
@@ -64,8 +71,9 @@ BuildWs carve(void *base, int64_t R) {
     Carver c(base);
     BuildWs w;
     w.ctl = c.take<BuildCtl>(1);
-    w.key = c.take<double>(R);
+    w.key = c.take<unsigned long long>(R);
     w.node_of = c.take<int32_t>(R);
+    w.nodes = c.take<int32_t>(R);
     w.bitmap = c.take<uint32_t>(W);
     w.wcount = c.take<int32_t>(W);
     w.wprefix = c.take<int64_t>(W + 1);
@@ -91,7 +99,20 @@ __device__ __forceinline__ uint32_t div_radix(const SmemSpace &s, int i, uint32_
     return s.radix[i] == 1 ? n : static_cast<uint32_t>(__umul64hi(n, s.magic[i]));
 }
 
-__device__ __forceinline__ double invalid_key() { return __longlong_as_double(0x7ff8000000000000LL); }
+// Keys: fit_key (failed points +inf) mapped by ordered_bits, which is
+// monotone and never 0 for a non-NaN double, so 0 marks an invalid point;
+// -0 is first made +0 (the two compare equal).  For valid keys a and b,
+// a < b as integers iff a < b as doubles; with the 0 of an invalid point,
+// (a - 1 < b - 1) and (a > b) are both false.
+constexpr unsigned long long kInvalidKey = 0ULL;
+constexpr unsigned long long kFailedKey = 0xfff0000000000000ULL;  // ordered_bits(+inf)
+__device__ __forceinline__ unsigned long long key_of(double f, double fail_thr) {
+    const double k = fit_key(f, fail_thr);
+    return ordered_bits(k == 0.0 ? 0.0 : k);
+}
+__device__ __forceinline__ bool key_below(unsigned long long a, unsigned long long b) {
+    return a - 1ULL < b - 1ULL;  // a < b, false when a is invalid
+}
 
 __device__ __forceinline__ void stage_space(const DevSpace &sp, SmemSpace &s, int64_t *vals,
                                             bool with_values) {
@@ -173,7 +194,8 @@ __device__ __forceinline__ int64_t mask_product(const SmemSpace &s, const int64_
 __device__ __forceinline__ void valid_body(const SmemSpace &s, const int64_t *vals, int64_t R,
                                            int64_t r, const double *__restrict__ fit,
                                            double fail_thr, uint32_t *__restrict__ bitmap,
-                                           int32_t *__restrict__ wcount, double *__restrict__ key,
+                                           int32_t *__restrict__ wcount,
+                                           unsigned long long *__restrict__ key,
                                            BuildCtl *ctl) {
     const int64_t W = (R + 31) >> 5;
     bool ok = false;
@@ -200,11 +222,11 @@ __device__ __forceinline__ void valid_body(const SmemSpace &s, const int64_t *va
             }
             ok = ok && h;
         }
-        double k = invalid_key();
+        unsigned long long k = kInvalidKey;
         if (ok) {
             const double f = fit[r];
             if (f < fail_thr) fbits = ordered_bits(f);
-            k = fit_key(f, fail_thr);
+            k = key_of(f, fail_thr);
         }
         key[r] = k;
     }
@@ -225,7 +247,8 @@ __global__ void __launch_bounds__(kThreads) k_valid(const DevSpace sp,
                                                     const double *__restrict__ fit,
                                                     double fail_thr, uint32_t *__restrict__ bitmap,
                                                     int32_t *__restrict__ wcount,
-                                                    double *__restrict__ key, BuildCtl *ctl) {
+                                                    unsigned long long *__restrict__ key,
+                                                    BuildCtl *ctl) {
     __shared__ SmemSpace s;
     __shared__ int64_t vals[FFG_MAX_VALUES];
     stage_space(sp, s, vals, true);
@@ -236,18 +259,42 @@ __global__ void __launch_bounds__(kThreads) k_valid(const DevSpace sp,
 // ---------------------------------------------------------------------------
 // out/in degree of every node
 // ---------------------------------------------------------------------------
-template <int NBH>
-__device__ __forceinline__ void count_body(const SmemSpace &s, int64_t R, int64_t r64,
-                                           const double *__restrict__ key, double fail_thr,
+// node id and node list of every valid raw point (raw point r, one block)
+__device__ __forceinline__ void nodes_body(int64_t R, int64_t r64,
+                                           const unsigned long long *__restrict__ key,
                                            const uint32_t *__restrict__ bitmap,
                                            const int64_t *__restrict__ wprefix, int64_t wbase,
+                                           int32_t *__restrict__ node_of,
+                                           int32_t *__restrict__ nodes) {
+    if (r64 >= R) return;
+    if (__ldg(key + r64) == kInvalidKey) return;  // not a valid point
+    const uint32_t r = static_cast<uint32_t>(r64);
+    const int32_t node = rank_of(bitmap, wprefix, wbase, r);
+    node_of[r] = node;
+    nodes[node] = static_cast<int32_t>(r);
+}
+
+__global__ void __launch_bounds__(kThreads) k_nodes(int64_t R,
+                                                    const unsigned long long *__restrict__ key,
+                                                    const uint32_t *__restrict__ bitmap,
+                                                    const int64_t *__restrict__ wprefix,
+                                                    int32_t *__restrict__ node_of,
+                                                    int32_t *__restrict__ nodes) {
+    nodes_body(R, int64_t(blockIdx.x) * kThreads + threadIdx.x, key, bitmap, wprefix, 0, node_of,
+               nodes);
+}
+
+// out/in degree of node `node` (one thread per node; nodes >= N idle)
+template <int NBH>
+__device__ __forceinline__ void count_body(const SmemSpace &s, int64_t N, int64_t node,
+                                           const int32_t *__restrict__ nodes,
+                                           const unsigned long long *__restrict__ key,
                                            int32_t *__restrict__ outdeg,
-                                           int32_t *__restrict__ indeg,
-                                           int32_t *__restrict__ node_of, BuildCtl *ctl) {
+                                           int32_t *__restrict__ indeg, BuildCtl *ctl) {
     unsigned long long n_out = 0, n_in = 0, n_min = 0;
-    const double k0 = r64 < R ? __ldg(key + r64) : invalid_key();
-    if (k0 == k0) {  // a valid point
-        const uint32_t r = static_cast<uint32_t>(r64);
+    if (node < N) {
+        const uint32_t r = static_cast<uint32_t>(__ldg(nodes + node));
+        const unsigned long long k0 = __ldg(key + r);
         int32_t out = 0, in = 0;
         uint32_t rem = r;
         for (int i = s.n - 1; i >= 0; --i) {
@@ -261,18 +308,16 @@ __device__ __forceinline__ void count_body(const SmemSpace &s, int64_t R, int64_
             const uint32_t jhi = NBH == FFG_HAMMING ? rad - 1 : (d + 1 < rad ? d + 1 : d);
             for (uint32_t j = jlo; j <= jhi; ++j) {
                 if (j == d) continue;
-                const double kk = __ldg(key + base + j * st);  // NaN if invalid
-                out += kk < k0;
+                const unsigned long long kk = __ldg(key + base + j * st);  // 0 if invalid
+                out += key_below(kk, k0);
                 in += kk > k0;
             }
         }
-        const int32_t node = rank_of(bitmap, wprefix, wbase, r);
-        node_of[r] = node;
         outdeg[node] = out;
         indeg[node] = in;
         n_out = out;
         n_in = in;
-        n_min = (k0 < fail_thr && out == 0) ? 1 : 0;
+        n_min = (k0 != kFailedKey && out == 0) ? 1 : 0;
     }
     const unsigned long long so = block_sum(n_out);
     const unsigned long long si = block_sum(n_in);
@@ -284,36 +329,37 @@ __device__ __forceinline__ void count_body(const SmemSpace &s, int64_t R, int64_
     }
 }
 
+// one thread per node; the node count comes from the device (blocks beyond
+// it have nothing to do)
 template <int NBH>
 __global__ void __launch_bounds__(kThreads) k_count(const DevSpace sp,
-                                                    const double *__restrict__ key,
-                                                    double fail_thr,
-                                                    const uint32_t *__restrict__ bitmap,
-                                                    const int64_t *__restrict__ wprefix,
+                                                    const int32_t *__restrict__ nodes,
+                                                    const unsigned long long *__restrict__ key,
                                                     int32_t *__restrict__ outdeg,
-                                                    int32_t *__restrict__ indeg,
-                                                    int32_t *__restrict__ node_of, BuildCtl *ctl) {
+                                                    int32_t *__restrict__ indeg, BuildCtl *ctl) {
+    const int64_t N = static_cast<int64_t>(*(volatile unsigned long long *)&ctl->n_nodes);
+    if (int64_t(blockIdx.x) * kThreads >= N) return;  // uniform over the block
     __shared__ SmemSpace s;
     stage_space(sp, s, nullptr, false);
-    count_body<NBH>(s, sp.n_raw, int64_t(blockIdx.x) * kThreads + threadIdx.x, key, fail_thr,
-                    bitmap, wprefix, 0, outdeg, indeg, node_of, ctl);
+    count_body<NBH>(s, N, int64_t(blockIdx.x) * kThreads + threadIdx.x, nodes, key, outdeg,
+                    indeg, ctl);
 }
 
 // ---------------------------------------------------------------------------
 // canonical CSR rows, outdeg, node_raw, is_min
 // ---------------------------------------------------------------------------
+// the CSR rows of node `node` (one thread per node)
 template <int NBH>
 __device__ __forceinline__ void emit_body(
-    const SmemSpace &s, int64_t R, int64_t r64, const double *__restrict__ key, double fail_thr,
-    const int32_t *__restrict__ node_of, const int64_t *__restrict__ out_ptr,
-    const int64_t *__restrict__ in_ptr, int32_t *__restrict__ out_idx,
-    int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg, int64_t *__restrict__ node_raw,
-    uint8_t *__restrict__ is_min) {
-    if (r64 >= R) return;
-    const double k0 = __ldg(key + r64);
-    if (!(k0 == k0)) return;  // not a valid point
-    const uint32_t r = static_cast<uint32_t>(r64);
-    const int32_t node = __ldg(node_of + r);
+    const SmemSpace &s, int64_t N, int64_t node64, const int32_t *__restrict__ nodes,
+    const unsigned long long *__restrict__ key, const int32_t *__restrict__ node_of,
+    const int64_t *__restrict__ out_ptr, const int64_t *__restrict__ in_ptr,
+    int32_t *__restrict__ out_idx, int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg,
+    int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min) {
+    if (node64 >= N) return;
+    const int32_t node = static_cast<int32_t>(node64);
+    const uint32_t r = static_cast<uint32_t>(__ldg(nodes + node));
+    const unsigned long long k0 = __ldg(key + r);
     const int64_t o0 = out_ptr[node];
     int64_t o = o0, q = in_ptr[node];
 
@@ -331,8 +377,8 @@ __device__ __forceinline__ void emit_body(
         }
     }
     auto visit = [&](uint32_t rr) {
-        const double kk = __ldg(key + rr);  // NaN if invalid: both tests false
-        if (kk < k0) out_idx[o++] = __ldg(node_of + rr);
+        const unsigned long long kk = __ldg(key + rr);  // 0 if invalid: both tests false
+        if (key_below(kk, k0)) out_idx[o++] = __ldg(node_of + rr);
         else if (kk > k0) in_idx[q++] = __ldg(node_of + rr);
     };
     // negative offsets: slowest parameter first, values ascending
@@ -357,20 +403,20 @@ __device__ __forceinline__ void emit_body(
     const int32_t od = static_cast<int32_t>(o - o0);
     outdeg[node] = od;
     node_raw[node] = r;
-    is_min[node] = (k0 < fail_thr && od == 0) ? 1 : 0;
+    is_min[node] = (k0 != kFailedKey && od == 0) ? 1 : 0;
 }
 
 template <int NBH>
 __global__ void __launch_bounds__(kThreads) k_emit(
-    const DevSpace sp, const double *__restrict__ key, double fail_thr,
-    const int32_t *__restrict__ node_of, const int64_t *__restrict__ out_ptr,
-    const int64_t *__restrict__ in_ptr, int32_t *__restrict__ out_idx,
-    int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg, int64_t *__restrict__ node_raw,
-    uint8_t *__restrict__ is_min) {
+    const DevSpace sp, int64_t N, const int32_t *__restrict__ nodes,
+    const unsigned long long *__restrict__ key, const int32_t *__restrict__ node_of,
+    const int64_t *__restrict__ out_ptr, const int64_t *__restrict__ in_ptr,
+    int32_t *__restrict__ out_idx, int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg,
+    int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min) {
     __shared__ SmemSpace s;
     stage_space(sp, s, nullptr, false);
-    emit_body<NBH>(s, sp.n_raw, int64_t(blockIdx.x) * kThreads + threadIdx.x, key, fail_thr,
-                   node_of, out_ptr, in_ptr, out_idx, in_idx, outdeg, node_raw, is_min);
+    emit_body<NBH>(s, N, int64_t(blockIdx.x) * kThreads + threadIdx.x, nodes, key, node_of,
+                   out_ptr, in_ptr, out_idx, in_idx, outdeg, node_raw, is_min);
 }
 
 ffg_status check_common(const ffg_space *space, const double *fitness_raw, ffg_nbh nbh,
@@ -421,14 +467,15 @@ extern "C" ffg_status ffg_build_count(const ffg_space *space, const double *fitn
     count_launch();
     FFG_TRY(check_launch("k_valid"));
     FFG_TRY(scan_exclusive(w.wcount, w.wprefix, W, w.scratch, stream));
+    k_nodes<<<grid, kThreads, 0, stream>>>(R, w.key, w.bitmap, w.wprefix, w.node_of, w.nodes);
+    count_launch();
+    FFG_TRY(check_launch("k_nodes"));
     if (nbh == FFG_HAMMING)
-        k_count<FFG_HAMMING><<<grid, kThreads, 0, stream>>>(d, w.key, fail_thr, w.bitmap,
-                                                            w.wprefix, w.outdeg, w.indeg,
-                                                            w.node_of, w.ctl);
+        k_count<FFG_HAMMING><<<grid, kThreads, 0, stream>>>(d, w.nodes, w.key, w.outdeg,
+                                                            w.indeg, w.ctl);
     else
-        k_count<FFG_ADJACENT><<<grid, kThreads, 0, stream>>>(d, w.key, fail_thr, w.bitmap,
-                                                             w.wprefix, w.outdeg, w.indeg,
-                                                             w.node_of, w.ctl);
+        k_count<FFG_ADJACENT><<<grid, kThreads, 0, stream>>>(d, w.nodes, w.key, w.outdeg,
+                                                             w.indeg, w.ctl);
     count_launch();
     FFG_TRY(check_launch("k_count"));
     BuildCtl h;
@@ -463,18 +510,18 @@ extern "C" ffg_status ffg_build_fill(const ffg_space *space, const double *fitne
     if (!g->out_ptr || !g->in_ptr || !g->outdeg || !g->node_raw || !g->is_min ||
         (g->n_edges > 0 && (!g->out_idx || !g->in_idx)))
         return set_error("a graph buffer is NULL"), FFG_ERR_INVALID_ARG;
-    const int64_t R = d.n_raw, N = g->n_nodes;
-    const unsigned grid = static_cast<unsigned>((R + kThreads - 1) / kThreads);
+    const int64_t N = g->n_nodes;
+    const unsigned grid = static_cast<unsigned>((N + kThreads - 1) / kThreads);
     FFG_TRY(scan_exclusive(w.outdeg, g->out_ptr, N, w.scratch, stream));
     FFG_TRY(scan_exclusive(w.indeg, g->in_ptr, N, w.scratch, stream));
     if (nbh == FFG_HAMMING)
         k_emit<FFG_HAMMING><<<grid, kThreads, 0, stream>>>(
-            d, w.key, fail_thr, w.node_of, g->out_ptr, g->in_ptr, g->out_idx, g->in_idx,
-            g->outdeg, g->node_raw, g->is_min);
+            d, N, w.nodes, w.key, w.node_of, g->out_ptr, g->in_ptr, g->out_idx,
+            g->in_idx, g->outdeg, g->node_raw, g->is_min);
     else
         k_emit<FFG_ADJACENT><<<grid, kThreads, 0, stream>>>(
-            d, w.key, fail_thr, w.node_of, g->out_ptr, g->in_ptr, g->out_idx, g->in_idx,
-            g->outdeg, g->node_raw, g->is_min);
+            d, N, w.nodes, w.key, w.node_of, g->out_ptr, g->in_ptr, g->out_idx,
+            g->in_idx, g->outdeg, g->node_raw, g->is_min);
     count_launch();
     return check_launch("k_emit");
 }
@@ -517,8 +564,10 @@ struct BatchBuildWs {
     int32_t *odeg, *ideg;
     int64_t *opre, *ipre;
     int64_t *scratch;
-    double *key;       // per raw point of every job
+    unsigned long long *key;  // per raw point of every job (see key_of)
     int32_t *node_of;  // per raw point of every job
+    int32_t *nodes;    // per node of every job (at the job's raw offset): its raw point
+    int64_t *blk0n;    // n + 1: first node block of every job (from the device counts)
     size_t bytes;
 };
 
@@ -540,8 +589,10 @@ BatchBuildWs carve_bb(void *base, int n, int64_t total_raw, int64_t total_words)
     w.ipre = c.take<int64_t>(total_raw + 1);
     w.scratch = c.take<int64_t>(scan_scratch_elems(total_raw > total_words ? total_raw
                                                                            : total_words));
-    w.key = c.take<double>(total_raw);
+    w.key = c.take<unsigned long long>(total_raw);
     w.node_of = c.take<int32_t>(total_raw);
+    w.nodes = c.take<int32_t>(total_raw);
+    w.blk0n = c.take<int64_t>(size_t(n) + 1);
     w.bytes = c.off;
     return w;
 }
@@ -574,7 +625,7 @@ __global__ void k_bctl_init(BuildCtl *ctl, int32_t *status, int n) {
 __global__ void __launch_bounds__(kThreads) k_valid_batch(const BJob *__restrict__ jobs,
                                                           const int64_t *__restrict__ blk0, int n,
                                                           uint32_t *bitmap, int32_t *wcount,
-                                                          double *key, BuildCtl *ctl) {
+                                                          unsigned long long *key, BuildCtl *ctl) {
     __shared__ SmemSpace s;
     __shared__ int64_t vals[FFG_MAX_VALUES];
     const int j = job_of_block(blk0, n);
@@ -585,27 +636,50 @@ __global__ void __launch_bounds__(kThreads) k_valid_batch(const BJob *__restrict
                key + J.roff, ctl + j);
 }
 
-__global__ void __launch_bounds__(kThreads) k_count_batch(const BJob *__restrict__ jobs,
+__global__ void __launch_bounds__(kThreads) k_nodes_batch(const BJob *__restrict__ jobs,
                                                           const int64_t *__restrict__ blk0, int n,
-                                                          const double *__restrict__ key,
+                                                          const unsigned long long *__restrict__ key,
                                                           const uint32_t *__restrict__ bitmap,
                                                           const int64_t *__restrict__ wpre,
-                                                          int32_t *odeg, int32_t *ideg,
-                                                          int32_t *node_of, BuildCtl *ctl) {
-    __shared__ SmemSpace s;
+                                                          int32_t *node_of, int32_t *nodes) {
     const int j = job_of_block(blk0, n);
     const BJob &J = jobs[j];
-    stage_space(*J.sp, s, nullptr, false);
     const int64_t r = (int64_t(blockIdx.x) - blk0[j]) * kThreads + threadIdx.x;
-    const int64_t wb = wpre[J.woff];
+    nodes_body(J.n_raw, r, key + J.roff, bitmap + J.woff, wpre + J.woff, wpre[J.woff],
+               node_of + J.roff, nodes + J.roff);
+}
+
+// first node block of every job, from the node counts of the validity pass
+__global__ void k_node_blocks(const BuildCtl *__restrict__ ctl, int n, int64_t *blk0n) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t b = 0;
+    for (int j = 0; j < n; ++j) {
+        blk0n[j] = b;
+        b += (static_cast<int64_t>(ctl[j].n_nodes) + kThreads - 1) / kThreads;
+    }
+    blk0n[n] = b;
+}
+
+// one thread per node; blocks past the last job's nodes have nothing to do
+__global__ void __launch_bounds__(kThreads) k_count_batch(const BJob *__restrict__ jobs,
+                                                          const int64_t *__restrict__ blk0n, int n,
+                                                          const unsigned long long *__restrict__ key,
+                                                          const int32_t *__restrict__ nodes,
+                                                          int32_t *odeg, int32_t *ideg,
+                                                          BuildCtl *ctl) {
+    if (int64_t(blockIdx.x) >= blk0n[n]) return;  // uniform over the block
+    __shared__ SmemSpace s;
+    const int j = job_of_block(blk0n, n);
+    const BJob &J = jobs[j];
+    stage_space(*J.sp, s, nullptr, false);
+    const int64_t node = (int64_t(blockIdx.x) - blk0n[j]) * kThreads + threadIdx.x;
+    const int64_t N = static_cast<int64_t>(ctl[j].n_nodes);
     if (J.nbh == FFG_HAMMING)
-        count_body<FFG_HAMMING>(s, J.n_raw, r, key + J.roff, J.fail_thr, bitmap + J.woff,
-                                wpre + J.woff, wb, odeg + J.roff, ideg + J.roff,
-                                node_of + J.roff, ctl + j);
+        count_body<FFG_HAMMING>(s, N, node, nodes + J.roff, key + J.roff, odeg + J.roff,
+                                ideg + J.roff, ctl + j);
     else
-        count_body<FFG_ADJACENT>(s, J.n_raw, r, key + J.roff, J.fail_thr, bitmap + J.woff,
-                                 wpre + J.woff, wb, odeg + J.roff, ideg + J.roff,
-                                 node_of + J.roff, ctl + j);
+        count_body<FFG_ADJACENT>(s, N, node, nodes + J.roff, key + J.roff, odeg + J.roff,
+                                 ideg + J.roff, ctl + j);
 }
 
 // the device counts of job j equal the sizes its graph arrays were made for
@@ -639,24 +713,26 @@ __global__ void k_rebase(const BJob *__restrict__ jobs, const int64_t *__restric
 }
 
 __global__ void __launch_bounds__(kThreads) k_emit_batch(const BJob *__restrict__ jobs,
-                                                         const int64_t *__restrict__ blk0, int n,
-                                                         const double *__restrict__ key,
+                                                         const int64_t *__restrict__ blk0n, int n,
+                                                         const unsigned long long *__restrict__ key,
+                                                         const int32_t *__restrict__ nodes,
                                                          const int32_t *__restrict__ node_of,
                                                          const BuildCtl *__restrict__ ctl) {
+    if (int64_t(blockIdx.x) >= blk0n[n]) return;  // uniform over the block
     __shared__ SmemSpace s;
-    const int j = job_of_block(blk0, n);
+    const int j = job_of_block(blk0n, n);
     const BJob &J = jobs[j];
     if (!sizes_match(J, ctl[j])) return;  // uniform over the block
     stage_space(*J.sp, s, nullptr, false);
-    const int64_t r = (int64_t(blockIdx.x) - blk0[j]) * kThreads + threadIdx.x;
+    const int64_t node = (int64_t(blockIdx.x) - blk0n[j]) * kThreads + threadIdx.x;
     if (J.nbh == FFG_HAMMING)
-        emit_body<FFG_HAMMING>(s, J.n_raw, r, key + J.roff, J.fail_thr, node_of + J.roff,
-                               J.out_ptr, J.in_ptr, J.out_idx, J.in_idx, J.outdeg, J.node_raw,
-                               J.is_min);
+        emit_body<FFG_HAMMING>(s, J.n_nodes, node, nodes + J.roff, key + J.roff,
+                               node_of + J.roff, J.out_ptr, J.in_ptr, J.out_idx, J.in_idx,
+                               J.outdeg, J.node_raw, J.is_min);
     else
-        emit_body<FFG_ADJACENT>(s, J.n_raw, r, key + J.roff, J.fail_thr, node_of + J.roff,
-                                J.out_ptr, J.in_ptr, J.out_idx, J.in_idx, J.outdeg, J.node_raw,
-                                J.is_min);
+        emit_body<FFG_ADJACENT>(s, J.n_nodes, node, nodes + J.roff, key + J.roff,
+                                node_of + J.roff, J.out_ptr, J.in_ptr, J.out_idx, J.in_idx,
+                                J.outdeg, J.node_raw, J.is_min);
 }
 
 struct BatchSizes {
@@ -705,8 +781,16 @@ ffg_status launch_count_phase(const BatchBuildWs &w, int n, int64_t total_raw,
     count_launch();
     FFG_TRY(check_launch("k_valid_batch"));
     FFG_TRY(scan_exclusive(w.wcount, w.wpre, total_words, w.scratch, stream));
+    k_nodes_batch<<<static_cast<unsigned>(total_blocks), kThreads, 0, stream>>>(
+        w.jobs, w.blk0, n, w.key, w.bitmap, w.wpre, w.node_of, w.nodes);
+    count_launch();
+    FFG_TRY(check_launch("k_nodes_batch"));
+    k_node_blocks<<<1, 32, 0, stream>>>(w.ctl, n, w.blk0n);
+    count_launch();
+    FFG_TRY(check_launch("k_node_blocks"));
+    // grid sized for every raw point: the node blocks are fewer
     k_count_batch<<<static_cast<unsigned>(total_blocks), kThreads, 0, stream>>>(
-        w.jobs, w.blk0, n, w.key, w.bitmap, w.wpre, w.odeg, w.ideg, w.node_of, w.ctl);
+        w.jobs, w.blk0n, n, w.key, w.nodes, w.odeg, w.ideg, w.ctl);
     count_launch();
     return check_launch("k_count_batch");
 }
@@ -721,7 +805,7 @@ ffg_status launch_fill_phase(const BatchBuildWs &w, int n, int64_t total_raw, in
     count_launch();
     FFG_TRY(check_launch("k_rebase"));
     k_emit_batch<<<static_cast<unsigned>(total_blocks), kThreads, 0, stream>>>(
-        w.jobs, w.blk0, n, w.key, w.node_of, w.ctl);
+        w.jobs, w.blk0n, n, w.key, w.nodes, w.node_of, w.ctl);
     count_launch();
     return check_launch("k_emit_batch");
 }
@@ -742,8 +826,10 @@ BatchBuildWs ws_of(const ffg_build_batch *plan) {
     w.opre = static_cast<int64_t *>(plan->tables[11]);
     w.ipre = static_cast<int64_t *>(plan->tables[12]);
     w.scratch = static_cast<int64_t *>(plan->tables[13]);
-    w.key = static_cast<double *>(plan->tables[14]);
+    w.key = static_cast<unsigned long long *>(plan->tables[14]);
     w.node_of = static_cast<int32_t *>(plan->tables[15]);
+    w.nodes = static_cast<int32_t *>(plan->tables[16]);
+    w.blk0n = static_cast<int64_t *>(plan->tables[17]);
     return w;
 }
 
@@ -820,9 +906,9 @@ extern "C" ffg_status ffg_build_batch_count(const ffg_build_job *jobs, int32_t n
     plan->total_words = z.total_words;
     plan->total_blocks = z.total_blocks;
     plan->total_rows = 0;
-    void *t[] = {w.dsp,  w.jobs, w.blk0, w.row0, w.ctl,  w.status,  w.bitmap, w.wcount,
-                 w.wpre, w.odeg, w.ideg, w.opre, w.ipre, w.scratch, w.key,    w.node_of};
-    for (int k = 0; k < 16; ++k) plan->tables[k] = t[k];
+    void *t[] = {w.dsp,  w.jobs, w.blk0, w.row0, w.ctl,     w.status, w.bitmap,  w.wcount, w.wpre,
+                 w.odeg, w.ideg, w.opre, w.ipre, w.scratch, w.key,    w.node_of, w.nodes,  w.blk0n};
+    for (int k = 0; k < 18; ++k) plan->tables[k] = t[k];
     if (empty) return set_error("a job has no valid configuration"), FFG_ERR_EMPTY;
     return FFG_OK;
 }
