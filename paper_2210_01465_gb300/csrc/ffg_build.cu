@@ -348,20 +348,36 @@ __global__ void __launch_bounds__(kThreads) k_count(const DevSpace sp,
 // ---------------------------------------------------------------------------
 // canonical CSR rows, outdeg, node_raw, is_min
 // ---------------------------------------------------------------------------
-// the CSR rows of node `node` (one thread per node)
+// The CSR rows of node `node` (one thread per node).  The rows of a warp's
+// 32 consecutive nodes are contiguous in out_idx (and in in_idx), so the
+// warp stages them in shared memory when they fit (kEmitBuf entries each)
+// and writes them out together, coalesced, instead of one scattered 4-byte
+// store per edge.  `stage`: this warp's 2 * kEmitBuf entries.
+constexpr int kEmitBuf = 640;
+
 template <int NBH>
 __device__ __forceinline__ void emit_body(
     const SmemSpace &s, int64_t N, int64_t node64, const int32_t *__restrict__ nodes,
     const unsigned long long *__restrict__ key, const int32_t *__restrict__ node_of,
     const int64_t *__restrict__ out_ptr, const int64_t *__restrict__ in_ptr,
     int32_t *__restrict__ out_idx, int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg,
-    int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min) {
-    if (node64 >= N) return;
+    int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min, int32_t *stage) {
+    const int lane = threadIdx.x & 31;
+    const int64_t first = node64 - lane;  // the warp's first node
+    if (first >= N) return;               // uniform over the warp
+    const int64_t last = first + 32 < N ? first + 32 : N;
+    const int64_t ob = out_ptr[first], lo = out_ptr[last] - ob;
+    const int64_t qb = in_ptr[first], lq = in_ptr[last] - qb;
+    const bool staged = lo <= kEmitBuf && lq <= kEmitBuf;  // uniform over the warp
+    int32_t *dst_out = staged ? stage : out_idx;
+    int32_t *dst_in = staged ? stage + kEmitBuf : in_idx;
+    if (node64 < N) {
     const int32_t node = static_cast<int32_t>(node64);
     const uint32_t r = static_cast<uint32_t>(__ldg(nodes + node));
     const unsigned long long k0 = __ldg(key + r);
     const int64_t o0 = out_ptr[node];
-    int64_t o = o0, q = in_ptr[node];
+    int64_t o = o0 - (staged ? ob : 0), q = in_ptr[node] - (staged ? qb : 0);
+    const int64_t os = o;
 
     uint32_t digit[FFG_MAX_PARAMS];
     {
@@ -378,8 +394,8 @@ __device__ __forceinline__ void emit_body(
     }
     auto visit = [&](uint32_t rr) {
         const unsigned long long kk = __ldg(key + rr);  // 0 if invalid: both tests false
-        if (key_below(kk, k0)) out_idx[o++] = __ldg(node_of + rr);
-        else if (kk > k0) in_idx[q++] = __ldg(node_of + rr);
+        if (key_below(kk, k0)) dst_out[o++] = __ldg(node_of + rr);
+        else if (kk > k0) dst_in[q++] = __ldg(node_of + rr);
     };
     // negative offsets: slowest parameter first, values ascending
 #pragma unroll
@@ -400,10 +416,16 @@ __device__ __forceinline__ void emit_body(
             for (uint32_t j = d + 1; j < jhi; ++j) visit(r + (j - d) * st);
         }
     }
-    const int32_t od = static_cast<int32_t>(o - o0);
+    const int32_t od = static_cast<int32_t>(o - os);
     outdeg[node] = od;
     node_raw[node] = r;
     is_min[node] = (k0 != kFailedKey && od == 0) ? 1 : 0;
+    }
+    if (staged) {  // the warp's rows, coalesced
+        __syncwarp();
+        for (int64_t k = lane; k < lo; k += 32) out_idx[ob + k] = stage[k];
+        for (int64_t k = lane; k < lq; k += 32) in_idx[qb + k] = stage[kEmitBuf + k];
+    }
 }
 
 template <int NBH>
@@ -414,9 +436,11 @@ __global__ void __launch_bounds__(kThreads) k_emit(
     int32_t *__restrict__ out_idx, int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg,
     int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min) {
     __shared__ SmemSpace s;
+    __shared__ int32_t stage[kThreads / 32][2 * kEmitBuf];
     stage_space(sp, s, nullptr, false);
     emit_body<NBH>(s, N, int64_t(blockIdx.x) * kThreads + threadIdx.x, nodes, key, node_of,
-                   out_ptr, in_ptr, out_idx, in_idx, outdeg, node_raw, is_min);
+                   out_ptr, in_ptr, out_idx, in_idx, outdeg, node_raw, is_min,
+                   stage[threadIdx.x >> 5]);
 }
 
 ffg_status check_common(const ffg_space *space, const double *fitness_raw, ffg_nbh nbh,
@@ -720,6 +744,7 @@ __global__ void __launch_bounds__(kThreads) k_emit_batch(const BJob *__restrict_
                                                          const BuildCtl *__restrict__ ctl) {
     if (int64_t(blockIdx.x) >= blk0n[n]) return;  // uniform over the block
     __shared__ SmemSpace s;
+    __shared__ int32_t stage[kThreads / 32][2 * kEmitBuf];
     const int j = job_of_block(blk0n, n);
     const BJob &J = jobs[j];
     if (!sizes_match(J, ctl[j])) return;  // uniform over the block
@@ -728,11 +753,11 @@ __global__ void __launch_bounds__(kThreads) k_emit_batch(const BJob *__restrict_
     if (J.nbh == FFG_HAMMING)
         emit_body<FFG_HAMMING>(s, J.n_nodes, node, nodes + J.roff, key + J.roff,
                                node_of + J.roff, J.out_ptr, J.in_ptr, J.out_idx, J.in_idx,
-                               J.outdeg, J.node_raw, J.is_min);
+                               J.outdeg, J.node_raw, J.is_min, stage[threadIdx.x >> 5]);
     else
         emit_body<FFG_ADJACENT>(s, J.n_nodes, node, nodes + J.roff, key + J.roff,
                                 node_of + J.roff, J.out_ptr, J.in_ptr, J.out_idx, J.in_idx,
-                                J.outdeg, J.node_raw, J.is_min);
+                                J.outdeg, J.node_raw, J.is_min, stage[threadIdx.x >> 5]);
 }
 
 struct BatchSizes {

@@ -113,12 +113,6 @@ constexpr int64_t kTileCost = 19;       // per-tile cost in descriptor units (bl
 // phases p with (p - 1) % 3 == b: blocks add theirs before the phase's
 // barrier, everyone reads them after it, and rank 0 clears the next buffer
 // during the phase (its last readers passed the previous barrier).
-// Blocks of a group take tiles left in each other's ranges once their own
-// is done (groups of up to kStealRanks blocks): tctr[b][r] counts the tiles
-// taken from rank r's range in the iterations that use buffer b (the
-// buffers rotate like acc).
-constexpr int kStealRanks = 256;
-
 struct PrCtl {
     unsigned int barrier;
     int status;
@@ -129,7 +123,6 @@ struct PrCtl {
     int pad;
     unsigned long long acc[3][4];
     unsigned long long busy_ns;  // sum over the job's blocks of their time on it
-    unsigned int tctr[3][kStealRanks];
 };
 
 struct PrWs {
@@ -935,38 +928,6 @@ __device__ __forceinline__ void advance(const JobDev &J, LoopState &ls, const Pr
     else if (ls.it >= J.max_iter) ls.stop = 1;
 }
 
-// A tile left in another rank's range (lanes look at the ranks in
-// parallel), or -1 when every range is used up: ctr[r] counts the tiles
-// taken from rank r's range [rng[r].x, rng[r].y) past its first `skip`
-// (which its own warps start with).  Kept out of line: it runs only at the
-// end of an iteration.
-#ifndef FFG_PR_STEAL_INLINE
-#define FFG_PR_STEAL_INLINE 0
-#endif
-#if FFG_PR_STEAL_INLINE
-__device__ __forceinline__
-#else
-__device__ __noinline__
-#endif
-    int steal_tile(unsigned *ctr, const int2 *rng, int rank, int nb, int skip, int lane) {
-    for (int attempt = 0; attempt < 16; ++attempt) {
-        int cand = -1;
-        for (int i = lane; i < nb && cand < 0; i += 32) {
-            const int r = (rank + 1 + i) % nb;
-            const int2 rg = rng[r];
-            if (rg.y - rg.x - skip - static_cast<int>(*(volatile unsigned *)&ctr[r]) > 0) cand = r;
-        }
-        const unsigned any = __ballot_sync(0xffffffffu, cand >= 0);
-        if (!any) return -1;
-        const int r = __shfl_sync(0xffffffffu, cand, __ffs(any) - 1);
-        unsigned g = 0;
-        if (lane == 0) g = atomicAdd(&ctr[r], 1u);
-        const int t = rng[r].x + skip + static_cast<int>(__shfl_sync(0xffffffffu, g, 0));
-        if (t < rng[r].y) return t;
-    }
-    return -1;
-}
-
 // A group of blocks runs all iterations of one job.  Returns false if the
 // block must stop (a bounded wait expired).
 template <typename T, int W>
@@ -994,21 +955,12 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     __shared__ unsigned s_next;
     __shared__ LoopState s_ls;
     __shared__ R s_c;
-    __shared__ int2 s_rng[kStealRanks];  // every rank's tile range (stealing groups)
-#ifndef FFG_PR_STEAL
-#define FFG_PR_STEAL 1
-#endif
-    const bool steal = FFG_PR_STEAL && nb > 1 && nb <= kStealRanks;
     __syncthreads();
-    const int64_t ntiles_all = (J.apre[n] - J.apre[0] + 31) >> 5;
-    if (steal)
-        for (int r = threadIdx.x; r < nb; r += kThreads)
-            s_rng[r] = make_int2(static_cast<int>(tile_split(J.tpre, ntiles_all, r, nb)),
-                                 static_cast<int>(tile_split(J.tpre, ntiles_all, r + 1, nb)));
     if (threadIdx.x == 0) {
-        s_range[2] = static_cast<int>(ntiles_all);
-        s_range[0] = static_cast<int>(tile_split(J.tpre, ntiles_all, rank, nb));
-        s_range[1] = static_cast<int>(tile_split(J.tpre, ntiles_all, rank + 1, nb));
+        const int64_t ntiles = (J.apre[n] - J.apre[0] + 31) >> 5;
+        s_range[2] = static_cast<int>(ntiles);
+        s_range[0] = static_cast<int>(tile_split(J.tpre, ntiles, rank, nb));
+        s_range[1] = static_cast<int>(tile_split(J.tpre, ntiles, rank + 1, nb));
         s_next = static_cast<unsigned>(s_range[0] + 2 * W);
         s_ls.res = __longlong_as_double(0x7ff0000000000000LL);
         s_ls.it = s_ls.stop = s_ls.converged = 0;
@@ -1051,28 +1003,6 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
     while (true) {
         const R c = s_c;
         Fix3 facc;
-        // this iteration's tile counters; rank 0 clears the next iteration's
-        // (their last users passed the previous barrier)
-        const int cb = buf == 2 ? 0 : buf + 1;
-        if (steal && rank == 0)
-            for (int r = threadIdx.x; r < nb; r += kThreads) ctl->tctr[cb == 2 ? 0 : cb + 1][r] = 0;
-        bool own_left = true;
-        // the next tile for this warp, or -1: from the block's range while it
-        // lasts, then (stealing groups) from the ranges of the other ranks
-        auto claim = [&]() -> int {
-            if (own_left) {
-                unsigned g = 0;
-                if (lane == 0)
-                    g = steal ? static_cast<unsigned>(bt0 + 2 * W) +
-                                    atomicAdd(&ctl->tctr[cb][rank], 1u)
-                              : atomicAdd(&s_next, 1u);
-                const int t = static_cast<int>(__shfl_sync(0xffffffffu, g, 0));
-                if (t < bt1) return t;
-                own_left = false;
-            }
-            if (!steal) return -1;
-            return steal_tile(ctl->tctr[cb], s_rng, rank, nb, 2 * W, lane);
-        };
         if (t0 < bt1 && !failed) {
             // cur: tile being summed; nxt: its successor (info loaded one tile
             // ahead, so its first segment can be issued at once); the tile
@@ -1087,13 +1017,16 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
                 nxt = load_head<T>(t1 < bt1 ? t1 : t0, ni, tinfo, perm, lane);
                 load_row<T>(cur, outdeg, wc, rinv);
             }
-            if (!(tn < bt1)) tn = claim();  // no second tile of its own
-            if (tn >= 0 && !(t1 < bt1)) nxt = load_head<T>(tn, ni, tinfo, perm, lane);
             while (true) {
-                const bool has_next = tn >= 0;
-                const int tn2 = has_next ? claim() : -1;
+                const bool has_next = tn < bt1;
+                int tn2 = bt1;
+                if (has_next) {
+                    unsigned g = 0;
+                    if (lane == 0) g = atomicAdd(&s_next, 1u);
+                    tn2 = static_cast<int>(__shfl_sync(0xffffffffu, g, 0));
+                }
                 load_row<T>(nxt, outdeg, wc, rinv);
-                const TileInfo<T> nx2 = load_head<T>(tn2 >= 0 ? tn2 : t, ni, tinfo, perm, lane);
+                const TileInfo<T> nx2 = load_head<T>(tn2 < bt1 ? tn2 : t, ni, tinfo, perm, lane);
                 const int v = cur.v;
                 R s = R(0);
                 if (!tile_sum<T>(desc, cur, nxt, has_next, st, wc + (v < 0 ? 0 : v), 1u << lane,
