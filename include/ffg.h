@@ -601,6 +601,22 @@ const char *ffg_status_str(ffg_status s);
 const char *ffg_last_error(void);
 /* Number of kernels this library has launched in this process. */
 uint64_t ffg_launch_count(void);
+/* Bounds-checked builds (compiled with -DFFG_CHECKED): every index a kernel
+ * derives from caller data -- CSR entries, row pointers, layout descriptors
+ * -- is checked before the access it guards; a failed check skips the
+ * access and is counted.  ffg_checked_build returns 1 in such a build, 0
+ * otherwise.  ffg_checked_failures returns the number of failed checks since
+ * the last reset (0 in a normal build), stores the site code of the first
+ * one in *first_code (if non-NULL; 0 if none) and, when `reset` is non-zero,
+ * clears the record.  Site codes: 1xx PageRank (101 a gather outside w, 102
+ * a layout write outside the tile's room), 2xx FFG build (201/202 a CSR
+ * write or a node id outside the node's row or the nodes,
+ * 203 a neighbour outside the raw points), 3xx DAG solve (301 an
+ * out-neighbour, 302 an in-neighbour outside the nodes), 401 a walk step
+ * to a node outside the nodes, 5xx C_p (501 in the rank sums, 502 in the
+ * minima listing: a node's raw point outside the fitness). */
+int ffg_checked_build(void);
+uint64_t ffg_checked_failures(uint64_t *first_code, int reset);
 
 #ifdef __cplusplus
 }

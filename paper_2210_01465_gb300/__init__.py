@@ -24,7 +24,7 @@ import os
 
 import numpy as np
 
-from ._build import LIB_PATH, build  # noqa: F401
+from ._build import CHECKED_LIB_PATH, LIB_PATH, build  # noqa: F401
 
 # ---- constants of include/ffg.h -------------------------------------------
 FFG_OK, FFG_ERR_INVALID_ARG, FFG_ERR_OVERFLOW, FFG_ERR_CUDA = 0, 1, 2, 3
@@ -154,9 +154,19 @@ ENTRY_POINTS = ("ffg_workspace_bytes", "ffg_build_count", "ffg_build_fill",
                 "centrality_batch_run", "centrality_batch_query", "centrality_batch",
                 "ffg_batch_run",
                 "ffg_status_str",
-                "ffg_last_error", "ffg_launch_count")
+                "ffg_last_error", "ffg_launch_count",
+                "ffg_checked_build", "ffg_checked_failures")
 
 _lib = None
+
+
+def default_lib_path() -> str:
+    """The library ``load()`` opens: ``FFG_LIB=checked`` selects the
+    bounds-checked build, another non-empty value is a path."""
+    sel = os.environ.get("FFG_LIB", "")
+    if sel == "checked":
+        return CHECKED_LIB_PATH
+    return sel or LIB_PATH
 
 
 def load(path: str | None = None):
@@ -164,7 +174,7 @@ def load(path: str | None = None):
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    p = path or default_lib_path()
     if not os.path.exists(p):
         raise ImportError(f"FFG CUDA library not built: {p} is missing "
                           "(run paper_2210_01465_gb300.build())")
@@ -234,6 +244,10 @@ def load(path: str | None = None):
     lib.ffg_last_error.restype = C.c_char_p
     lib.ffg_launch_count.argtypes = []
     lib.ffg_launch_count.restype = C.c_uint64
+    lib.ffg_checked_build.argtypes = []
+    lib.ffg_checked_build.restype = C.c_int
+    lib.ffg_checked_failures.argtypes = [P(C.c_uint64), C.c_int]
+    lib.ffg_checked_failures.restype = C.c_uint64
     if path is None:
         _lib = lib
     return lib
@@ -251,6 +265,17 @@ def ffg_last_error() -> str:
 
 def ffg_launch_count() -> int:
     return int(load().ffg_launch_count())
+
+
+def ffg_checked_build() -> bool:
+    return bool(load().ffg_checked_build())
+
+
+def ffg_checked_failures(reset: bool = False) -> tuple[int, int]:
+    """(failed checks since the last reset, site code of the first one)."""
+    first = C.c_uint64(0)
+    n = load().ffg_checked_failures(C.byref(first), int(bool(reset)))
+    return int(n), int(first.value)
 
 
 def ffg_workspace_bytes(space: "Space", nbh: int) -> int:

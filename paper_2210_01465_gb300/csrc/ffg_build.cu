@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kThreads) k_nodes(int64_t R,
 
 // out/in degree of node `node` (one thread per node; nodes >= N idle)
 template <int NBH>
-__device__ __forceinline__ void count_body(const SmemSpace &s, int64_t N, int64_t node,
+__device__ __forceinline__ void count_body(const SmemSpace &s, int64_t R, int64_t N, int64_t node,
                                            const int32_t *__restrict__ nodes,
                                            const unsigned long long *__restrict__ key,
                                            int32_t *__restrict__ outdeg,
@@ -308,7 +308,9 @@ __device__ __forceinline__ void count_body(const SmemSpace &s, int64_t N, int64_
             const uint32_t jhi = NBH == FFG_HAMMING ? rad - 1 : (d + 1 < rad ? d + 1 : d);
             for (uint32_t j = jlo; j <= jhi; ++j) {
                 if (j == d) continue;
-                const unsigned long long kk = __ldg(key + base + j * st);  // 0 if invalid
+                const uint32_t rr = base + j * st;
+                const unsigned long long kk =
+                    FFG_CHECK(rr < R, 203) ? __ldg(key + rr) : kInvalidKey;  // 0 if invalid
                 out += key_below(kk, k0);
                 in += kk > k0;
             }
@@ -341,43 +343,28 @@ __global__ void __launch_bounds__(kThreads) k_count(const DevSpace sp,
     if (int64_t(blockIdx.x) * kThreads >= N) return;  // uniform over the block
     __shared__ SmemSpace s;
     stage_space(sp, s, nullptr, false);
-    count_body<NBH>(s, N, int64_t(blockIdx.x) * kThreads + threadIdx.x, nodes, key, outdeg,
-                    indeg, ctl);
+    count_body<NBH>(s, sp.n_raw, N, int64_t(blockIdx.x) * kThreads + threadIdx.x, nodes, key,
+                    outdeg, indeg, ctl);
 }
 
 // ---------------------------------------------------------------------------
 // canonical CSR rows, outdeg, node_raw, is_min
 // ---------------------------------------------------------------------------
-// The CSR rows of node `node` (one thread per node).  The rows of a warp's
-// 32 consecutive nodes are contiguous in out_idx (and in in_idx), so the
-// warp stages them in shared memory when they fit (kEmitBuf entries each)
-// and writes them out together, coalesced, instead of one scattered 4-byte
-// store per edge.  `stage`: this warp's 2 * kEmitBuf entries.
-constexpr int kEmitBuf = 640;
-
+// The CSR rows of node `node` (one thread per node).
 template <int NBH>
 __device__ __forceinline__ void emit_body(
-    const SmemSpace &s, int64_t N, int64_t node64, const int32_t *__restrict__ nodes,
+    const SmemSpace &s, int64_t R, int64_t N, int64_t node64, const int32_t *__restrict__ nodes,
     const unsigned long long *__restrict__ key, const int32_t *__restrict__ node_of,
     const int64_t *__restrict__ out_ptr, const int64_t *__restrict__ in_ptr,
     int32_t *__restrict__ out_idx, int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg,
-    int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min, int32_t *stage) {
-    const int lane = threadIdx.x & 31;
-    const int64_t first = node64 - lane;  // the warp's first node
-    if (first >= N) return;               // uniform over the warp
-    const int64_t last = first + 32 < N ? first + 32 : N;
-    const int64_t ob = out_ptr[first], lo = out_ptr[last] - ob;
-    const int64_t qb = in_ptr[first], lq = in_ptr[last] - qb;
-    const bool staged = lo <= kEmitBuf && lq <= kEmitBuf;  // uniform over the warp
-    int32_t *dst_out = staged ? stage : out_idx;
-    int32_t *dst_in = staged ? stage + kEmitBuf : in_idx;
-    if (node64 < N) {
+    int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min) {
+    if (node64 >= N) return;
     const int32_t node = static_cast<int32_t>(node64);
     const uint32_t r = static_cast<uint32_t>(__ldg(nodes + node));
     const unsigned long long k0 = __ldg(key + r);
     const int64_t o0 = out_ptr[node];
-    int64_t o = o0 - (staged ? ob : 0), q = in_ptr[node] - (staged ? qb : 0);
-    const int64_t os = o;
+    [[maybe_unused]] const int64_t o1 = out_ptr[node + 1], q1 = in_ptr[node + 1];  // checks
+    int64_t o = o0, q = in_ptr[node];
 
     uint32_t digit[FFG_MAX_PARAMS];
     {
@@ -393,9 +380,19 @@ __device__ __forceinline__ void emit_body(
         }
     }
     auto visit = [&](uint32_t rr) {
+        // the key and the node id load together (the node id is used only
+        // for an edge, but loading it unconditionally keeps the two loads
+        // independent instead of chaining a second latency per edge)
+        if (!FFG_CHECK(rr < R, 203)) return;
         const unsigned long long kk = __ldg(key + rr);  // 0 if invalid: both tests false
-        if (key_below(kk, k0)) dst_out[o++] = __ldg(node_of + rr);
-        else if (kk > k0) dst_in[q++] = __ldg(node_of + rr);
+        const int32_t id = __ldg(node_of + rr);
+        if (key_below(kk, k0)) {
+            if (FFG_CHECK(o < o1 && id >= 0 && id < N, 201)) out_idx[o] = id;
+            ++o;
+        } else if (kk > k0) {
+            if (FFG_CHECK(q < q1 && id >= 0 && id < N, 202)) in_idx[q] = id;
+            ++q;
+        }
     };
     // negative offsets: slowest parameter first, values ascending
 #pragma unroll
@@ -416,16 +413,10 @@ __device__ __forceinline__ void emit_body(
             for (uint32_t j = d + 1; j < jhi; ++j) visit(r + (j - d) * st);
         }
     }
-    const int32_t od = static_cast<int32_t>(o - os);
+    const int32_t od = static_cast<int32_t>(o - o0);
     outdeg[node] = od;
     node_raw[node] = r;
     is_min[node] = (k0 != kFailedKey && od == 0) ? 1 : 0;
-    }
-    if (staged) {  // the warp's rows, coalesced
-        __syncwarp();
-        for (int64_t k = lane; k < lo; k += 32) out_idx[ob + k] = stage[k];
-        for (int64_t k = lane; k < lq; k += 32) in_idx[qb + k] = stage[kEmitBuf + k];
-    }
 }
 
 template <int NBH>
@@ -436,11 +427,9 @@ __global__ void __launch_bounds__(kThreads) k_emit(
     int32_t *__restrict__ out_idx, int32_t *__restrict__ in_idx, int32_t *__restrict__ outdeg,
     int64_t *__restrict__ node_raw, uint8_t *__restrict__ is_min) {
     __shared__ SmemSpace s;
-    __shared__ int32_t stage[kThreads / 32][2 * kEmitBuf];
     stage_space(sp, s, nullptr, false);
-    emit_body<NBH>(s, N, int64_t(blockIdx.x) * kThreads + threadIdx.x, nodes, key, node_of,
-                   out_ptr, in_ptr, out_idx, in_idx, outdeg, node_raw, is_min,
-                   stage[threadIdx.x >> 5]);
+    emit_body<NBH>(s, sp.n_raw, N, int64_t(blockIdx.x) * kThreads + threadIdx.x, nodes, key,
+                   node_of, out_ptr, in_ptr, out_idx, in_idx, outdeg, node_raw, is_min);
 }
 
 ffg_status check_common(const ffg_space *space, const double *fitness_raw, ffg_nbh nbh,
@@ -699,11 +688,11 @@ __global__ void __launch_bounds__(kThreads) k_count_batch(const BJob *__restrict
     const int64_t node = (int64_t(blockIdx.x) - blk0n[j]) * kThreads + threadIdx.x;
     const int64_t N = static_cast<int64_t>(ctl[j].n_nodes);
     if (J.nbh == FFG_HAMMING)
-        count_body<FFG_HAMMING>(s, N, node, nodes + J.roff, key + J.roff, odeg + J.roff,
-                                ideg + J.roff, ctl + j);
+        count_body<FFG_HAMMING>(s, J.n_raw, N, node, nodes + J.roff, key + J.roff,
+                                odeg + J.roff, ideg + J.roff, ctl + j);
     else
-        count_body<FFG_ADJACENT>(s, N, node, nodes + J.roff, key + J.roff, odeg + J.roff,
-                                 ideg + J.roff, ctl + j);
+        count_body<FFG_ADJACENT>(s, J.n_raw, N, node, nodes + J.roff, key + J.roff,
+                                 odeg + J.roff, ideg + J.roff, ctl + j);
 }
 
 // the device counts of job j equal the sizes its graph arrays were made for
@@ -744,20 +733,19 @@ __global__ void __launch_bounds__(kThreads) k_emit_batch(const BJob *__restrict_
                                                          const BuildCtl *__restrict__ ctl) {
     if (int64_t(blockIdx.x) >= blk0n[n]) return;  // uniform over the block
     __shared__ SmemSpace s;
-    __shared__ int32_t stage[kThreads / 32][2 * kEmitBuf];
     const int j = job_of_block(blk0n, n);
     const BJob &J = jobs[j];
     if (!sizes_match(J, ctl[j])) return;  // uniform over the block
     stage_space(*J.sp, s, nullptr, false);
     const int64_t node = (int64_t(blockIdx.x) - blk0n[j]) * kThreads + threadIdx.x;
     if (J.nbh == FFG_HAMMING)
-        emit_body<FFG_HAMMING>(s, J.n_nodes, node, nodes + J.roff, key + J.roff,
+        emit_body<FFG_HAMMING>(s, J.n_raw, J.n_nodes, node, nodes + J.roff, key + J.roff,
                                node_of + J.roff, J.out_ptr, J.in_ptr, J.out_idx, J.in_idx,
-                               J.outdeg, J.node_raw, J.is_min, stage[threadIdx.x >> 5]);
+                               J.outdeg, J.node_raw, J.is_min);
     else
-        emit_body<FFG_ADJACENT>(s, J.n_nodes, node, nodes + J.roff, key + J.roff,
+        emit_body<FFG_ADJACENT>(s, J.n_raw, J.n_nodes, node, nodes + J.roff, key + J.roff,
                                 node_of + J.roff, J.out_ptr, J.in_ptr, J.out_idx, J.in_idx,
-                                J.outdeg, J.node_raw, J.is_min, stage[threadIdx.x >> 5]);
+                                J.outdeg, J.node_raw, J.is_min);
 }
 
 struct BatchSizes {
@@ -1010,3 +998,7 @@ extern "C" ffg_status ffg_build_batch_query(const ffg_build_batch *plan, int32_t
     if (worst != FFG_OK) set_error("a job's counts differ from the sizes of its arrays");
     return worst;
 }
+
+namespace ffg {
+FFG_CHECK_READER(check_read_build)
+}  // namespace ffg

@@ -126,4 +126,28 @@ const char *ffg_last_error(void) { return ffg::t_error; }
 
 uint64_t ffg_launch_count(void) { return ffg::g_launches.load(); }
 
+int ffg_checked_build(void) {
+#ifdef FFG_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+uint64_t ffg_checked_failures(uint64_t *first_code, int reset) {
+    using Reader = void (*)(unsigned long long *, unsigned long long *, bool);
+    const Reader readers[] = {ffg::check_read_build, ffg::check_read_pagerank,
+                              ffg::check_read_dag, ffg::check_read_walk,
+                              ffg::check_read_centrality};
+    unsigned long long total = 0, first = 0;
+    for (Reader r : readers) {
+        unsigned long long code = 0, count = 0;
+        r(&code, &count, reset != 0);
+        if (!first && code) first = code;
+        total += count;
+    }
+    if (first_code) *first_code = first;
+    return total;
+}
+
 }  // extern "C"

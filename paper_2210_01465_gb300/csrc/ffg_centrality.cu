@@ -53,7 +53,8 @@ __device__ __forceinline__ void neumaier(double &s, double &c, double v) {
 
 template <typename T>
 __global__ void __launch_bounds__(kCpThreads) k_cp_partial(
-    int64_t n, const uint8_t *__restrict__ is_min, const int64_t *__restrict__ node_raw,
+    int64_t n, int64_t n_raw, const uint8_t *__restrict__ is_min,
+    const int64_t *__restrict__ node_raw,
     const double *__restrict__ fit, const T *__restrict__ x, const Thresholds th,
     double *__restrict__ partials) {
     double acc[kBuckets];
@@ -61,7 +62,9 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_partial(
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
         if (!is_min[v]) continue;
-        const double f = fit[node_raw[v]];
+        const int64_t rv = node_raw[v];
+        if (!FFG_CHECK(rv >= 0 && rv < n_raw, 501)) continue;
+        const double f = fit[rv];
         int b = 0;
         while (b < th.n && !(f <= th.thr[b])) ++b;
         acc[b] += static_cast<double>(x[v]);
@@ -186,12 +189,12 @@ extern "C" ffg_status centrality_proportion(const ffg_graph *g, const double *fi
     if (nblocks < 1) nblocks = 1;
     if (prec == FFG_F64)
         k_cp_partial<double><<<nblocks, kCpThreads, 0, stream>>>(
-            g->n_nodes, g->is_min, g->node_raw, fitness_raw, static_cast<const double *>(ranks), th,
-            w.partials);
+            g->n_nodes, g->n_raw, g->is_min, g->node_raw, fitness_raw,
+            static_cast<const double *>(ranks), th, w.partials);
     else
         k_cp_partial<float><<<nblocks, kCpThreads, 0, stream>>>(
-            g->n_nodes, g->is_min, g->node_raw, fitness_raw, static_cast<const float *>(ranks), th,
-            w.partials);
+            g->n_nodes, g->n_raw, g->is_min, g->node_raw, fitness_raw,
+            static_cast<const float *>(ranks), th, w.partials);
     FFG_TRY(check_launch("k_cp_partial"));
     k_cp_final<<<1, 32 * std::min(n_p + 1, 32), 0, stream>>>(w.partials, nblocks, n_p, w.buckets);
     count_launch(2);
@@ -227,7 +230,7 @@ struct CpJobDev {
     const int64_t *node_raw;
     const double *fit;
     const void *ranks;
-    int64_t n;
+    int64_t n, n_raw;
 };
 
 struct CpBatchWs {
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_fopt_batch(const CpJobDev *__
     unsigned long long m = ~0ULL;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < J.n; v += stride)
-        if (J.is_min[v]) {
+        if (J.is_min[v] && FFG_CHECK(J.node_raw[v] >= 0 && J.node_raw[v] < J.n_raw, 501)) {
             const unsigned long long b = ordered_bits(J.fit[J.node_raw[v]]);
             m = b < m ? b : m;
         }
@@ -313,6 +316,7 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_partial_batch(
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < J.n; v += stride) {
         if (!J.is_min[v]) continue;
+        if (!FFG_CHECK(J.node_raw[v] >= 0 && J.node_raw[v] < J.n_raw, 501)) continue;
         const double f = J.fit[J.node_raw[v]];
         int b = 0;
         while (b < n_p && !(f <= s_th.thr[b])) ++b;
@@ -432,6 +436,7 @@ extern "C" ffg_status centrality_batch_plan(const ffg_cp_job *jobs, int32_t n_jo
         jd[j].fit = jobs[j].fitness_raw;
         jd[j].ranks = jobs[j].ranks;
         jd[j].n = g->n_nodes;
+        jd[j].n_raw = g->n_raw;
     }
     FFG_TRY(check_cuda(cudaMemcpyAsync(w.jobs, jd.data(), sizeof(CpJobDev) * n_jobs,
                                        cudaMemcpyHostToDevice, stream), "upload jobs"));
@@ -527,11 +532,12 @@ __global__ void k_min_flags(const uint8_t *__restrict__ is_min, int64_t n, int32
 __global__ void k_min_emit(const uint8_t *__restrict__ is_min,
                            const int64_t *__restrict__ node_raw,
                            const double *__restrict__ fit, const int64_t *__restrict__ pos,
-                           int64_t n, double f_opt, double *frac, int64_t *node) {
+                           int64_t n, int64_t n_raw, double f_opt, double *frac, int64_t *node) {
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
          v += int64_t(gridDim.x) * blockDim.x) {
         if (!is_min[v]) continue;
         const int64_t k = pos[v];
+        if (!FFG_CHECK(node_raw[v] >= 0 && node_raw[v] < n_raw, 502)) continue;
         frac[k] = f_opt / fit[node_raw[v]];
         if (node) node[k] = v;
     }
@@ -576,7 +582,11 @@ extern "C" ffg_status minima_fraction(const ffg_graph *g, const double *fitness_
     FFG_TRY(check_launch("k_min_flags"));
     FFG_TRY(scan_exclusive(flag, pos, n, scratch, stream));
     k_min_emit<<<min_grid(n), 256, 0, stream>>>(g->is_min, g->node_raw, fitness_raw, pos, n,
-                                                g->f_opt, frac, node);
+                                                g->n_raw, g->f_opt, frac, node);
     count_launch();
     return check_launch("k_min_emit");
 }
+
+namespace ffg {
+FFG_CHECK_READER(check_read_centrality)
+}  // namespace ffg

@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(kDagThreads) k_dag(DagArgs a) {
                 double term = 0.0;
                 if (b + lane < e1) {
                     const int32_t u = a.in_idx[b + lane];
-                    term = __ddiv_rn(__ldcg(a.y + u), static_cast<double>(a.outdeg[u]));
+                    if (FFG_CHECK(u >= 0 && u < n, 301))
+                        term = __ddiv_rn(__ldcg(a.y + u), static_cast<double>(a.outdeg[u]));
                 }
                 const int m = e1 - b < 32 ? static_cast<int>(e1 - b) : 32;
                 for (int k = 0; k < m; ++k) s = __dadd_rn(s, __shfl_sync(0xffffffffu, term, k));
@@ -191,7 +192,8 @@ __global__ void __launch_bounds__(kDagThreads) k_dag(DagArgs a) {
                 bool ready = false;
                 if (b + lane < o1) {
                     t = a.out_idx[b + lane];
-                    ready = atomicSub(&a.w.remaining[t], 1) == 1;
+                    ready = FFG_CHECK(t >= 0 && t < n, 302) &&
+                            atomicSub(&a.w.remaining[t], 1) == 1;
                 }
                 const unsigned mask = __ballot_sync(0xffffffffu, ready);
                 if (mask) {
@@ -316,3 +318,7 @@ extern "C" ffg_status dag_solve(const ffg_graph *g, double damping, ffg_dag_mode
     }
     return FFG_OK;
 }
+
+namespace ffg {
+FFG_CHECK_READER(check_read_dag)
+}  // namespace ffg

@@ -31,6 +31,55 @@ ffg_status check_cuda(cudaError_t e, const char *what);
     } while (0)
 
 // ---------------------------------------------------------------------------
+// bounds-checked builds (-DFFG_CHECKED)
+// Every index a kernel derives from caller data (a CSR entry, a descriptor
+// offset, a row pointer) is checked before the access it guards; a failed
+// check skips the access and records its site code in a word of the
+// translation unit, which ffg_checked_failures() reads.  Normal builds
+// compile the checks away (FFG_CHECK is `true`).
+// ---------------------------------------------------------------------------
+#ifdef FFG_CHECKED
+static __device__ unsigned long long g_check_code;   // first failed site, 0 if none
+static __device__ unsigned long long g_check_count;  // failed checks
+__device__ __forceinline__ bool ffg_check(bool ok, unsigned code) {
+    if (!ok) {
+        atomicCAS(&g_check_code, 0ULL, static_cast<unsigned long long>(code));
+        atomicAdd(&g_check_count, 1ULL);
+    }
+    return ok;
+}
+#define FFG_CHECK(cond, code) ffg::ffg_check((cond), (code))
+// this translation unit's words (host side; reset clears them)
+static inline void check_read_tu(unsigned long long *code, unsigned long long *count,
+                                 bool reset) {
+    cudaMemcpyFromSymbol(code, g_check_code, sizeof(*code));
+    cudaMemcpyFromSymbol(count, g_check_count, sizeof(*count));
+    if (reset) {
+        const unsigned long long z = 0;
+        cudaMemcpyToSymbol(g_check_code, &z, sizeof(z));
+        cudaMemcpyToSymbol(g_check_count, &z, sizeof(z));
+    }
+}
+#define FFG_CHECK_READER(name)                                                         \
+    void name(unsigned long long *code, unsigned long long *count, bool reset) {       \
+        check_read_tu(code, count, reset);                                            \
+    }
+#else
+#define FFG_CHECK(cond, code) true
+#define FFG_CHECK_READER(name)                                                         \
+    void name(unsigned long long *code, unsigned long long *count, bool) {             \
+        *code = 0;                                                                    \
+        *count = 0;                                                                   \
+    }
+#endif
+// the readers of the translation units with checks
+void check_read_build(unsigned long long *, unsigned long long *, bool);
+void check_read_pagerank(unsigned long long *, unsigned long long *, bool);
+void check_read_dag(unsigned long long *, unsigned long long *, bool);
+void check_read_walk(unsigned long long *, unsigned long long *, bool);
+void check_read_centrality(unsigned long long *, unsigned long long *, bool);
+
+// ---------------------------------------------------------------------------
 // device copy of a search space (passed to kernels by value)
 // ---------------------------------------------------------------------------
 struct DevClause {

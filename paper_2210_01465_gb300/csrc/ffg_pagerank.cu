@@ -128,7 +128,7 @@ struct PrCtl {
 struct PrWs {
     PrCtl *ctl;
     void *w0, *w1;
-    double *rinv;         // 1 / outdeg per row (FP32: as floats)
+    double *rinv;         // FP64: 1 / outdeg per row
     uint2 *desc;          // tile descriptors (off, mask)
     int32_t *cnt;         // per tile: descriptors, padded to a multiple of kU
     uint2 *tinfo;         // per tile: (first descriptor / kU, cnt)
@@ -160,8 +160,7 @@ PrWs carve(void *base, int64_t n, int64_t e, ffg_prec prec) {
     w.ctl = c.take<PrCtl>(1);
     w.w0 = c.take<char>(size_t(n) * w_bytes(prec));
     w.w1 = c.take<char>(size_t(n) * w_bytes(prec));
-    w.rinv = prec == FFG_F64 ? c.take<double>(size_t(n))
-                             : reinterpret_cast<double *>(c.take<float>(size_t(n)));
+    w.rinv = prec == FFG_F64 ? c.take<double>(size_t(n)) : nullptr;
     w.desc = c.take<uint2>(size_t(desc_capacity(n, e)));
     w.cnt = c.take<int32_t>(size_t((n + 31) / 32));
     w.tinfo = c.take<uint2>(size_t((n + 31) / 32));
@@ -425,12 +424,19 @@ __device__ void layout_tile(const int64_t *__restrict__ in_ptr,
     const int32_t row = static_cast<int32_t>(row0 + vi);  // global row, < 2^31
     int32_t head = cur < end ? __ldg(in_idx + cur) - row : INT32_MAX;
     int k = 0;
+#ifdef FFG_CHECKED
+    // the tile's room: one descriptor per in-edge plus the padding
+    int64_t room = end - cur;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) room += __shfl_xor_sync(0xffffffffu, room, o);
+    room += kU;
+#endif
     while (true) {
         const int32_t m = __reduce_min_sync(0xffffffffu, head);
         if (m == INT32_MAX) break;
         const bool hit = head == m;
         const unsigned mask = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) out[k] = make_uint2(static_cast<uint32_t>(m), mask);
+        if (lane == 0 && FFG_CHECK(k < room, 102)) out[k] = make_uint2(static_cast<uint32_t>(m), mask);
         ++k;
         if (hit) {
             ++cur;
@@ -438,7 +444,7 @@ __device__ void layout_tile(const int64_t *__restrict__ in_ptr,
         }
     }
     const int padded = (k + kU - 1) / kU * kU;
-    if (k + lane < padded) out[k + lane] = make_uint2(0u, 0u);
+    if (k + lane < padded && FFG_CHECK(k + lane < room, 102)) out[k + lane] = make_uint2(0u, 0u);
     if (lane == 0) {
         cnt[t] = padded;
         tinfo[t] = make_uint2(static_cast<uint32_t>(dbeg / kU), static_cast<uint32_t>(padded));
@@ -561,48 +567,26 @@ template <typename T>
 struct Rows;
 
 template <>
-#ifndef FFG_PR_RCP32
-#define FFG_PR_RCP32 0
-#endif
-template <>
 struct Rows<float> {
     using Real = float;
     using W = float;
-#if FFG_PR_RCP32
-    // the correctly rounded reciprocal of the out-degree, formed once per
-    // solve by the prologue (the array `rinv` then holds floats)
-    struct Extra {
-        float r;
-    };
-    __device__ static void store_rinv(double *rinv, int64_t v, int od) {
-        reinterpret_cast<float *>(rinv)[v] = od ? __frcp_rn(static_cast<float>(od)) : 1.0f;
-    }
-    __device__ static void load_extra(Extra &e, const double *rinv, int v) {
-        e.r = v >= 0 ? reinterpret_cast<const float *>(rinv)[v] : 1.0f;
-    }
-    __device__ static float recip(const Extra &e, int) { return e.r; }
-#else
     struct Extra {};
-    __device__ static void store_rinv(double *, int64_t, int) {}
-    __device__ static void load_extra(Extra &, const double *, int) {}
-    __device__ static float recip(const Extra &, int od) {
-        return __frcp_rn(static_cast<float>(od));
-    }
-#endif
     __device__ static W init(double x0, int od) { return static_cast<float>(od ? x0 / od : x0); }
+    __device__ static void store_rinv(double *, int64_t, int) {}
     __device__ static double x_of(W w, int od) {
         return od ? static_cast<double>(w) * od : static_cast<double>(w);
     }
     __device__ static long long fix_x(W w, int od) { return to_fix(x_of(w, od)); }
+    __device__ static void load_extra(Extra &, const double *, int) {}
     // x' = alpha*s + c from the row's in-sum; w' = x'/outdeg as x' times the
     // correctly rounded reciprocal (two roundings, no division sequence)
-    __device__ static void update(float s, float a, float c, int od, W wold, const Extra &e,
+    __device__ static void update(float s, float a, float c, int od, W wold, const Extra &,
                                   W *dst, Fix3 &f) {
         const float xo = od ? wold * static_cast<float>(od) : wold;
         const float xn = a * s + c;
         f.r += to_fix(xn > xo ? xn - xo : xo - xn);
         if (od == 0) f.d += to_fix(xn);
-        *dst = od ? xn * recip(e, od) : xn;
+        *dst = od ? xn * __frcp_rn(static_cast<float>(od)) : xn;
     }
 };
 
@@ -730,16 +714,24 @@ struct Stream {
     }
 };
 
+// The lane has an in-edge at offset `off` of descriptor mask `mask`; in a
+// bounds-checked build the gather must also stay inside w: gb = [lo, hi) of
+// the offsets that do, for this lane's row.
+__device__ __forceinline__ bool take(uint32_t mask, uint32_t bit, uint32_t off, int2 gb) {
+    return (mask & bit) &&
+           FFG_CHECK(static_cast<int32_t>(off) >= gb.x && static_cast<int32_t>(off) < gb.y, 101);
+}
+
 // N descriptors (q: N/2 pairs, the same for every lane): the sum of this
 // lane's gathers, added pairwise.
 template <typename T, int N>
-__device__ __forceinline__ T gather_step(const uint4 *q, const T *wrow, uint32_t bit) {
+__device__ __forceinline__ T gather_step(const uint4 *q, const T *wrow, uint32_t bit, int2 gb) {
     T v[N];
 #pragma unroll
     for (int j = 0; j < N / 2; ++j) {
         const uint4 d = q[j];  // two descriptors, read by broadcast
-        v[2 * j] = (d.y & bit) ? wrow[static_cast<int32_t>(d.x)] : T(0);
-        v[2 * j + 1] = (d.w & bit) ? wrow[static_cast<int32_t>(d.z)] : T(0);
+        v[2 * j] = take(d.y, bit, d.x, gb) ? wrow[static_cast<int32_t>(d.x)] : T(0);
+        v[2 * j + 1] = take(d.w, bit, d.z, gb) ? wrow[static_cast<int32_t>(d.z)] : T(0);
     }
 #pragma unroll
     for (int h = N / 2; h > 0; h >>= 1)  // depth log2(N)
@@ -758,8 +750,8 @@ template <>
 struct Accum<float> {
     float s = 0.f;
     template <int N>
-    __device__ __forceinline__ void step(const uint4 *q, const float *wrow, uint32_t bit) {
-        s += gather_step<float, N>(q, wrow, bit);
+    __device__ __forceinline__ void step(const uint4 *q, const float *wrow, uint32_t bit, int2 gb) {
+        s += gather_step<float, N>(q, wrow, bit, gb);
     }
     __device__ __forceinline__ float value() const { return s; }
 };
@@ -768,13 +760,14 @@ template <>
 struct Accum<double> {
     Fx s{0ULL, 0ULL};
     template <int N>
-    __device__ __forceinline__ void step(const uint4 *q, const double *wrow, uint32_t bit) {
+    __device__ __forceinline__ void step(const uint4 *q, const double *wrow, uint32_t bit,
+                                         int2 gb) {
         double v[N];
 #pragma unroll
         for (int j = 0; j < N / 2; ++j) {
             const uint4 d = q[j];
-            v[2 * j] = (d.y & bit) ? wrow[static_cast<int32_t>(d.x)] : 0.0;
-            v[2 * j + 1] = (d.w & bit) ? wrow[static_cast<int32_t>(d.z)] : 0.0;
+            v[2 * j] = take(d.y, bit, d.x, gb) ? wrow[static_cast<int32_t>(d.x)] : 0.0;
+            v[2 * j + 1] = take(d.w, bit, d.z, gb) ? wrow[static_cast<int32_t>(d.z)] : 0.0;
         }
 #pragma unroll
         for (int j = 0; j < N; ++j) s = fx_add(s, fx_of(v[j]));
@@ -786,13 +779,14 @@ template <>
 struct Accum<F64x> {
     Fx s{0ULL, 0ULL};
     template <int N>
-    __device__ __forceinline__ void step(const uint4 *q, const Fx *wrow, uint32_t bit) {
+    __device__ __forceinline__ void step(const uint4 *q, const Fx *wrow, uint32_t bit, int2 gb) {
         Fx v[N];
 #pragma unroll
         for (int j = 0; j < N / 2; ++j) {
             const uint4 d = q[j];
-            v[2 * j] = (d.y & bit) ? wrow[static_cast<int32_t>(d.x)] : Fx{0ULL, 0ULL};
-            v[2 * j + 1] = (d.w & bit) ? wrow[static_cast<int32_t>(d.z)] : Fx{0ULL, 0ULL};
+            v[2 * j] = take(d.y, bit, d.x, gb) ? wrow[static_cast<int32_t>(d.x)] : Fx{0ULL, 0ULL};
+            v[2 * j + 1] = take(d.w, bit, d.z, gb) ? wrow[static_cast<int32_t>(d.z)]
+                                                   : Fx{0ULL, 0ULL};
         }
 #pragma unroll
         for (int j = 0; j < N; ++j) s = fx_add(s, v[j]);
@@ -808,8 +802,8 @@ struct Accum<F64x> {
 template <typename T>
 __device__ __forceinline__ bool tile_sum(const uint2 *dcur, int cnt, const uint2 *dnxt, int ncnt,
                                          bool next_any, Stream &st,
-                                         const typename Rows<T>::W *wrow, uint32_t bit, int lane,
-                                         typename Rows<T>::Real &sum) {
+                                         const typename Rows<T>::W *wrow, uint32_t bit, int2 gb,
+                                         int lane, typename Rows<T>::Real &sum) {
     const int nseg = (cnt + kSegD - 1) / kSegD;
     Accum<T> acc;
     for (int sg = 0; sg < nseg; ++sg) {
@@ -830,9 +824,9 @@ __device__ __forceinline__ bool tile_sum(const uint2 *dcur, int cnt, const uint2
         const uint4 *q = reinterpret_cast<const uint4 *>(st.stage + st.buf * kSegD);
         constexpr int kS = Step<T>::value;
         int k = 0;
-        for (; k + kS <= m; k += kS) acc.template step<kS>(q + (k >> 1), wrow, bit);
+        for (; k + kS <= m; k += kS) acc.template step<kS>(q + (k >> 1), wrow, bit, gb);
         if (kS > kU)
-            for (; k < m; k += kU) acc.template step<kU>(q + (k >> 1), wrow, bit);
+            for (; k < m; k += kU) acc.template step<kU>(q + (k >> 1), wrow, bit, gb);
         st.buf ^= 1;
     }
     if (nseg == 0 && !st.issued && next_any) {
@@ -847,10 +841,16 @@ __device__ __forceinline__ bool tile_sum(const uint2 *dcur, int cnt, const uint2
 template <typename T>
 __device__ __forceinline__ bool tile_sum(const uint2 *__restrict__ desc, const TileInfo<T> &cur,
                                          const TileInfo<T> &nxt, bool has_next, Stream &st,
-                                         const typename Rows<T>::W *wrow, uint32_t bit, int lane,
-                                         typename Rows<T>::Real &sum) {
+                                         const typename Rows<T>::W *wrow, uint32_t bit, int2 gb,
+                                         int lane, typename Rows<T>::Real &sum) {
     return tile_sum<T>(desc + size_t(cur.d8) * kU, cur.cnt, desc + size_t(nxt.d8) * kU, nxt.cnt,
-                       has_next && nxt.cnt > 0, st, wrow, bit, lane, sum);
+                       has_next && nxt.cnt > 0, st, wrow, bit, gb, lane, sum);
+}
+
+// the offsets whose gather stays inside w (n rows) for row v (bounds checks)
+__device__ __forceinline__ int2 gather_bounds(int64_t v, int64_t n) {
+    return v < 0 ? make_int2(0, 0)
+                 : make_int2(static_cast<int>(-v), static_cast<int>(n - v));
 }
 
 // First tile of part w when the tiles are split into nw contiguous ranges of
@@ -886,7 +886,7 @@ struct JobDev {
     const uint2 *desc;
     const uint2 *tinfo;
     const int32_t *perm;
-    double *rinv;  // 1 / outdeg per row (FP32: as floats), written by the prologue
+    double *rinv;  // FP64: 1 / outdeg per row, written by the prologue
     const int64_t *tpre;
     const int64_t *apre;  // rows with in-edges: apre[n] - apre[0]
     void *ranks, *w0, *w1;
@@ -1030,7 +1030,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
                 const int v = cur.v;
                 R s = R(0);
                 if (!tile_sum<T>(desc, cur, nxt, has_next, st, wc + (v < 0 ? 0 : v), 1u << lane,
-                                 lane, s)) {
+                                 gather_bounds(v, n), lane, s)) {
                     failed = 1;
                     break;
                 }
@@ -1670,7 +1670,8 @@ __global__ void __launch_bounds__(32 * W, 1) k_pagerank_sweep(const SweepArgs A)
             const bool next_tile = u1.kind == 1 && nxt.cnt > 0;
             const uint2 *dn = next_tile ? sjd[u1.job].desc + size_t(nxt.d8) * kU : nullptr;
             if (!tile_sum<T>(J0.desc + size_t(cur.d8) * kU, cur.cnt, dn, next_tile ? nxt.cnt : 0,
-                             next_tile, st, wc + (v < 0 ? 0 : v), 1u << lane, lane, sum)) {
+                             next_tile, st, wc + (v < 0 ? 0 : v), 1u << lane,
+                             gather_bounds(v, J0.n), lane, sum)) {
                 failed = true;
                 break;
             }
@@ -2025,6 +2026,7 @@ struct RowsDev {
     unsigned long long *sums;
     ffg_rows_ctl *ctl;      // the solve's state: dangling mass, scale, decisions
     int64_t n, n_all;       // rows of the range, of the graph
+    int64_t row0;           // the range's first row
     double alpha;
 };
 
@@ -2092,7 +2094,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_rows_step(const RowsDev R) {
             const int v = cur.v;
             Rr sum = Rr(0);
             if (!tile_sum<T>(R.desc, cur, nxt, has_next, st, wc + (v < 0 ? 0 : v), 1u << lane,
-                             lane, sum)) {
+                             gather_bounds(v < 0 ? v : R.row0 + v, R.n_all), lane, sum)) {
                 failed = true;
                 break;
             }
@@ -2331,6 +2333,7 @@ extern "C" ffg_status pagerank_rows_run(const ffg_graph *g, int64_t row0, int64_
     R.rinv = w.rinv;
     R.n = n;
     R.n_all = g->n_nodes;
+    R.row0 = row0;
     R.alpha = op->damping;
     R.ctl = op->ctl;
     R.sums = sums;
@@ -2592,9 +2595,7 @@ BatchWs carve_batch(void *base, const ffg_pr_job *jobs, int n_jobs, ffg_prec pre
         J.ranks = jobs[j].ranks;
         J.w0 = c.take<char>(size_t(g->n_nodes) * w_bytes(prec));
         J.w1 = c.take<char>(size_t(g->n_nodes) * w_bytes(prec));
-        J.rinv = prec == FFG_F64
-                     ? c.take<double>(size_t(g->n_nodes))
-                     : reinterpret_cast<double *>(c.take<float>(size_t(g->n_nodes)));
+        J.rinv = prec == FFG_F64 ? c.take<double>(size_t(g->n_nodes)) : nullptr;
         J.ctl = w.ctl + j;
         J.n = g->n_nodes;
         J.alpha = jobs[j].damping;
@@ -2988,3 +2989,7 @@ extern "C" ffg_status pagerank_batch_times(const ffg_pr_batch *plan, double *blo
     for (int j = 0; j < plan->n_jobs; ++j) block_seconds_out[j] = 1e-9 * double(h[j].busy_ns);
     return FFG_OK;
 }
+
+namespace ffg {
+FFG_CHECK_READER(check_read_pagerank)
+}  // namespace ffg

@@ -58,6 +58,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walks(const int64_t *__restric
             ++k;
             const uint64_t i = pick(splitmix64(s0 + k * kGamma), static_cast<uint64_t>(d));
             v = __ldg(out_idx + __ldg(out_ptr + v) + static_cast<int64_t>(i));
+            if (!FFG_CHECK(v >= 0 && v < n, 401)) {
+                ok = false;
+                break;
+            }
             d = __ldg(outdeg + v);
         }
         if (ok) atomicAdd(counts + v, 1ULL);
@@ -117,3 +121,7 @@ extern "C" ffg_status walk_simulate(const ffg_graph *g, uint64_t seed, int64_t n
     }
     return FFG_OK;
 }
+
+namespace ffg {
+FFG_CHECK_READER(check_read_walk)
+}  // namespace ffg

@@ -37,6 +37,21 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_checked_build_exports_the_same_symbols(lib):
+    """The bounds-checked variant (-DFFG_CHECKED) builds, exports the same
+    entry points and says which build it is; with no kernel run it has
+    recorded no failed check (reading its record needs the GPU, so only the
+    flag is read here)."""
+    path = ffg.build(checked=True)
+    chk = C.CDLL(path)
+    for name in _declared_functions():
+        assert hasattr(chk, name), name
+    chk.ffg_checked_build.restype = C.c_int
+    assert chk.ffg_checked_build() == 1
+    assert lib.ffg_checked_build() == 0
+    assert not ffg.ffg_checked_build()
+
+
 def test_status_strings(lib):
     for s in range(8):
         assert ffg.ffg_status_str(s) not in ("", "unknown status")
