@@ -409,7 +409,7 @@ def autotune_summary(batch, tuned):
     a perfectly balanced schedule of the same per-job work would take."""
     best, tried = tuned
     busy = batch.times()
-    return {"chosen (split/grain/max_blocks/block_warps/claim)":
+    return {"chosen (split/grain/max_blocks/block_warps/claim[/fp64_form/min_tiles])":
             "/".join(map(str, best)) + ("+measured" if batch.job_cost is not None else ""),
             "ms_per_candidate": tried,
             "balanced_ms": 1e3 * float(busy.sum()) / batch.plan.n_blocks}

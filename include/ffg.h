@@ -426,9 +426,9 @@ size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs, ff
  *   block runs its multi-block ranks in one global order (largest job
  *   first), then its one-block jobs (longest first onto the least loaded
  *   block), so a group only waits for blocks busy with an earlier job;
- * - claim order: the ranks of multi-block jobs (at most one per block)
- *   first, then the one-block jobs longest first; a block takes the next
- *   unclaimed item whenever it is free.
+ * - claim order: every job's ranks as consecutive items, longest job
+ *   first; a block takes the next unclaimed item whenever it is free, and a
+ *   group starts when its last rank is taken.
  * Carves the workspace and uploads the tables.  Synchronises `stream`. */
 ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec prec,
                                void *workspace, size_t ws_bytes, ffg_pr_batch *plan,
@@ -443,16 +443,20 @@ ffg_status pagerank_batch_plan(const ffg_pr_job *jobs, int32_t n_jobs, ffg_prec 
  * jobs (its job table then travels in the kernel's parameters), else 16;
  * `claim` 1 selects the claim order, 0 the per-block lists; `fp64_form`
  * (FFG_F64 only) keeps w as exact 128-bit fixed point (1) or as double (2),
- * 0 = fixed point when every graph has at most 2^21 nodes.  `job_cost` (HOST, n_jobs positive finite
+ * 0 = fixed point when every graph has at most 2^21 nodes; `min_tiles`
+ * caps a job's group so that each warp of it has at least that many tiles
+ * per iteration (0 or 1: one tile; larger values keep medium jobs on fewer
+ * blocks, where the per-iteration barrier would cost more than the work it
+ * spreads).  `job_cost` (HOST, n_jobs positive finite
  * values in any one unit, or NULL) replaces the cost model (edges + 20 x
  * nodes, times an iteration estimate from the damping) that sizes the groups
  * and balances the blocks, e.g. with the block-seconds that
  * pagerank_batch_times measured on an earlier run; it is read during the
- * call only.  pagerank_batch_plan uses 0.05, 0.005, 0, 0, 0, 0, NULL.
+ * call only.  pagerank_batch_plan uses 0.05, 0.005, 0, 0, 0, 0, 0, NULL.
  * They change only the schedule, never results or the workspace size. */
 typedef struct {
     double split, grain;
-    int32_t max_blocks, block_warps, claim, fp64_form;
+    int32_t max_blocks, block_warps, claim, fp64_form, min_tiles, reserved;
     const double *job_cost;
 } ffg_pr_tuning;
 

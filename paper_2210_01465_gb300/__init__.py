@@ -99,6 +99,7 @@ class ffg_build_batch(C.Structure):
 class ffg_pr_tuning(C.Structure):
     _fields_ = [("split", C.c_double), ("grain", C.c_double), ("max_blocks", C.c_int32),
                 ("block_warps", C.c_int32), ("claim", C.c_int32), ("fp64_form", C.c_int32),
+                ("min_tiles", C.c_int32), ("reserved", C.c_int32),
                 ("job_cost", C.POINTER(C.c_double))]
 
 
@@ -341,12 +342,13 @@ def pagerank_batch_plan(jobs, prec: int, ws: int, ws_bytes: int, plan: "ffg_pr_b
 
 def pagerank_batch_plan_tuned(jobs, prec: int, tuning, ws: int, ws_bytes: int,
                               plan: "ffg_pr_batch", stream: int = 0, job_cost=None) -> int:
-    """``tuning``: (split, grain, max_blocks[, block_warps[, claim[, fp64_form]]]);
-    ``job_cost``: per-job costs replacing the cost model (or None)."""
+    """``tuning``: (split, grain, max_blocks[, block_warps[, claim[, fp64_form[,
+    min_tiles]]]]]); ``job_cost``: per-job costs replacing the cost model (or None)."""
     t = ffg_pr_tuning(float(tuning[0]), float(tuning[1]), int(tuning[2]),
                       int(tuning[3]) if len(tuning) > 3 else 0,
                       int(tuning[4]) if len(tuning) > 4 else 0,
-                      int(tuning[5]) if len(tuning) > 5 else 0)
+                      int(tuning[5]) if len(tuning) > 5 else 0,
+                      int(tuning[6]) if len(tuning) > 6 else 0)
     cost = None
     if job_cost is not None:
         cost = np.ascontiguousarray(job_cost, dtype=np.float64)
@@ -831,7 +833,8 @@ class PageRankBatch:
 
     def replan(self, tuning, stream=None, job_cost=None):
         """Re-plan into the same workspace with (split, grain, max_blocks[, block_warps[,
-        claim[, fp64_form]]]), and per-job costs in place of the model if given."""
+        claim[, fp64_form[, min_tiles]]]]), and per-job costs in place of the model if
+        given."""
         _check(pagerank_batch_plan_tuned(self.jobs, self.prec, tuning, self.ws.data_ptr(),
                                          self.need, self.plan, _stream_handle(stream),
                                          job_cost=job_cost),

@@ -6,9 +6,12 @@ workload is the schedule of a batch: which jobs get dedicated blocks
 (`split`), how many (`grain`), how large the grid is (`max_blocks`) and how
 wide its blocks are (`block_warps`: 8 warps, several blocks per SM; 16, one
 block per SM with room for every job pointer in registers; or 24, one block
-per SM) and the order (`claim`): fixed per-block lists, blocks claiming
+per SM), the order (`claim`): fixed per-block lists, blocks claiming
 jobs as they free up, or the sweep, where every job advances one step per
-phase on the whole grid.  ``tune`` runs the batch once per candidate (same
+phase on the whole grid, and the least work per warp of a group
+(`min_tiles`: more blocks share a job's rows, which keeps each block's
+gathers closer together in its L1, but every block of the group pays the
+per-iteration barrier).  ``tune`` runs the batch once per candidate (same
 workspace, re-planned), times it with CUDA events and leaves the fastest
 plan in place.
 
@@ -27,7 +30,7 @@ import os
 
 import numpy as np
 
-# (split, grain, max_blocks, block_warps, claim)
+# (split, grain, max_blocks, block_warps, claim[, fp64_form, min_tiles])
 CANDIDATES = (
     (1.0, 1.0, 0, 8, 0),
     (0.5, 0.25, 0, 8, 0),
@@ -39,7 +42,10 @@ CANDIDATES = (
     (0.5, 0.1, 0, 24, 0),
     (0.1, 0.02, 0, 24, 0),
     (0.05, 0.005, 0, 24, 0),
-    (0.5, 0.5, 0, 24, 1),
+    (0.02, 0.002, 0, 24, 0, 0, 8),
+    (0.05, 0.005, 0, 24, 1, 0, 4),
+    (0.02, 0.002, 0, 24, 1, 0, 8),
+    (0.01, 0.001, 0, 24, 1, 0, 4),
     (1.0, 1.0, 0, 24, 2),
     (1.0, 1.0, 0, 16, 2),
 )
@@ -64,7 +70,7 @@ def _time(batch, reps):
 def tune(batch, candidates=CANDIDATES, reps: int = 1, table_path: str | None = None,
          measured: int = MEASURED):
     """Pick the fastest schedule for ``batch`` (a PageRankBatch); returns
-    (best (split, grain, max_blocks, block_warps, claim), {candidate: ms}).
+    (best candidate tuple, {candidate: ms}).
     Candidates re-planned with measured job costs are keyed with a
     ``+measured`` suffix; the chosen plan's costs stay in ``batch.job_cost``."""
     times, costs = {}, {}
@@ -88,8 +94,9 @@ def tune(batch, candidates=CANDIDATES, reps: int = 1, table_path: str | None = N
             with open(table_path) as fh:
                 table = json.load(fh)
         table[key] = {"split": best[0], "grain": best[1], "max_blocks": best[2],
-                      "block_warps": best[3], "claim": best[4], "measured_costs": use_cost,
-                      "ms": times[best_key]}
+                      "block_warps": best[3], "claim": best[4],
+                      "min_tiles": best[6] if len(best) > 6 else 0,
+                      "measured_costs": use_cost, "ms": times[best_key]}
         with open(table_path, "w") as fh:
             json.dump(table, fh, indent=1)
     return best, {"/".join(map(str, c)) + ("+measured" if m else ""): round(t, 3)

@@ -1137,10 +1137,12 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
 // - lists (queue == nullptr): block b runs items [first[b], first[b+1]),
 //   its multi-block rank (if any) first, so no two groups wait on each other;
 // - claims: the blocks claim the items in order through a counter (`queue`,
-//   zero at launch).  The ranks of every multi-block job come first and
-//   number at most the grid size, so when all blocks wait at group barriers
-//   every multi-block rank has been claimed and no group waits forever;
-//   one-block jobs follow, longest first, and go to whichever block is free.
+//   zero at launch), a job's ranks being consecutive items, and a block runs
+//   its item to the end before it claims another.  So at most one group --
+//   the last one claimed -- can be short of ranks: every other group has all
+//   of its ranks running and completes, and its blocks then claim the
+//   missing ranks (a group has at most as many ranks as the grid has
+//   blocks).  No group waits forever.
 // shared memory: per-warp stages, then mbarriers
 template <int W>
 __device__ __forceinline__ Stream make_stream(unsigned char *s_dyn) {
@@ -2444,13 +2446,12 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, int warps,
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     P.group.assign(n_jobs, 1);
     P.items.clear();
-    // Claim order: the multi-block ranks all fit in the grid (sum k <= nb).
+    // Claim order: every job's ranks, consecutive, longest job first.
     // Lists: a block may hold ranks of several multi-block jobs; every block
     // runs them in the same global order (largest job first), then its
     // one-block jobs, so a group only ever waits for blocks busy with an
     // earlier job and the first job in the order always completes.  A job's
     // ranks go to the k least loaded blocks.
-    int used = 0;  // claim order: ranks of multi-block jobs so far
     std::vector<int> small;
     std::vector<std::vector<int2>> per_block(nb);
     std::vector<double> load(nb, 0.0);
@@ -2461,18 +2462,19 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, int warps,
         int k = cost[j] > tu.split * share
                     ? static_cast<int>(std::llround(cost[j] / (tu.grain * share)))
                     : 1;
-        k = static_cast<int>(std::min<int64_t>(k, std::max<int64_t>(1, tiles / warps)));
-        k = std::min(k, P.claim ? nb - used : nb);
+        const int64_t per_rank = int64_t(warps) * std::max(1, tu.min_tiles);
+        k = static_cast<int>(std::min<int64_t>(k, std::max<int64_t>(1, tiles / per_rank)));
+        k = std::min(k, nb);
+        if (P.claim) {  // every job in cost order, its ranks consecutive
+            P.group[j] = k;
+            for (int r = 0; r < k; ++r) P.items.push_back(make_int2(j, r));
+            continue;
+        }
         if (k < 2) {
             small.push_back(j);
             continue;
         }
         P.group[j] = k;
-        if (P.claim) {
-            for (int r = 0; r < k; ++r) P.items.push_back(make_int2(j, r));
-            used += k;
-            continue;
-        }
         std::iota(by_load.begin(), by_load.end(), 0);
         std::stable_sort(by_load.begin(), by_load.end(),
                          [&](int a, int b) { return load[a] < load[b]; });
@@ -2485,10 +2487,7 @@ ffg_status make_plan(const ffg_pr_job *jobs, int n_jobs, int nb_max, int warps,
         }
     }
     P.first.clear();
-    if (P.claim) {
-        for (int j : small) P.items.push_back(make_int2(j, 0));  // longest first
-        return FFG_OK;
-    }
+    if (P.claim) return FFG_OK;
     // per-block lists: one-block jobs, longest first, onto the least loaded block
     using Slot = std::pair<double, int>;
     std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
@@ -2681,7 +2680,7 @@ ffg_status launch_batch(ffg_prec prec, bool fx, const BatchParams *P, const JobD
 // 0.5 % of a share; the block width follows the size of the job table
 // (0.05 / 0.005 was the best or close to it on both the 234-space batch and
 // the 512-solve sweep)
-const ffg_pr_tuning kDefaultTuning = {0.05, 0.005, 0, 0, 0, 0, nullptr};
+const ffg_pr_tuning kDefaultTuning = {0.05, 0.005, 0, 0, 0, 0, 0, 0, nullptr};
 
 extern "C" size_t pagerank_batch_workspace_bytes(const ffg_pr_job *jobs, int32_t n_jobs,
                                                  ffg_prec prec) {
@@ -2724,10 +2723,10 @@ extern "C" ffg_status pagerank_batch_plan_tuned(const ffg_pr_job *jobs, int32_t 
                                              : kWarpsBatchWide;
     if (!(tu.split > 0.0) || !(tu.grain > 0.0) || tu.max_blocks < 0 || !batch_width_ok(warps) ||
         tu.claim < 0 || tu.claim > 2 || (tu.claim == 2 && warps == kWarpsBatch) ||
-        tu.fp64_form < 0 || tu.fp64_form > 2)
+        tu.fp64_form < 0 || tu.fp64_form > 2 || tu.min_tiles < 0 || tu.min_tiles > (1 << 20))
         return set_error("tuning: split and grain must be > 0, max_blocks >= 0, block_warps "
                          "0, %d, %d or %d, claim 0, 1 or 2 (2 with %d or %d warps), fp64_form "
-                         "0, 1 or 2",
+                         "0, 1 or 2, min_tiles 0..2^20",
                          kWarpsBatch, kWarpsBatchWide, kWarpsSingle, kWarpsBatchWide,
                          kWarpsSingle),
                FFG_ERR_INVALID_ARG;

@@ -402,7 +402,9 @@ def test_batch_tuning_changes_schedule_not_results():
                    (0.1, 0.1, 0, 8), (0.1, 0.1, 0, 8, 1), (0.5, 0.5, 0, 24, 1),
                    (1.0, 1.0, 0, 16), (0.1, 0.02, 0, 16, 0), (0.5, 0.5, 0, 16, 1),
                    (1.0, 1.0, 0, 8, 0, 2), (0.1, 0.02, 0, 24, 0, 2), (0.1, 0.02, 0, 16, 0, 2),
-                   (1.0, 1.0, 0, 24, 2), (1.0, 1.0, 0, 16, 2), (1.0, 1.0, 0, 24, 2, 2)):
+                   (1.0, 1.0, 0, 24, 2), (1.0, 1.0, 0, 16, 2), (1.0, 1.0, 0, 24, 2, 2),
+                   (0.05, 0.005, 0, 24, 1, 0, 4), (0.02, 0.002, 0, 16, 0, 0, 8),
+                   (0.01, 0.001, 0, 8, 1, 2, 2)):
         batch.replan(tuning)
         batch.run()
         it, res, st = batch.query()
