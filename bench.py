@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="headline only: skip the single-space, sweep, DAG and row sub-keys")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one small case for a profiler (two launches of its kernel, the "
+                         "second one measured) and print its sizes; no bench line")
     return ap.parse_args()
 
 
@@ -502,11 +505,12 @@ def run_gpu(args):
     peak, peak_kind = hbm_peak()
     achieved = pr_bytes / (solve_ms / 1e3) / 1e9
     kv = ncu_summary("pagerank_batch_f32_batched_sample.txt")
-    traffic = None
+    traffic = ratio = None
     if kv.get("dram_bytes_per_launch") and kv.get("alg_bytes_per_launch"):
         # the capture ran a reduced batch; its traffic scales with the
         # algorithmic bytes (the same templates, one seed each)
-        traffic = float(kv["dram_bytes_per_launch"]) / float(kv["alg_bytes_per_launch"]) * pr_bytes
+        ratio = float(kv["dram_bytes_per_launch"]) / float(kv["alg_bytes_per_launch"])
+        traffic = ratio * pr_bytes
     tuned = autotune_summary(b, step.tuned)
 
     # plain FP64, one space at a time, on the same graphs
@@ -629,6 +633,15 @@ def run_gpu(args):
                          "traffic_source": "profiles/pagerank_batch_f32_batched_sample.txt "
                                            "(one seed per template), scaled by algorithmic bytes"
                                            if traffic is not None else None,
+                         "traffic_over_alg": ratio,
+                         "dram_gbs": traffic / (solve_ms / 1e3) / 1e9 if traffic else None,
+                         "limiter": "latency and issue: the descriptor layout reads about a "
+                                    "ninth of the CSR model's bytes from DRAM (each job's "
+                                    "working set stays in L2), so the kernel runs at ~50 % "
+                                    "issue, led by fixed-latency, L1/L2 and barrier stalls; "
+                                    "achieved/frac are the model's bytes over the launch time",
+                         "warp_inst_per_edge_iter": float(kv["warp_inst_per_edge_iter"])
+                         if kv.get("warp_inst_per_edge_iter") else None,
                          "algorithmic_bytes": pr_bytes, "launch_ms": solve_ms,
                          "bytes_model": "per solve: iters x (4E + 20N) + 20N (CSR form)"},
             "phases_ms": {"build": build_ms, "layout": layout_ms, "pagerank": solve_ms,
@@ -767,7 +780,12 @@ def run_scale(ffg, fi, dev, stream, reps=3):
         "roofline": {"bound": "hbm", "kernel": "k_pagerank<float>", "achieved": gbs,
                      "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": peak_kind,
                      "frac_of_nominal": gbs / HBM_NOMINAL_GBS, "algorithmic_bytes": alg,
-                     "traffic": traffic, "l2_resident": False},
+                     "traffic": traffic, "l2_resident": False,
+                     "dram_gbs": traffic / (ms / 1e3) / 1e9 if traffic else None,
+                     "traffic_over_alg": traffic / alg if traffic else None,
+                     "traffic_source": "profiles/pagerank_f32_precision_scale.txt "
+                                       "(DRAM bytes per iteration x iterations)"
+                                       if traffic else None},
         "pagerank_f64_ms": ms64, "iters_f64": it64, "us_per_iter_f64": 1e3 * ms64 / it64,
         "f32_vs_f64_rank_l1": float((x32.double() - x64).abs().sum()),
         "cp": list(cp32), "_x": x32.double().cpu().numpy(),
@@ -922,8 +940,96 @@ def run_rows(ffg, g, dev, f64_single, parts=4, reps=3):
         return {"error": f"{type(e).__name__}: {e}"}
 
 
+# --------------------------------------------------------------------------
+# small cases for profilers: each runs its kernel twice (the second launch is
+# the one to capture: ncu -k regex:<kernel> -s 1 -c 1) on a few GB of device
+# memory and prints what the capture is compared with
+# --------------------------------------------------------------------------
+
+def _case_batch_sample(ffg, fi, dev, stream):
+    """One fitness seed of each of the 26 templates (26 spaces, about a ninth
+    of the 234-space batch), Hamming FFGs, FP32, the default plan."""
+    work = [w for w in fi.batch_workload() if w[1] % 100 == 1]
+    spaces = [ffg.Space.from_spec(sp) for sp, _, _ in work]
+    fits = [fi.runtimes_torch(sp, seed, fail, device=dev) for sp, seed, fail in work]
+    builds = ffg.BuildBatch([(sp, f, ffg.HAMMING) for sp, f in zip(spaces, fits)], stream=stream)
+    batch = ffg.PageRankBatch([(g, DAMPING) for g in builds.graphs], prec=ffg.F32, tol=TOL)
+    batch.run(stream=stream)
+    batch.query(stream=stream)
+    batch.solve(stream=stream)
+    it, _, st = batch.query(stream=stream)
+    assert (st == 0).all(), st
+    it = [int(k) for k in it]
+    N = [g.n_nodes for g in builds.graphs]
+    E = [g.n_edges for g in builds.graphs]
+    alg = float(sum(pagerank_bytes(n, e, k, 4) for n, e, k in zip(N, E, it)))
+    return {"kernel": "k_pagerank_batch_p", "spaces": len(work), "nodes": int(sum(N)),
+            "edges": int(sum(E)), "iters_sum": sum(it),
+            "edge_iters": float(sum(e * k for e, k in zip(E, it))), "alg_bytes_per_launch": alg,
+            "blocks": int(batch.plan.n_blocks), "warps": int(batch.plan.warps),
+            "per_job": {"nodes": N, "edges": E, "iters": it}}
+
+
+def _case_single(ffg, fi, dev, stream, spec, prec, name):
+    fd = torch_from(fi.runtimes(spec, seed=1), dev)
+    g = ffg.build_graph(ffg.Space.from_spec(spec), fd, ffg.HAMMING)
+    need = ffg.pagerank_workspace_bytes(g.n_nodes, g.n_edges, prec)
+    ws = ffg.workspace(need, dev)
+    import torch
+    x = torch.empty(g.n_nodes, dtype=torch.float32 if prec == ffg.F32 else torch.float64,
+                    device=dev)
+    sh = stream.cuda_stream
+    assert ffg.pagerank_prepare(g.c, prec, ws.data_ptr(), need, sh) == 0
+    for _ in range(2):
+        st, _, _ = ffg.pagerank_solve(g.c, DAMPING, TOL, 10000, prec, x.data_ptr(),
+                                      ffg.INIT_LAYOUT, ws.data_ptr(), need, sync=False, stream=sh)
+        assert st == 0, st
+    st, it, _ = ffg.pagerank_query(ws.data_ptr(), sh)
+    assert st == 0, st
+    it = int(it)
+    elem = 4 if prec == ffg.F32 else 8
+    return {"kernel": name, "space": spec.name, "nodes": g.n_nodes, "edges": g.n_edges,
+            "iters": it, "alg_bytes_per_launch": float(pagerank_bytes(g.n_nodes, g.n_edges, it,
+                                                                      elem))}
+
+
+def torch_from(a, dev):
+    import torch
+    return torch.from_numpy(a).to(dev)
+
+
+PROFILE_CASES = {
+    "batch_sample": lambda ffg, fi, dev, st: _case_batch_sample(ffg, fi, dev, st),
+    "precision_scale_f32": lambda ffg, fi, dev, st: _case_single(
+        ffg, fi, dev, st, fi.precision_large(), ffg.F32, "k_pagerank<float>"),
+    "single_large_f32": lambda ffg, fi, dev, st: _case_single(
+        ffg, fi, dev, st, fi.single_large(), ffg.F32, "k_pagerank<float>"),
+    "single_large_f64": lambda ffg, fi, dev, st: _case_single(
+        ffg, fi, dev, st, fi.single_large(), ffg.F64, "k_pagerank<F64x>"),
+}
+
+
+def run_profile_case(args):
+    import torch
+    import ffg_inputs as fi
+    import paper_2210_01465_gb300 as ffg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ffg.build()
+    ffg.load()
+    stream = torch.cuda.current_stream(dev)
+    out = PROFILE_CASES[args.profile_case](ffg, fi, dev, stream)
+    torch.cuda.synchronize(dev)
+    out["case"] = args.profile_case
+    out["device_bytes_peak"] = int(torch.cuda.max_memory_allocated(dev))
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
