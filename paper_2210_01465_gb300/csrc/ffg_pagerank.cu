@@ -266,6 +266,42 @@ __device__ bool group_barrier(PrCtl *ctl, unsigned target, int group) {
     return s_ok != 0;
 }
 
+// The same barrier in two halves, for the iteration loop: thread 0 arrives
+// as soon as the block's sums are published (its block barrier has ordered
+// the block's writes before), the block does work that needs no other block
+// (loads for its next tiles), and only then waits.
+__device__ __forceinline__ void group_arrive(PrCtl *ctl, int group) {
+    if (threadIdx.x == 0 && group > 1) red_release_add(&ctl->barrier, 1u);
+}
+__device__ bool group_wait(PrCtl *ctl, unsigned target, int group) {
+    __shared__ int s_ok;
+    if (group == 1) {
+        __syncthreads();
+        return true;
+    }
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = global_ns();
+        unsigned ns = 0;
+        int ok = 1;
+        for (uint32_t polls = 0; ld_acquire(&ctl->barrier) < target; ++polls) {
+            if ((polls & 15) == 15 && *(volatile int *)&ctl->status != 0) { ok = 0; break; }
+            if (polls > (1u << 24) || global_ns() - t0 > kTimeoutNs) {
+                atomicCAS(&ctl->status, 0, (int)FFG_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            if (polls > 64) {
+                __nanosleep(ns);
+                ns = ns < 32 ? 32 : (ns < 256 ? ns << 1 : ns);
+            }
+        }
+        if (*(volatile int *)&ctl->status != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
@@ -1058,10 +1094,18 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
             failed = 2;
         }
         const Fix3 b = block_sum_fix<W>(facc);
-        // The block's rows of w' are written (block barrier above), so the
-        // next iteration's first two tiles -- in this block's range -- load
-        // their row data, and the first one its first descriptor segment,
-        // while the grid barrier completes.  Unused if the solve stops here
+        // The block's rows of w' are written (block barrier above): publish
+        // the sums and arrive at once.
+        buf = buf == 2 ? 0 : buf + 1;
+        if (threadIdx.x == 0) {
+            publish(ctl, buf, b, rank);
+            s_next = static_cast<unsigned>(bt0 + 2 * W);  // next iteration's counter
+        }
+        group_arrive(ctl, nb);
+        ++phase;
+        // While the others arrive, the next iteration's first two tiles --
+        // in this block's range -- load their row data, and the first one
+        // its first descriptor segment.  Unused if the solve stops here
         // (drained below).
         have_pre = false;
         if (t0 < bt1 && !failed) {
@@ -1075,13 +1119,7 @@ __device__ bool run_job(const JobDev &J, int rank, Stream &st) {
             }
             have_pre = true;
         }
-        buf = buf == 2 ? 0 : buf + 1;
-        if (threadIdx.x == 0) {
-            publish(ctl, buf, b, rank);
-            s_next = static_cast<unsigned>(bt0 + 2 * W);  // next iteration's counter
-        }
-        ++phase;
-        if (!group_barrier(ctl, phase * nb, nb)) {
+        if (!group_wait(ctl, phase * nb, nb)) {
             st.drain();
             st.issued = false;
             return false;
