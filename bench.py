@@ -687,6 +687,20 @@ def run_single_large(ffg, fi, dev, stream, reps=5):
     for name, nbh in (("hamming", ffg.HAMMING), ("adjacent", ffg.ADJACENT)):
         g = ffg.build_graph(space, fd, nbh)
         graphs[name] = g
+        # the FFG build alone: count (one read-back of the sizes) + fill into
+        # the graph's arrays
+        need_b = ffg.ffg_workspace_bytes(space, nbh)
+        wsb = ffg.workspace(need_b, dev)
+
+        def count_fill():
+            g0 = ffg.ffg_graph()
+            assert ffg.ffg_build_count(space, fd.data_ptr(), nbh, 1e10, g0, wsb.data_ptr(),
+                                       need_b, sh) == 0
+            assert ffg.ffg_build_fill(space, fd.data_ptr(), nbh, 1e10, g.c, wsb.data_ptr(),
+                                      need_b, sh) == 0
+        count_fill()
+        build_us = 1e3 * ev_ms(stream, count_fill, reps=reps, agg=statistics.median)
+        del wsb
         need = ffg.pagerank_workspace_bytes(g.n_nodes, g.n_edges, ffg.F64)
         ws = ffg.workspace(need, dev)
         res = {}
@@ -711,7 +725,8 @@ def run_single_large(ffg, fi, dev, stream, reps=5):
             if prec == ffg.F32:
                 res["_x"] = x.double().cpu().numpy()
                 res["cp"] = np.asarray(ffg.centrality(g, fd, x, P_LIST))
-        out[name] = {"n_nodes": g.n_nodes, "n_edges": g.n_edges, **res,
+        out[name] = {"n_nodes": g.n_nodes, "n_edges": g.n_edges, "count_fill_us": build_us,
+                     **res,
                      "roofline": {"bound": "l2/issue", "kernel": "k_pagerank<float>",
                                   "effective_gbs": res["f32"]["effective_gbs"],
                                   "frac_of_measured_hbm_effective":
