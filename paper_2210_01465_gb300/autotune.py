@@ -46,6 +46,7 @@ CANDIDATES = (
     (0.05, 0.005, 0, 24, 1, 0, 4),
     (0.02, 0.002, 0, 24, 1, 0, 8),
     (0.01, 0.001, 0, 24, 1, 0, 4),
+    (0.05, 0.005, 0, 16, 1),
     (1.0, 1.0, 0, 24, 2),
     (1.0, 1.0, 0, 16, 2),
 )
