@@ -141,7 +141,8 @@ def test_batch_tuning_validated_on_host(lib):
     jobs = (ffg.ffg_pr_job * 1)()
     plan = ffg.ffg_pr_batch()
     for tuning in ((0.0, 1.0, 0), (1.0, -1.0, 0), (float("nan"), 1.0, 0), (1.0, 1.0, -2),
-                   (1.0, 1.0, 0, 12), (1.0, 1.0, 0, 32), (1.0, 1.0, 0, 8, 2), (1.0, 1.0, 0, 8, 0, 3)):
+                   (1.0, 1.0, 0, 12), (1.0, 1.0, 0, 32), (1.0, 1.0, 0, 8, 2), (1.0, 1.0, 0, 8, 0, 3),
+                   (1.0, 1.0, 0, 24, 1, 0, -1), (1.0, 1.0, 0, 24, 0, 0, (1 << 20) + 1)):
         assert ffg.pagerank_batch_plan_tuned(jobs, ffg.F32, tuning, 256, 1 << 20, plan) == \
             ffg.FFG_ERR_INVALID_ARG
         assert "tuning" in ffg.ffg_last_error()
