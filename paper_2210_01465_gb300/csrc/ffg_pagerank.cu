@@ -232,9 +232,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     }
 }
 
+// Liveness of the PageRank kernels of this context: every block adds one
+// each time it publishes a phase's sums.  A bounded wait restarts its clock
+// whenever the count moves, so a group may wait for ranks that are busy with
+// an earlier job for as long as that job takes, and gives up only after
+// kTimeoutNs in which no block anywhere made progress.
+__device__ unsigned int g_heartbeat;
+__device__ __forceinline__ void beat() {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&g_heartbeat) : "memory");
+}
+__device__ __forceinline__ unsigned heartbeat() { return *(volatile unsigned *)&g_heartbeat; }
+
 // Barrier over the `group` blocks of one job (all co-resident: cooperative
-// launch).  Bounded: gives up after
-// kTimeoutNs (or 2^24 polls), records FFG_ERR_TIMEOUT.  Returns false
+// launch).  Bounded: gives up after kTimeoutNs (or 2^24 polls) without
+// progress anywhere (see beat), records FFG_ERR_TIMEOUT.  Returns false
 // (uniformly for the whole block) if the run must stop.
 __device__ bool group_barrier(PrCtl *ctl, unsigned target, int group) {
     __shared__ int s_ok;
@@ -244,11 +255,19 @@ __device__ bool group_barrier(PrCtl *ctl, unsigned target, int group) {
         // release: this block's writes (ordered before by the block barrier)
         // become visible to every block that acquires the count
         red_release_add(&ctl->barrier, 1u);
-        const uint64_t t0 = global_ns();
-        unsigned ns = 0;
+        uint64_t t0 = global_ns();
+        unsigned ns = 0, hb = heartbeat();
         int ok = 1;
         for (uint32_t polls = 0; ld_acquire(&ctl->barrier) < target; ++polls) {
-            if ((polls & 15) == 15 && *(volatile int *)&ctl->status != 0) { ok = 0; break; }
+            if ((polls & 15) == 15) {
+                if (*(volatile int *)&ctl->status != 0) { ok = 0; break; }
+                const unsigned h = heartbeat();
+                if (h != hb) {  // some block progressed: wait on
+                    hb = h;
+                    t0 = global_ns();
+                    polls = 0;
+                }
+            }
             if (polls > (1u << 24) || global_ns() - t0 > kTimeoutNs) {
                 atomicCAS(&ctl->status, 0, (int)FFG_ERR_TIMEOUT);
                 ok = 0;
@@ -280,11 +299,19 @@ __device__ bool group_wait(PrCtl *ctl, unsigned target, int group) {
         return true;
     }
     if (threadIdx.x == 0) {
-        const uint64_t t0 = global_ns();
-        unsigned ns = 0;
+        uint64_t t0 = global_ns();
+        unsigned ns = 0, hb = heartbeat();
         int ok = 1;
         for (uint32_t polls = 0; ld_acquire(&ctl->barrier) < target; ++polls) {
-            if ((polls & 15) == 15 && *(volatile int *)&ctl->status != 0) { ok = 0; break; }
+            if ((polls & 15) == 15) {
+                if (*(volatile int *)&ctl->status != 0) { ok = 0; break; }
+                const unsigned h = heartbeat();
+                if (h != hb) {  // some block progressed: wait on
+                    hb = h;
+                    t0 = global_ns();
+                    polls = 0;
+                }
+            }
             if (polls > (1u << 24) || global_ns() - t0 > kTimeoutNs) {
                 atomicCAS(&ctl->status, 0, (int)FFG_ERR_TIMEOUT);
                 ok = 0;
@@ -386,6 +413,7 @@ __device__ __forceinline__ Fix3 block_sum_fix(Fix3 v) {
 // thread 0: add the block's sums into buffer `buf`; rank 0 also clears the
 // buffer of the next phase
 __device__ __forceinline__ void publish(PrCtl *ctl, int buf, const Fix3 &b, int rank) {
+    beat();
     if (b.r) atomicAdd(&ctl->acc[buf][0], static_cast<unsigned long long>(b.r));
     if (b.d) atomicAdd(&ctl->acc[buf][1], static_cast<unsigned long long>(b.d));
     if (b.s) atomicAdd(&ctl->acc[buf][2], static_cast<unsigned long long>(b.s));
@@ -1336,11 +1364,19 @@ __device__ bool sweep_barrier(SweepCtl *ctl, unsigned target, int *s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
         red_release_add(&ctl->barrier, 1u);
-        const uint64_t t0 = global_ns();
-        unsigned ns = 0;
+        uint64_t t0 = global_ns();
+        unsigned ns = 0, hb = heartbeat();
         int ok = 1;
         for (uint32_t polls = 0; ld_acquire(&ctl->barrier) < target; ++polls) {
-            if ((polls & 15) == 15 && *(volatile int *)&ctl->status != 0) { ok = 0; break; }
+            if ((polls & 15) == 15) {
+                if (*(volatile int *)&ctl->status != 0) { ok = 0; break; }
+                const unsigned h = heartbeat();
+                if (h != hb) {  // some block progressed: wait on
+                    hb = h;
+                    t0 = global_ns();
+                    polls = 0;
+                }
+            }
             if (polls > (1u << 24) || global_ns() - t0 > kTimeoutNs) {
                 atomicCAS(&ctl->status, 0, (int)FFG_ERR_TIMEOUT);
                 ok = 0;

@@ -362,6 +362,42 @@ def test_bounded_wait_reports_timeout():
     assert (sts == ffg.FFG_OK).all()
 
 
+def test_group_waits_for_a_long_earlier_job():
+    """A group's blocks wait for a rank that is busy with an earlier job for as
+    long as that job runs: a bounded wait gives up only when no block makes
+    progress.  Job A (PnPoly, 8184 nodes, FP64, tol 0: it runs all of
+    max_iter, several seconds, on one block) is claimed first; job B (1.42M
+    nodes) has a rank on every block, one of them A's, so B's other ranks wait
+    at B's first barrier longer than the 2 s a wait without progress may last.
+    Both finish, and B gives the bits of a solve of B alone."""
+    small, big = fi.pnpoly_space(), fi.single_large()
+    ga, _ = run_build(small, fi.runtimes(small, 3), "hamming")
+    gb, _ = run_build(big, fi.runtimes(big, 1), "adjacent")
+    batch = ffg.PageRankBatch([(ga, 0.85), (gb, 0.85)], prec=ffg.F64, tol=1e-12)
+    batch.jobs[0].tol = 0.0
+    batch.jobs[0].max_iter = 60000
+    # min_tiles 12 keeps A on one block and still spreads B over every block
+    batch.replan((0.01, 0.001, 0, 24, 1, 0, 12), job_cost=[100.0, 10.0])
+    assert batch.plan.n_items == 1 + batch.plan.n_blocks   # A alone, B on every block
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    batch.run()
+    e1.record()
+    e1.synchronize()
+    st, it, res, sts = ffg.pagerank_batch_query(batch.plan,
+                                                torch.cuda.current_stream().cuda_stream)
+    ms = e0.elapsed_time(e1)
+    print(f"\nA {it[0]} iterations, B {it[1]} iterations, {ms:.0f} ms")
+    assert sts[0] == ffg.FFG_ERR_NOT_CONVERGED and it[0] == 60000
+    assert sts[1] == ffg.FFG_OK
+    assert ms > 2100.0, ms   # B's ranks did wait longer than the limit
+    ref = ffg.PageRankBatch([(gb, 0.85)], prec=ffg.F64, tol=1e-12)
+    ref.run()
+    it_r, _, st_r = ref.query()
+    assert st_r[0] == ffg.FFG_OK and it_r[0] == it[1]
+    np.testing.assert_array_equal(_np(batch.ranks[1]), _np(ref.ranks[0]))
+
+
 def test_precision_form_at_scale():
     """11 parameters, 19.5M raw / 12.8M valid points, Hamming: the FFG is
     bit-exact; FP32 ranks (FP64/exact reductions) and C_p are compared with the
