@@ -53,7 +53,9 @@ typedef enum {
     FFG_ERR_CUDA = 3,          /* a CUDA runtime call failed (see ffg_last_error) */
     FFG_ERR_EMPTY = 4,         /* the space has no valid configuration / no minimum */
     FFG_ERR_NOT_CONVERGED = 5, /* max_iter reached; the ranks are still written */
-    FFG_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired */
+    FFG_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired: PageRank's
+                                  barriers give up after 2 s in which no block of
+                                  any PageRank kernel made progress */
     FFG_ERR_NO_MEMORY = 7      /* the workspace passed is too small */
 } ffg_status;
 
